@@ -1,0 +1,309 @@
+"""Benchmark: gate applications per second of the random-layer circuit.
+
+Workload (one "step" = one pass of the whole hot path over one circuit):
+  * state |0...0> initialised on the device (a1);
+  * the 20-layer random-layer circuit -- U3(theta, phi, lambda) on every qubit,
+    then CZ on (i, i+1) for even i in even layers and odd i in odd layers,
+    angles ~ U[0, 2 pi) from seed 2 -- on n = 32 qubits in complex64 (32 GiB):
+    950 gates, applied by the planner's tiled multi-gate passes (a2-a6);
+  * read-out: squared norm and <sum_i Z_i Z_{i+1}> with FP64 accumulation (a8).
+The state (32 GiB) is far larger than L2 (129 MB), so no L2 flush is needed.
+
+Metric: logical (pre-fusion) gate applications per second, whole job (all
+ranks). Multi-GPU: independent replicas, one per rank ("replicas only":
+the single-state path does not shard without an exchange step), weak scaling.
+
+``--impl reference`` times the CPU oracle (the plain complex128 unfused
+simulator) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "gate apps/s (random-layer circuit, 20 layers)"
+UNIT = "gate/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--layers", type=int, default=20)
+    ap.add_argument("--mode", default="auto", choices=["auto", "unfused", "tiled", "fused"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"random-layer circuit, {a.layers} layers, n={a.n}, {a.dtype}",
+            "n_qubits": a.n, "state_dtype": a.dtype, "layers": a.layers, "seed": 2,
+            "mode": a.mode, "state_bytes": (1 << a.n) * (8 if a.dtype == "c64" else 16),
+            "l2_flush": "not needed: state larger than L2"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(a, budget_s: float = 15.0):
+    """Time the oracle (plain C complex128, one thread) on a bounded sample of
+    the workload: the same circuit family at n_s qubits, first gates in order,
+    until ~budget_s; per-gate time scaled by 2^(n - n_s) to the full n."""
+    import oracle
+    from paper_2009_01845_gb300 import inputs as qi
+    n_s = min(a.n, 24)
+    gates = qi.random_layer_circuit(n_s, a.layers, seed=2)
+    psi = oracle.zero_state(n_s)
+    done, t0 = 0, time.perf_counter()
+    for g in gates:
+        oracle.apply_gate(psi, n_s, g)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    per_gate_full = dt / done * 2.0 ** (a.n - n_s)
+    return {"value": 1.0 / per_gate_full, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} gates of the same circuit at n={n_s} (complex128, "
+                      f"{dt:.1f} s), per-gate time scaled by 2^{a.n - n_s} to n={a.n}"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = []
+    for i in range(a.warmup + a.steps):
+        r = oracle_sample(a, budget_s=max(2.0, 60.0 / max(1, a.steps + a.warmup)))
+        if i >= a.warmup:
+            per_step.append(r)
+    v = statistics.median(x["value"] for x in per_step)
+    ms = 1000.0 * (a.layers * a.n + a.layers * (a.n - 1) // 2 + 0) / v if v else None
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": per_step[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2009_01845_gb300 import build as qbuild
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+
+    if rank == 0 or not os.path.exists(qbuild.LIB):
+        qbuild.build()
+    barrier()
+    qsim.load()
+
+    n = a.n
+    gates = qi.random_layer_circuit(n, a.layers, seed=2)
+    zz = [(1.0, 0, (1 << i) | (1 << (i + 1))) for i in range(n - 1)]
+    st = qsim.State(n, dtype=a.dtype)
+    gate_arr, keep = qsim.marshal_gates(gates)
+    o = qsim.opts(a.mode)
+    zz_arr, zz_n = qsim.marshal_terms(zz)
+    import ctypes
+    import numpy as np
+    out_re = np.zeros(1)
+    out_n = np.zeros(1)
+
+    def step():
+        st.init_basis(0)
+        qsim._check(st.lib.qs_apply_gates(st.handle, gate_arr, len(gates), ctypes.byref(o)))
+        qsim._check(st.lib.qs_norm2(st.handle, ctypes.c_void_p(out_n.ctypes.data)))
+        qsim._check(st.lib.qs_expectation(st.handle, zz_arr, zz_n, ctypes.c_void_p(out_re.ctypes.data), None))
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if abs(out_n[0] - 1.0) > 1e-3:
+        raise RuntimeError(f"norm drifted: {out_n[0]}")
+
+    clocks = ClockSampler(local)
+    qsim.profile_collect()
+    qsim.profile_enable(True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(a.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    qsim.profile_enable(False)
+    prof = qsim.profile_collect()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * len(gates) / (ms / 1000.0)
+
+    # roofline of the dominant kernel class (algorithmic bytes: one read and one
+    # write of the state per dense or tiled pass)
+    b = 8 if a.dtype == "c64" else 16
+    B = 2 * (1 << n) * b
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (tot_ms, launches) = dom
+    per_launch_bytes = {"dense": B, "tiled": B, "fused_tc": B}.get(name)
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if per_launch_bytes and launches:
+        ach = per_launch_bytes * launches / (tot_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                "launches_per_step": launches / a.steps,
+                "avg_launch_ms": tot_ms / launches}
+    launches_total = int(sum(v[1] for v in prof.values()))
+
+    # end to end through the public Python API with host inputs: marshal the
+    # gate list from Python objects, apply, read back the results to the host
+    e2e = None
+    if not a.no_e2e:
+        e_steps = max(1, min(a.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(e_steps):
+            st.init_basis(0)
+            arr, kp = qsim.marshal_gates(gates)
+            h2d = ctypes.sizeof(arr) + 8
+            qsim._check(st.lib.qs_apply_gates(st.handle, arr, len(gates), ctypes.byref(o)))
+            r1 = st.norm2()
+            r2 = st.expectation(zz)
+            d2h = r1.nbytes + 16
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1000.0 / e_steps
+        e2e = {"value": world * len(gates) / (e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = oracle_sample(a)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if a.dtype == "c64" else "f64",
+                "data": "synthetic", "config": workload_config(a),
+                "parallelism": "replicas" if world > 1 else "single",
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches_total,
+                "kernels": {k: {"ms_per_step": v[0] / a.steps, "launches_per_step": v[1] / a.steps}
+                            for k, v in prof.items() if v[1]},
+                "energy_zz": float(out_re[0]), "norm2": float(out_n[0])}
+        print(json.dumps(line), flush=True)
+    st.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * qsim.h -- C-ABI of the GB300 (sm_103a) state-vector simulator core.
+ *
+ * The operations follow the Qibo paper (arXiv:2009.01845):
+ *   - state allocation and initialisation: Sec. 2.3 (dense 2^n complex state,
+ *     updated in place, 2^n complex numbers of memory);
+ *   - gate application: Eq. (1) of Sec. 2.3, controls as in Sec. 2.4
+ *     ("Controlled gates"), fused blocks as in Sec. 2.4 ("Gate fusion");
+ *   - probabilities: Sec. 2.4 ("Measurements");
+ *   - Pauli-sum expectation values: Sec. 2.4 ("Callbacks", Energy);
+ *   - Trotter steps of H(s) = (1-s) H0 + s H1: Sec. 2.6, Eqs. (4)-(6);
+ *   - adjoint gradients and batched execution have no counterpart in the
+ *     paper (which differentiates through its TensorFlow backends only,
+ *     Sec. 2.3); their definitions are stated at each declaration.
+ *
+ * Conventions used by every call:
+ *   - qubit q is bit (n-1-q) of a basis index: qubit 0 is the most
+ *     significant bit (Sec. 2.5, global qubits split the state in contiguous
+ *     halves);
+ *   - amplitudes are interleaved (re, im): complex64 = 2 x float,
+ *     complex128 = 2 x double; a batch of B states of n qubits is B contiguous
+ *     blocks of 2^n amplitudes;
+ *   - a k-target gate matrix is row-major 2^k x 2^k with local index
+ *     sum_j bit(target_j) 2^(k-1-j) (the first target is the local MSB);
+ *   - rotation conventions: R_P(t) = exp(-i t P/2); U1(l) = diag(1, e^{il});
+ *     CU1(t) = diag(1,1,1,e^{it}); U3 is OpenQASM 2's
+ *     [[cos t/2, -e^{il} sin t/2], [e^{ip} sin t/2, e^{i(p+l)} cos t/2]];
+ *     U2(p,l) = U3(pi/2,p,l);
+ *   - Pauli masks: bit q of x_mask/z_mask refers to qubit q; X = x only,
+ *     Z = z only, Y = both (Y = i X Z).
+ *
+ * Errors: every call returns a qs_status and never throws or aborts. On a
+ * non-zero status nothing was launched unless the status is QS_ERR_CUDA, in
+ * which case the device state is unspecified. qs_last_error() returns a
+ * thread-local message for the last failure on the calling thread.
+ *
+ * Streams: every call is ordered on the state's stream (set at create/wrap;
+ * NULL = the legacy default stream). Calls that return values to host memory
+ * synchronise that stream before returning; all others are asynchronous.
+ * Host pointers need not be pinned.
+ *
+ * Threads: a qs_state may be used by one host thread at a time.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qs_status;
+#define QS_OK 0
+#define QS_ERR_ARG 1          /* invalid argument: qubit range, arity, null pointer, size */
+#define QS_ERR_OOM 2          /* device allocation failed */
+#define QS_ERR_CUDA 3         /* a CUDA runtime call or kernel launch failed */
+#define QS_ERR_UNSUPPORTED 4  /* valid request outside what this build implements */
+#define QS_ERR_TIMEOUT 5      /* a bounded device-side wait ran out */
+
+typedef int32_t qs_dtype;
+#define QS_C64 0              /* complex64 state: float re, float im */
+#define QS_C128 1             /* complex128 state: double re, double im */
+
+/* Gate kinds. Arity (targets, parameters) in parentheses. */
+#define QS_GATE_H 0           /* (1,0) Hadamard */
+#define QS_GATE_X 1           /* (1,0) */
+#define QS_GATE_Y 2           /* (1,0) */
+#define QS_GATE_Z 3           /* (1,0) */
+#define QS_GATE_S 4           /* (1,0) diag(1, i) */
+#define QS_GATE_SDG 5         /* (1,0) diag(1, -i) */
+#define QS_GATE_T 6           /* (1,0) diag(1, e^{i pi/4}) */
+#define QS_GATE_TDG 7         /* (1,0) diag(1, e^{-i pi/4}) */
+#define QS_GATE_RX 8          /* (1,1) */
+#define QS_GATE_RY 9          /* (1,1) */
+#define QS_GATE_RZ 10         /* (1,1) */
+#define QS_GATE_U1 11         /* (1,1) */
+#define QS_GATE_U2 12         /* (1,2) */
+#define QS_GATE_U3 13         /* (1,3) */
+#define QS_GATE_CZ 14         /* (2,0) diag(1,1,1,-1) */
+#define QS_GATE_CU1 15        /* (2,1) diag(1,1,1,e^{it}); CZPow(t) = CU1(pi t) */
+#define QS_GATE_SWAP 16       /* (2,0) */
+#define QS_GATE_UNITARY 17    /* (k,0), 1 <= k <= 5, matrix given */
+#define QS_GATE_KIND_COUNT 18
+
+#define QS_MAX_TARGETS 5
+#define QS_MAX_QUBITS 40
+
+/* One gate of a queue (Eq. (1); a circuit is an ordered queue, Sec. 2.3). */
+typedef struct qs_gate {
+    int32_t kind;                     /* QS_GATE_* */
+    int32_t n_targets;                /* must equal the kind's arity; 1..5 for UNITARY */
+    int32_t targets[QS_MAX_TARGETS];  /* qubit indices, distinct, in [0, n) */
+    int32_t param_index;              /* batched calls: column of the parameter
+                                         table driving params[0], or -1 */
+    uint64_t control_mask;            /* bit q set: qubit q is a control (all must be 1) */
+    double params[3];                 /* angles, used by RX RY RZ U1 U2 U3 CU1 */
+    const double *matrix;             /* UNITARY only: host pointer to 2^k x 2^k
+                                         complex128 (interleaved, row-major); read
+                                         during the call only */
+} qs_gate;
+
+/* One term c * P of a Pauli-sum Hamiltonian. */
+typedef struct qs_pauli_term {
+    double coeff;
+    uint64_t x_mask;
+    uint64_t z_mask;
+} qs_pauli_term;
+
+/* Execution strategy for qs_apply_gates. */
+#define QS_MODE_AUTO 0        /* planner's choice (tiled passes) */
+#define QS_MODE_UNFUSED 1     /* one kernel pass per gate (the plain simulator) */
+#define QS_MODE_TILED 2       /* shared-memory/register tiles, many gates per pass */
+#define QS_MODE_FUSED_TC 3    /* gates fused into <=5-qubit dense blocks on tensor cores */
+
+typedef struct qs_opts {
+    int32_t mode;             /* QS_MODE_* */
+    int32_t tile_qubits;      /* tiled mode: tile width k (0 = default) */
+    int32_t fuse_qubits;      /* fused mode: block width (0 = 5) */
+    int32_t flags;            /* reserved, must be 0 */
+} qs_opts;
+
+typedef struct qs_state qs_state;
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *qs_last_error(void);
+/* Library version string. */
+const char *qs_version(void);
+
+/* ---------------------------------------------------------------- states */
+/* Allocate a batch of `batch` states of n qubits (batch * 2^n amplitudes) on the
+   current CUDA device; the library owns and frees the memory. Contents are
+   undefined until initialised. QS_ERR_OOM if the allocation fails. */
+qs_status qs_state_create(int n, int batch, qs_dtype dtype, void *cuda_stream, qs_state **out);
+/* Wrap caller-owned device memory of batch * 2^n amplitudes (16-byte aligned);
+   the handle never frees it and it must outlive the handle. */
+qs_status qs_state_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *cuda_stream,
+                        qs_state **out);
+/* Release the handle (and the memory if the library allocated it). NULL is a no-op. */
+qs_status qs_state_destroy(qs_state *s);
+/* Device pointer of the amplitudes. */
+qs_status qs_state_data(const qs_state *s, void **dev_ptr);
+/* Change the stream later calls are ordered on. */
+qs_status qs_state_set_stream(qs_state *s, void *cuda_stream);
+
+/* |x> in every batch member (x < 2^n). */
+qs_status qs_state_init_basis(qs_state *s, uint64_t x);
+/* |+>^n in every batch member: every amplitude 2^{-n/2}. */
+qs_status qs_state_init_plus(qs_state *s);
+/* Copy batch * 2^n amplitudes in (from host when on_device = 0, else device). */
+qs_status qs_state_set(qs_state *s, const void *src, int on_device);
+/* Copy batch * 2^n amplitudes out (to host when on_device = 0, else device). */
+qs_status qs_state_get(const qs_state *s, void *dst, int on_device);
+
+/* ---------------------------------------------------------------- gates */
+/* Apply a gate queue in order to every batch member (Eq. (1), Sec. 2.3-2.4).
+   opts may be NULL (= QS_MODE_AUTO). Qubits are validated: in range, targets
+   distinct, controls disjoint from targets, arity matching the kind, else
+   QS_ERR_ARG and nothing is applied. */
+qs_status qs_apply_gates(qs_state *s, const qs_gate *gates, size_t count, const qs_opts *opts);
+
+/* Batched parameters: like qs_apply_gates, but a gate whose param_index p >= 0
+   takes its angle params[0] from params[b * n_params + p] for batch member b.
+   `params` is a device pointer to batch * n_params doubles (row-major), read
+   in stream order. Supported for RX RY RZ U1 CU1 gates. */
+qs_status qs_apply_gates_batched(qs_state *s, const qs_gate *gates, size_t count,
+                                 const double *params_dev, int n_params, const qs_opts *opts);
+
+/* ---------------------------------------------------------------- read-out */
+/* |psi_x|^2 for every batch member, FP64, index = b * 2^n + x (qubit 0 = MSB of x).
+   out: host (on_device = 0) or device pointer to batch * 2^n doubles. */
+qs_status qs_probabilities(qs_state *s, double *out, int on_device);
+/* sum_x |psi_x|^2 per batch member (FP64 accumulation); out: host, batch doubles. */
+qs_status qs_norm2(qs_state *s, double *out);
+/* <psi|H|psi> per batch member for H = sum_t coeff_t P_t (FP64 accumulation).
+   out_re/out_im: host arrays of batch doubles (out_im may be NULL). */
+qs_status qs_expectation(qs_state *s, const qs_pauli_term *terms, size_t count,
+                         double *out_re, double *out_im);
+
+/* ---------------------------------------------------------------- Trotter (Sec. 2.6) */
+/* One second-order Trotter step of H(s) = (1-s) H0 + s H1 on every batch member:
+     psi <- exp(-i dt/2 D(s)) exp(-i dt X(s)) exp(-i dt/2 D(s)) psi
+   where D(s) collects the Z-string terms (x_mask = 0) and X(s) the
+   single-qubit X terms (z_mask = 0, one x bit) of H(s). Phase angles are
+   evaluated in FP64. Any other term: QS_ERR_UNSUPPORTED. */
+qs_status qs_trotter_step(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
+                          const qs_pauli_term *h1, size_t n_h1, double s_val, double dt);
+/* Adiabatic evolution with the linear schedule s = t/T (Sec. 2.6): K = round(T/dt)
+   second-order steps, step k taking s = (k + 1/2) dt / T; `steps` >= 0 stops after
+   that many steps (-1 = all K). Adjacent half-step diagonals of consecutive steps
+   are merged (they commute), which changes only rounding. */
+qs_status qs_adiabatic_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
+                              const qs_pauli_term *h1, size_t n_h1, double T, double dt,
+                              int steps);
+
+/* ---------------------------------------------------------------- launch accounting */
+/* Tracing aid (no counterpart in the paper). While enabled, every kernel launch
+   of the library is bracketed by CUDA events on the launching stream, grouped
+   by kernel class (dense, phase, diag, swap, param, tiled, fused_tc, reduce,
+   trotter_diag, adjoint, init). Process-wide. */
+qs_status qs_profile_enable(int on);
+/* Wait for the recorded launches, write per-class total milliseconds and launch
+   counts into arrays of n_classes entries, and reset the record. */
+qs_status qs_profile_collect(double *total_ms, long long *launches, int n_classes);
+/* Name of kernel class c ("" if out of range) and the number of classes. */
+const char *qs_profile_class_name(int c);
+int qs_profile_class_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

@@ -1,0 +1,389 @@
+// The C-ABI entry points declared in include/qsim.h: argument validation,
+// state handles, and dispatch to the planners and kernels. No exception or
+// abort crosses this boundary; every failure becomes a qs_status plus a
+// thread-local message.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace qsim {
+const char *last_error();
+}
+
+using namespace qsim;
+
+#define QS_GUARD_BEGIN try {
+#define QS_GUARD_END                                                     \
+    }                                                                    \
+    catch (const std::bad_alloc &) {                                     \
+        set_error("host allocation failed");                             \
+        return QS_ERR_OOM;                                               \
+    }                                                                    \
+    catch (...) {                                                        \
+        set_error("internal error");                                     \
+        return QS_ERR_CUDA;                                              \
+    }
+
+static qs_status check_state(const qs_state *s) {
+    if (!s) {
+        set_error("null state handle");
+        return QS_ERR_ARG;
+    }
+    return QS_OK;
+}
+
+static qs_status check_shape(int n, int batch, qs_dtype dtype) {
+    if (n < 1 || n > QS_MAX_QUBITS) {
+        set_error("n = %d outside [1, %d]", n, QS_MAX_QUBITS);
+        return QS_ERR_ARG;
+    }
+    if (batch < 1 || batch > (1 << 24)) {
+        set_error("batch = %d outside [1, 2^24]", batch);
+        return QS_ERR_ARG;
+    }
+    if (dtype != QS_C64 && dtype != QS_C128) {
+        set_error("unknown dtype %d", dtype);
+        return QS_ERR_ARG;
+    }
+    // total amplitudes must stay below 2^46 (64-bit index arithmetic with headroom)
+    if ((uint64_t)batch > (1ull << (46 - n))) {
+        set_error("batch * 2^n too large");
+        return QS_ERR_ARG;
+    }
+    return QS_OK;
+}
+
+static size_t state_bytes(const qs_state *s) {
+    return ((size_t)s->batch << s->n) * (s->dtype == QS_C64 ? 8 : 16);
+}
+
+extern "C" {
+
+const char *qs_last_error(void) { return qsim::last_error(); }
+const char *qs_version(void) { return "qsim-gb300 0.1 (sm_103a)"; }
+
+qs_status qs_state_create(int n, int batch, qs_dtype dtype, void *stream, qs_state **out) {
+    QS_GUARD_BEGIN
+    clear_error();
+    if (!out) {
+        set_error("null output pointer");
+        return QS_ERR_ARG;
+    }
+    *out = nullptr;
+    QS_TRY(check_shape(n, batch, dtype));
+    qs_state *s = new qs_state();
+    s->n = n;
+    s->batch = batch;
+    s->dtype = dtype;
+    s->stream = (cudaStream_t)stream;
+    s->owns = true;
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaMalloc(&s->data, state_bytes(s));
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_status(e, "cudaMalloc(state)");
+    }
+    *out = s;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_state_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *stream, qs_state **out) {
+    QS_GUARD_BEGIN
+    clear_error();
+    if (!out) {
+        set_error("null output pointer");
+        return QS_ERR_ARG;
+    }
+    *out = nullptr;
+    QS_TRY(check_shape(n, batch, dtype));
+    if (!dev_ptr || ((uintptr_t)dev_ptr & 15u)) {
+        set_error("device pointer must be non-null and 16-byte aligned");
+        return QS_ERR_ARG;
+    }
+    qs_state *s = new qs_state();
+    s->n = n;
+    s->batch = batch;
+    s->dtype = dtype;
+    s->stream = (cudaStream_t)stream;
+    s->data = dev_ptr;
+    s->owns = false;
+    cudaGetDevice(&s->device);
+    *out = s;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_state_destroy(qs_state *s) {
+    QS_GUARD_BEGIN
+    if (!s) return QS_OK;
+    if (s->owns || s->scratch || s->host_pinned || s->gtab) cudaStreamSynchronize(s->stream);
+    if (s->owns && s->data) cudaFree(s->data);
+    if (s->scratch) cudaFree(s->scratch);
+    if (s->host_pinned) cudaFreeHost(s->host_pinned);
+    if (s->gtab) cudaFree(s->gtab);
+    plan_cache_release(s);
+    delete s;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_state_data(const qs_state *s, void **dev_ptr) {
+    QS_TRY(check_state(s));
+    if (!dev_ptr) {
+        set_error("null output pointer");
+        return QS_ERR_ARG;
+    }
+    *dev_ptr = s->data;
+    return QS_OK;
+}
+
+qs_status qs_state_set_stream(qs_state *s, void *stream) {
+    QS_TRY(check_state(s));
+    s->stream = (cudaStream_t)stream;
+    return QS_OK;
+}
+
+qs_status qs_state_init_basis(qs_state *s, uint64_t x) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (s->n < 64 && (x >> s->n) != 0) {
+        set_error("basis index %llu >= 2^%d", (unsigned long long)x, s->n);
+        return QS_ERR_ARG;
+    }
+    return k_init_basis(s, x);
+    QS_GUARD_END
+}
+
+qs_status qs_state_init_plus(qs_state *s) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    return k_init_plus(s);
+    QS_GUARD_END
+}
+
+qs_status qs_state_set(qs_state *s, const void *src, int on_device) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!src) {
+        set_error("null source");
+        return QS_ERR_ARG;
+    }
+    QS_CUDA_TRY(cudaMemcpyAsync(s->data, src, state_bytes(s),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
+    if (!on_device) QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_state_get(const qs_state *s, void *dst, int on_device) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!dst) {
+        set_error("null destination");
+        return QS_ERR_ARG;
+    }
+    QS_CUDA_TRY(cudaMemcpyAsync(dst, s->data, state_bytes(s),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+    if (!on_device) QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return QS_OK;
+    QS_GUARD_END
+}
+
+static qs_status lower_all(const qs_state *s, const qs_gate *gates, size_t count, std::vector<LGate> *out) {
+    if (count && !gates) {
+        set_error("null gate array");
+        return QS_ERR_ARG;
+    }
+    out->resize(count);
+    for (size_t i = 0; i < count; ++i) {
+        qs_status st = lower_gate(s->n, gates[i], &(*out)[i]);
+        if (st != QS_OK) {
+            char buf[512];
+            std::snprintf(buf, sizeof(buf), "gate %zu: %s", i, qs_last_error());
+            set_error("%s", buf);
+            return st;
+        }
+    }
+    return QS_OK;
+}
+
+static qs_status check_opts(const qs_opts *o, int *mode) {
+    *mode = o ? o->mode : QS_MODE_AUTO;
+    if (*mode < QS_MODE_AUTO || *mode > QS_MODE_FUSED_TC) {
+        set_error("unknown mode %d", *mode);
+        return QS_ERR_ARG;
+    }
+    if (o && o->flags != 0) {
+        set_error("opts.flags must be 0");
+        return QS_ERR_ARG;
+    }
+    return QS_OK;
+}
+
+qs_status qs_apply_gates(qs_state *s, const qs_gate *gates, size_t count, const qs_opts *opts) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    int mode;
+    QS_TRY(check_opts(opts, &mode));
+    std::vector<LGate> lg;
+    QS_TRY(lower_all(s, gates, count, &lg));
+    for (auto &g : lg)
+        if (g.param_index >= 0) g.param_index = -1;  // unbatched call: angles come from params
+    return run_gates(s, lg, mode, opts, nullptr, 0);
+    QS_GUARD_END
+}
+
+qs_status qs_apply_gates_batched(qs_state *s, const qs_gate *gates, size_t count, const double *params_dev,
+                                 int n_params, const qs_opts *opts) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    int mode;
+    QS_TRY(check_opts(opts, &mode));
+    std::vector<LGate> lg;
+    QS_TRY(lower_all(s, gates, count, &lg));
+    for (size_t i = 0; i < lg.size(); ++i) {
+        const int p = lg[i].param_index;
+        if (p < 0) continue;
+        if (p >= n_params || !params_dev) {
+            set_error("gate %zu: param_index %d outside [0, %d)", i, p, n_params);
+            return QS_ERR_ARG;
+        }
+        const int kd = lg[i].kind;
+        if (kd != QS_GATE_RX && kd != QS_GATE_RY && kd != QS_GATE_RZ && kd != QS_GATE_U1 && kd != QS_GATE_CU1) {
+            set_error("gate %zu: batched parameters apply to RX RY RZ U1 CU1 only", i);
+            return QS_ERR_ARG;
+        }
+    }
+    return run_gates(s, lg, mode, opts, params_dev, n_params);
+    QS_GUARD_END
+}
+
+static qs_status read_back(qs_state *s, const double *dev, double *host, size_t count) {
+    QS_CUDA_TRY(cudaMemcpyAsync(host, dev, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return QS_OK;
+}
+
+qs_status qs_probabilities(qs_state *s, double *out, int on_device) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!out) {
+        set_error("null output");
+        return QS_ERR_ARG;
+    }
+    if (on_device) return k_probabilities(s, out);
+    const size_t total = (size_t)s->batch << s->n;
+    double *tmp = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync(&tmp, total * sizeof(double), s->stream));
+    qs_status st = k_probabilities(s, tmp);
+    if (st == QS_OK) st = read_back(s, tmp, out, total);
+    cudaFreeAsync(tmp, s->stream);
+    return st;
+    QS_GUARD_END
+}
+
+qs_status qs_norm2(qs_state *s, double *out) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!out) {
+        set_error("null output");
+        return QS_ERR_ARG;
+    }
+    QS_TRY(ensure_host_pinned(s, (size_t)s->batch));
+    double *dev = nullptr;
+    QS_TRY(k_norm2(s, &dev));
+    QS_TRY(read_back(s, dev, s->host_pinned, s->batch));
+    std::memcpy(out, s->host_pinned, sizeof(double) * s->batch);
+    return QS_OK;
+    QS_GUARD_END
+}
+
+static qs_status check_terms(const qs_state *s, const qs_pauli_term *t, size_t count) {
+    if (count && !t) {
+        set_error("null term array");
+        return QS_ERR_ARG;
+    }
+    for (size_t i = 0; i < count; ++i) {
+        if (s->n < 64 && ((t[i].x_mask | t[i].z_mask) >> s->n) != 0) {
+            set_error("term %zu names a qubit >= n", i);
+            return QS_ERR_ARG;
+        }
+        if (!std::isfinite(t[i].coeff)) {
+            set_error("term %zu has a non-finite coefficient", i);
+            return QS_ERR_ARG;
+        }
+    }
+    return QS_OK;
+}
+
+qs_status qs_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, double *out_re, double *out_im) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!out_re) {
+        set_error("null output");
+        return QS_ERR_ARG;
+    }
+    QS_TRY(check_terms(s, terms, count));
+    QS_TRY(ensure_host_pinned(s, (size_t)2 * s->batch));
+    double *dev = nullptr;
+    QS_TRY(k_expectation(s, terms, count, &dev));
+    QS_TRY(read_back(s, dev, s->host_pinned, 2 * (size_t)s->batch));
+    for (int b = 0; b < s->batch; ++b) {
+        out_re[b] = s->host_pinned[2 * b];
+        if (out_im) out_im[b] = s->host_pinned[2 * b + 1];
+    }
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_trotter_step(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                          size_t n_h1, double s_val, double dt) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    QS_TRY(check_terms(s, h0, n_h0));
+    QS_TRY(check_terms(s, h1, n_h1));
+    if (!std::isfinite(s_val) || !std::isfinite(dt)) {
+        set_error("non-finite s or dt");
+        return QS_ERR_ARG;
+    }
+    return run_trotter(s, h0, n_h0, h1, n_h1, s_val, dt, 0.0, 1);
+    QS_GUARD_END
+}
+
+qs_status qs_adiabatic_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                              size_t n_h1, double T, double dt, int steps) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    QS_TRY(check_terms(s, h0, n_h0));
+    QS_TRY(check_terms(s, h1, n_h1));
+    if (!(T > 0) || !(dt > 0) || !std::isfinite(T) || !std::isfinite(dt)) {
+        set_error("T and dt must be positive and finite");
+        return QS_ERR_ARG;
+    }
+    const long K = std::lround(T / dt);
+    if (K < 1 || K > (1l << 30)) {
+        set_error("T/dt gives %ld steps", K);
+        return QS_ERR_ARG;
+    }
+    const long run = steps < 0 ? K : std::min<long>(K, steps);
+    return run_trotter(s, h0, n_h0, h1, n_h1, -1.0, dt, T, (int)run);
+    QS_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Internal declarations of the qsim CUDA library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qsim.h"
+
+struct qs_state {
+    int n = 0;              // qubits per batch member
+    int batch = 1;          // number of members
+    qs_dtype dtype = QS_C64;
+    void *data = nullptr;   // batch * 2^n amplitudes
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // device scratch for reductions, owned by the handle
+    double *scratch = nullptr;
+    size_t scratch_doubles = 0;
+    // pinned host buffer for read-outs
+    double *host_pinned = nullptr;
+    size_t host_pinned_doubles = 0;
+    // device table of per-member gate matrices (batched parameters)
+    void *gtab = nullptr;
+    size_t gtab_bytes = 0;
+};
+
+namespace qsim {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+void clear_error();
+qs_status cuda_status(cudaError_t e, const char *what);
+
+#define QS_CUDA_TRY(expr)                                                  \
+    do {                                                                   \
+        cudaError_t _e = (expr);                                           \
+        if (_e != cudaSuccess) return ::qsim::cuda_status(_e, #expr);      \
+    } while (0)
+
+#define QS_TRY(expr)                                                       \
+    do {                                                                   \
+        qs_status _s = (expr);                                             \
+        if (_s != QS_OK) return _s;                                        \
+    } while (0)
+
+inline uint64_t qbit(int n, int q) { return 1ull << (n - 1 - q); }
+
+// ------------------------------------------------------------------ gates (host)
+// A gate lowered to index-bit form: targets as bit positions, controls as a
+// bit mask, matrix in double precision (row-major, local index MSB = target 0).
+struct LGate {
+    int k = 0;                 // number of targets
+    int tbit[QS_MAX_TARGETS];  // bit position of target j (= n-1-qubit)
+    uint64_t cmask = 0;        // control bits (index-bit mask)
+    std::vector<cd> m;         // 2^k x 2^k
+    bool diagonal = false;     // m is diagonal
+    bool phase_only = false;   // diagonal with all entries 1 but the last
+    bool is_swap = false;      // the SWAP permutation
+    int param_index = -1;      // batched parameter column, or -1
+    int kind = -1;             // QS_GATE_* of the source gate
+};
+
+// number of targets and parameters of a kind, or -1 if unknown
+int kind_targets(int kind);
+int kind_params(int kind);
+// matrix of a named kind (not UNITARY) with angles p
+std::vector<cd> kind_matrix(int kind, const double *p);
+// validate one gate against n qubits and lower it (qubit -> bit form)
+qs_status lower_gate(int n, const qs_gate &g, LGate *out);
+
+// ------------------------------------------------------------------ kernels (host launchers)
+qs_status k_init_basis(qs_state *s, uint64_t x);
+qs_status k_init_plus(qs_state *s);
+qs_status k_apply_unfused(qs_state *s, const LGate &g);
+qs_status k_probabilities(qs_state *s, double *out_dev);
+// reductions: results land in the state's scratch; *out_dev points at them
+qs_status k_norm2(qs_state *s, double **out_dev);        // batch doubles
+qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count,
+                        double **out_dev);               // 2 * batch doubles (re, im)
+qs_status ensure_scratch(qs_state *s, size_t doubles);
+qs_status ensure_gtab(qs_state *s, size_t bytes);
+// batched-parameter rotation (RX RY RZ U1 CU1) of one gate
+qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params_dev, int n_params);
+qs_status ensure_host_pinned(qs_state *s, size_t doubles);
+
+// Trotter factors
+qs_status k_diagonal_evolution(qs_state *s, const std::vector<double> &coeff,
+                               const std::vector<uint64_t> &zbits, double tau);
+
+}  // namespace qsim

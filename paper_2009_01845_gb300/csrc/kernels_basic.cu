@@ -1,0 +1,727 @@
+// One-gate-per-pass kernels (the plain, unfused simulator) and the read-out
+// reductions.
+//
+//  * dense k-qubit gate (k = 1..5) with controls: Eq. (1), Sec. 2.3-2.4; every
+//    thread owns one index group of 2^k amplitudes whose control bits are 1,
+//    so controlled gates touch only the 2^(n-c) amplitudes they change;
+//  * diagonal gates: only the amplitudes a diagonal changes are touched
+//    (Sec. 2.3: "Z flips the sign of half the components"); a phase gate
+//    (Z, S, T, U1, CZ, CU1, multi-controlled Z) touches 2^(n-c) amplitudes;
+//  * SWAP exchanges the |01> and |10> sub-blocks (QFT, Sec. 3.1);
+//  * probabilities |psi_x|^2 (Sec. 2.4, "Measurements"), squared norm and
+//    Pauli-sum expectation values (Sec. 2.4, Energy callback), all with FP64
+//    accumulation and a fixed reduction order (run-to-run deterministic).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "device.cuh"
+#include "internal.h"
+#include "prof.h"
+
+namespace qsim {
+
+static int sm_count(int device) {
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) return 148;
+    if (!cached[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+            v = 148;
+        cached[device] = v;
+    }
+    return cached[device];
+}
+
+static unsigned grid_for(const qs_state *s, uint64_t work, int threads, int waves = 8) {
+    const uint64_t need = (work + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)sm_count(s->device) * (uint64_t)waves * (2048 / threads);
+    return (unsigned)std::max<uint64_t>(1, std::min(need, cap));
+}
+
+static void fill_insert(InsertBits *ib, uint64_t bits) {
+    ib->count = 0;
+    for (int p = 0; p < 64; ++p)
+        if ((bits >> p) & 1ull) ib->pos[ib->count++] = (int8_t)p;
+}
+
+// ================================================================== init
+template <typename R>
+__global__ void init_basis_kernel(V<R> *psi, int n, int batch, uint64_t x) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < batch) psi[((uint64_t)b << n) + x] = mkc<R>(1, 0);
+}
+
+template <typename R>
+__global__ void fill_kernel(V<R> *psi, uint64_t total, R re) {
+    for (uint64_t i = global_tid(); i < total; i += global_stride()) psi[i] = mkc<R>(re, 0);
+}
+
+static size_t amp_bytes(const qs_state *s) { return s->dtype == QS_C64 ? 8 : 16; }
+
+qs_status k_init_basis(qs_state *s, uint64_t x) {
+    ProfScope _ps(s->stream, KC_INIT);
+    const uint64_t total = (uint64_t)s->batch << s->n;
+    QS_CUDA_TRY(cudaMemsetAsync(s->data, 0, total * amp_bytes(s), s->stream));
+    const int thr = 128, blk = (s->batch + thr - 1) / thr;
+    if (s->dtype == QS_C64)
+        init_basis_kernel<float><<<blk, thr, 0, s->stream>>>((float2 *)s->data, s->n, s->batch, x);
+    else
+        init_basis_kernel<double><<<blk, thr, 0, s->stream>>>((double2 *)s->data, s->n, s->batch, x);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+qs_status k_init_plus(qs_state *s) {
+    ProfScope _ps(s->stream, KC_INIT);
+    const uint64_t total = (uint64_t)s->batch << s->n;
+    const double a = std::pow(2.0, -0.5 * s->n);
+    const unsigned g = grid_for(s, total, 256);
+    if (s->dtype == QS_C64)
+        fill_kernel<float><<<g, 256, 0, s->stream>>>((float2 *)s->data, total, (float)a);
+    else
+        fill_kernel<double><<<g, 256, 0, s->stream>>>((double2 *)s->data, total, a);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+// ================================================================== dense k-qubit gate
+template <typename R, int K> struct DenseP {
+    V<R> m[(1 << K) * (1 << K)];
+    uint64_t off[1 << K];
+    uint64_t setmask;
+    InsertBits ib;
+    int n;
+    int n_free;
+    uint64_t total;
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(256) dense_kernel(V<R> *__restrict__ psi,
+                                                    const __grid_constant__ DenseP<R, K> p) {
+    constexpr int D = 1 << K;
+    const uint64_t fmask = (1ull << p.n_free) - 1ull;
+    for (uint64_t g = global_tid(); g < p.total; g += global_stride()) {
+        const uint64_t b = g >> p.n_free;
+        const uint64_t base = (b << p.n) | expand_bits(g & fmask, p.ib) | p.setmask;
+        V<R> a[D];
+#pragma unroll
+        for (int l = 0; l < D; ++l) a[l] = psi[base | p.off[l]];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            V<R> acc = mkc<R>(0, 0);
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc = cmadd<R>(p.m[r * D + c], a[c], acc);
+            psi[base | p.off[r]] = acc;
+        }
+    }
+}
+
+template <typename R, int K>
+static qs_status launch_dense(qs_state *s, const LGate &g) {
+    ProfScope _ps(s->stream, KC_DENSE);
+    DenseP<R, K> p;
+    constexpr int D = 1 << K;
+    for (int i = 0; i < D * D; ++i) p.m[i] = mkc<R>((R)g.m[i].real(), (R)g.m[i].imag());
+    uint64_t tmask = 0;
+    for (int j = 0; j < K; ++j) tmask |= 1ull << g.tbit[j];
+    for (int l = 0; l < D; ++l) {
+        uint64_t o = 0;
+        for (int j = 0; j < K; ++j)
+            if ((l >> (K - 1 - j)) & 1) o |= 1ull << g.tbit[j];
+        p.off[l] = o;
+    }
+    p.setmask = g.cmask;
+    fill_insert(&p.ib, tmask | g.cmask);
+    p.n = s->n;
+    p.n_free = s->n - p.ib.count;
+    p.total = (uint64_t)s->batch << p.n_free;
+    dense_kernel<R, K><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data, p);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+// ================================================================== diagonal gates
+template <typename R> struct PhaseP {
+    V<R> ph;
+    uint64_t setmask;
+    InsertBits ib;
+    int n;
+    int n_free;
+    uint64_t total;
+};
+
+// psi[x] *= ph for every x whose `setmask` bits are all 1
+template <typename R>
+__global__ void __launch_bounds__(256) phase_kernel(V<R> *__restrict__ psi,
+                                                    const __grid_constant__ PhaseP<R> p) {
+    const uint64_t fmask = (1ull << p.n_free) - 1ull;
+    for (uint64_t g = global_tid(); g < p.total; g += global_stride()) {
+        const uint64_t x = ((g >> p.n_free) << p.n) | expand_bits(g & fmask, p.ib) | p.setmask;
+        psi[x] = cmul<R>(psi[x], p.ph);
+    }
+}
+
+template <typename R, int K> struct DiagP {
+    V<R> d[1 << K];
+    int tbit[K];
+    uint64_t setmask;
+    InsertBits ib;
+    int n;
+    int n_free;
+    uint64_t total;
+};
+
+// psi[x] *= d[local(x)] for every x whose control bits are all 1
+template <typename R, int K>
+__global__ void __launch_bounds__(256) diag_kernel(V<R> *__restrict__ psi,
+                                                   const __grid_constant__ DiagP<R, K> p) {
+    const uint64_t fmask = (1ull << p.n_free) - 1ull;
+    for (uint64_t g = global_tid(); g < p.total; g += global_stride()) {
+        const uint64_t x = ((g >> p.n_free) << p.n) | expand_bits(g & fmask, p.ib) | p.setmask;
+        int l = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) l |= (int)((x >> p.tbit[j]) & 1ull) << (K - 1 - j);
+        psi[x] = cmul<R>(psi[x], p.d[l]);
+    }
+}
+
+template <typename R>
+static qs_status launch_phase(qs_state *s, uint64_t setmask, std::complex<double> ph) {
+    ProfScope _ps(s->stream, KC_PHASE);
+    PhaseP<R> p;
+    p.ph = mkc<R>((R)ph.real(), (R)ph.imag());
+    p.setmask = setmask;
+    fill_insert(&p.ib, setmask);
+    p.n = s->n;
+    p.n_free = s->n - p.ib.count;
+    p.total = (uint64_t)s->batch << p.n_free;
+    phase_kernel<R><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data, p);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+template <typename R, int K>
+static qs_status launch_diag(qs_state *s, const LGate &g) {
+    ProfScope _ps(s->stream, KC_DIAG);
+    DiagP<R, K> p;
+    constexpr int D = 1 << K;
+    for (int l = 0; l < D; ++l) p.d[l] = mkc<R>((R)g.m[l * D + l].real(), (R)g.m[l * D + l].imag());
+    for (int j = 0; j < K; ++j) p.tbit[j] = g.tbit[j];
+    p.setmask = g.cmask;
+    fill_insert(&p.ib, g.cmask);
+    p.n = s->n;
+    p.n_free = s->n - p.ib.count;
+    p.total = (uint64_t)s->batch << p.n_free;
+    diag_kernel<R, K><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data, p);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+// ================================================================== SWAP
+struct SwapP {
+    uint64_t A, B, setmask;
+    InsertBits ib;
+    int n;
+    int n_free;
+    uint64_t total;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) swap_kernel(V<R> *__restrict__ psi,
+                                                   const __grid_constant__ SwapP p) {
+    const uint64_t fmask = (1ull << p.n_free) - 1ull;
+    for (uint64_t g = global_tid(); g < p.total; g += global_stride()) {
+        const uint64_t x = ((g >> p.n_free) << p.n) | expand_bits(g & fmask, p.ib) | p.setmask;
+        const V<R> a = psi[x | p.A];
+        const V<R> b = psi[x | p.B];
+        psi[x | p.A] = b;
+        psi[x | p.B] = a;
+    }
+}
+
+template <typename R>
+static qs_status launch_swap(qs_state *s, const LGate &g) {
+    ProfScope _ps(s->stream, KC_SWAP);
+    SwapP p;
+    p.A = 1ull << g.tbit[0];
+    p.B = 1ull << g.tbit[1];
+    p.setmask = g.cmask;
+    fill_insert(&p.ib, p.A | p.B | g.cmask);
+    p.n = s->n;
+    p.n_free = s->n - p.ib.count;
+    p.total = (uint64_t)s->batch << p.n_free;
+    swap_kernel<R><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data, p);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+template <typename R>
+static qs_status apply_unfused_t(qs_state *s, const LGate &g) {
+    const int K = 1 << g.k;
+    if (g.is_swap) return launch_swap<R>(s, g);
+    if (g.phase_only) {
+        uint64_t setmask = g.cmask;
+        for (int j = 0; j < g.k; ++j) setmask |= 1ull << g.tbit[j];
+        const std::complex<double> ph = g.m[(K - 1) * K + (K - 1)];
+        if (ph == std::complex<double>(1.0, 0.0)) return QS_OK;  // identity
+        return launch_phase<R>(s, setmask, ph);
+    }
+    if (g.diagonal) {
+        switch (g.k) {
+        case 1: return launch_diag<R, 1>(s, g);
+        case 2: return launch_diag<R, 2>(s, g);
+        case 3: return launch_diag<R, 3>(s, g);
+        case 4: return launch_diag<R, 4>(s, g);
+        case 5: return launch_diag<R, 5>(s, g);
+        }
+    }
+    switch (g.k) {
+    case 1: return launch_dense<R, 1>(s, g);
+    case 2: return launch_dense<R, 2>(s, g);
+    case 3: return launch_dense<R, 3>(s, g);
+    case 4: return launch_dense<R, 4>(s, g);
+    case 5: return launch_dense<R, 5>(s, g);
+    }
+    set_error("gate with %d targets", g.k);
+    return QS_ERR_ARG;
+}
+
+qs_status k_apply_unfused(qs_state *s, const LGate &g) {
+    return s->dtype == QS_C64 ? apply_unfused_t<float>(s, g) : apply_unfused_t<double>(s, g);
+}
+
+// ================================================================== reductions
+qs_status ensure_scratch(qs_state *s, size_t doubles) {
+    if (s->scratch_doubles >= doubles) return QS_OK;
+    if (s->scratch) {
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        cudaFree(s->scratch);
+        s->scratch = nullptr;
+        s->scratch_doubles = 0;
+    }
+    QS_CUDA_TRY(cudaMalloc(&s->scratch, doubles * sizeof(double)));
+    s->scratch_doubles = doubles;
+    return QS_OK;
+}
+
+qs_status ensure_host_pinned(qs_state *s, size_t doubles) {
+    if (s->host_pinned_doubles >= doubles) return QS_OK;
+    if (s->host_pinned) {
+        cudaFreeHost(s->host_pinned);
+        s->host_pinned = nullptr;
+        s->host_pinned_doubles = 0;
+    }
+    QS_CUDA_TRY(cudaMallocHost(&s->host_pinned, doubles * sizeof(double)));
+    s->host_pinned_doubles = doubles;
+    return QS_OK;
+}
+
+template <typename R>
+__global__ void probs_kernel(const V<R> *__restrict__ psi, double *__restrict__ out, uint64_t total) {
+    for (uint64_t i = global_tid(); i < total; i += global_stride()) {
+        const V<R> a = psi[i];
+        const double re = (double)a.x, im = (double)a.y;
+        out[i] = re * re + im * im;
+    }
+}
+
+qs_status k_probabilities(qs_state *s, double *out_dev) {
+    ProfScope _ps(s->stream, KC_REDUCE);
+    const uint64_t total = (uint64_t)s->batch << s->n;
+    const unsigned g = grid_for(s, total, 256);
+    if (s->dtype == QS_C64)
+        probs_kernel<float><<<g, 256, 0, s->stream>>>((const float2 *)s->data, out_dev, total);
+    else
+        probs_kernel<double><<<g, 256, 0, s->stream>>>((const double2 *)s->data, out_dev, total);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+// Block-wide sum of two doubles; result valid in thread 0.
+__device__ __forceinline__ double2 block_sum2(double a, double b) {
+    __shared__ double2 sh[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = make_double2(a, b);
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        r = lane < nw ? sh[lane] : make_double2(0.0, 0.0);
+        for (int o = 16; o > 0; o >>= 1) {
+            r.x += __shfl_down_sync(0xffffffffu, r.x, o);
+            r.y += __shfl_down_sync(0xffffffffu, r.y, o);
+        }
+    }
+    __syncthreads();
+    return r;
+}
+
+constexpr int kRedThreads = 256;
+
+static int red_blocks_per_member(const qs_state *s) {
+    const uint64_t per = 1ull << s->n;
+    const uint64_t want = std::max<uint64_t>(1, per / (kRedThreads * 16));
+    const uint64_t cap = std::max<uint64_t>(1, (uint64_t)sm_count(s->device) * 8 / s->batch);
+    return (int)std::min<uint64_t>(std::min<uint64_t>(want, cap), 4096);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) norm2_partial_kernel(const V<R> *__restrict__ psi, int n,
+                                                                    double2 *__restrict__ part) {
+    const uint64_t per = 1ull << n;
+    const V<R> *p = psi + (uint64_t)blockIdx.y * per;
+    double acc = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const V<R> a = p[i];
+        acc += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+    }
+    const double2 r = block_sum2(acc, 0.0);
+    if (threadIdx.x == 0) part[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = r;
+}
+
+// out[b] = sum of the member's partials (x and y parts), in a fixed order
+__global__ void finalize_kernel(const double2 *__restrict__ part, int per_member, double *__restrict__ out,
+                                int two) {
+    const int b = blockIdx.x;
+    double x = 0.0, y = 0.0;
+    for (int i = threadIdx.x; i < per_member; i += blockDim.x) {
+        x += part[(uint64_t)b * per_member + i].x;
+        y += part[(uint64_t)b * per_member + i].y;
+    }
+    const double2 r = block_sum2(x, y);
+    if (threadIdx.x == 0) {
+        if (two) {
+            out[2 * b] = r.x;
+            out[2 * b + 1] = r.y;
+        } else {
+            out[b] = r.x;
+        }
+    }
+}
+
+qs_status k_norm2(qs_state *s, double **out) {
+    const int P = red_blocks_per_member(s);
+    QS_TRY(ensure_scratch(s, (size_t)2 * P * s->batch + 2 * (size_t)s->batch));
+    double *out_dev = s->scratch + (size_t)2 * P * s->batch;
+    *out = out_dev;
+    ProfScope _ps(s->stream, KC_REDUCE);
+    dim3 grid(P, s->batch);
+    if (s->dtype == QS_C64)
+        norm2_partial_kernel<float><<<grid, kRedThreads, 0, s->stream>>>((const float2 *)s->data, s->n,
+                                                                          (double2 *)s->scratch);
+    else
+        norm2_partial_kernel<double><<<grid, kRedThreads, 0, s->stream>>>((const double2 *)s->data, s->n,
+                                                                           (double2 *)s->scratch);
+    QS_CUDA_TRY(cudaGetLastError());
+    finalize_kernel<<<s->batch, kRedThreads, 0, s->stream>>>((const double2 *)s->scratch, P, out_dev, 0);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------ Pauli expectation
+// Terms sharing one X mask m form f_m(x) = sum_t c_t i^{#Y_t} (-1)^{popcount(x & z_t)},
+// and <psi|H|psi> = sum_m sum_x conj(psi[x ^ m]) f_m(x) psi[x].
+constexpr int kMaxTermsPerLaunch = 256;
+
+struct ExpP {
+    double cre[kMaxTermsPerLaunch];
+    double cim[kMaxTermsPerLaunch];
+    uint64_t zb[kMaxTermsPerLaunch];
+    int nt;
+    uint64_t xb;      // X mask in index bits (0 for the diagonal group)
+    int n;
+    int n_free;       // n (diagonal group) or n - 1 (pairs)
+    int hb;           // highest bit of xb (pairs)
+    int accumulate;   // add to the partials instead of overwriting
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> *__restrict__ psi,
+                                                                     const __grid_constant__ ExpP p,
+                                                                     double2 *__restrict__ part) {
+    const uint64_t per = 1ull << p.n;
+    const V<R> *q = psi + (uint64_t)blockIdx.y * per;
+    const uint64_t cnt = 1ull << p.n_free;
+    double ar = 0.0, ai = 0.0;
+    if (p.xb == 0) {
+        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < cnt;
+             x += (uint64_t)gridDim.x * blockDim.x) {
+            R f = 0;
+            for (int t = 0; t < p.nt; ++t) {
+                const R c = (R)p.cre[t];
+                f += (__popcll(x & p.zb[t]) & 1) ? -c : c;
+            }
+            const V<R> a = q[x];
+            ar += (double)f * ((double)a.x * (double)a.x + (double)a.y * (double)a.y);
+        }
+    } else {
+        const uint64_t lo = (1ull << p.hb) - 1ull;
+        for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt;
+             j += (uint64_t)gridDim.x * blockDim.x) {
+            const uint64_t x = ((j >> p.hb) << (p.hb + 1)) | (j & lo);
+            const uint64_t y = x ^ p.xb;
+            R fxr = 0, fxi = 0, fyr = 0, fyi = 0;
+            for (int t = 0; t < p.nt; ++t) {
+                const R cr = (R)p.cre[t], ci = (R)p.cim[t];
+                const bool sx = __popcll(x & p.zb[t]) & 1, sy = __popcll(y & p.zb[t]) & 1;
+                fxr += sx ? -cr : cr;
+                fxi += sx ? -ci : ci;
+                fyr += sy ? -cr : cr;
+                fyi += sy ? -ci : ci;
+            }
+            const V<R> a = q[x], b = q[y];
+            // conj(b) * a * f(x) + conj(a) * b * f(y)
+            const double abr = (double)b.x * a.x + (double)b.y * a.y;   // Re(conj(b) a)
+            const double abi = (double)b.x * a.y - (double)b.y * a.x;   // Im(conj(b) a)
+            ar += abr * fxr - abi * fxi;
+            ai += abr * fxi + abi * fxr;
+            // conj(a) b = conj(conj(b) a)
+            ar += abr * fyr + abi * fyi;
+            ai += abr * fyi - abi * fyr;
+        }
+    }
+    const double2 r = block_sum2(ar, ai);
+    if (threadIdx.x == 0) {
+        double2 *slot = &part[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x];
+        if (p.accumulate) {
+            double2 v = *slot;
+            v.x += r.x;
+            v.y += r.y;
+            *slot = v;
+        } else {
+            *slot = r;
+        }
+    }
+}
+
+qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, double **out) {
+    const int n = s->n;
+    const int P = red_blocks_per_member(s);
+    QS_TRY(ensure_scratch(s, (size_t)2 * P * s->batch + 2 * (size_t)s->batch));
+    double *out_dev = s->scratch + (size_t)2 * P * s->batch;
+    *out = out_dev;
+    // group the terms by X mask (in index bits), keeping first-seen order
+    std::vector<uint64_t> masks;
+    std::vector<std::vector<size_t>> groups;
+    for (size_t t = 0; t < count; ++t) {
+        uint64_t xb = 0;
+        for (int q = 0; q < n; ++q)
+            if ((terms[t].x_mask >> q) & 1ull) xb |= qbit(n, q);
+        size_t gi = 0;
+        while (gi < masks.size() && masks[gi] != xb) ++gi;
+        if (gi == masks.size()) {
+            masks.push_back(xb);
+            groups.emplace_back();
+        }
+        groups[gi].push_back(t);
+    }
+    bool first = true;
+    ProfScope _ps(s->stream, KC_REDUCE);
+    dim3 grid(P, s->batch);
+    for (size_t gi = 0; gi < masks.size(); ++gi) {
+        const auto &idx = groups[gi];
+        for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxTermsPerLaunch) {
+            ExpP p;
+            std::memset(&p, 0, sizeof(p));
+            p.nt = (int)std::min<size_t>(kMaxTermsPerLaunch, idx.size() - c0);
+            for (int j = 0; j < p.nt; ++j) {
+                const qs_pauli_term &t = terms[idx[c0 + j]];
+                int ny = __builtin_popcountll(t.x_mask & t.z_mask) & 3;
+                // c * i^ny
+                const double c = t.coeff;
+                const double re[4] = {c, 0.0, -c, 0.0}, im[4] = {0.0, c, 0.0, -c};
+                p.cre[j] = re[ny];
+                p.cim[j] = im[ny];
+                uint64_t zb = 0;
+                for (int q = 0; q < n; ++q)
+                    if ((t.z_mask >> q) & 1ull) zb |= qbit(n, q);
+                p.zb[j] = zb;
+            }
+            p.xb = masks[gi];
+            p.n = n;
+            p.hb = p.xb ? 63 - __builtin_clzll(p.xb) : 0;
+            p.n_free = p.xb ? n - 1 : n;
+            p.accumulate = first ? 0 : 1;
+            first = false;
+            if (s->dtype == QS_C64)
+                expect_partial_kernel<float><<<grid, kRedThreads, 0, s->stream>>>(
+                    (const float2 *)s->data, p, (double2 *)s->scratch);
+            else
+                expect_partial_kernel<double><<<grid, kRedThreads, 0, s->stream>>>(
+                    (const double2 *)s->data, p, (double2 *)s->scratch);
+            QS_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    if (first) {  // no terms: the zero operator
+        QS_CUDA_TRY(cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * s->batch, s->stream));
+        return QS_OK;
+    }
+    finalize_kernel<<<s->batch, kRedThreads, 0, s->stream>>>((const double2 *)s->scratch, P, out_dev, 1);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+// ================================================================== diagonal evolution
+// psi[x] *= exp(-i tau E(x)), E(x) = sum_t c_t (-1)^{popcount(x & z_t)}: the exact
+// exponential of a Z-string Hamiltonian (one factor of the Trotter step, Sec. 2.6).
+// The angle tau E(x) is evaluated in FP64.
+struct DiagEvoP {
+    double c[kMaxTermsPerLaunch];
+    uint64_t zb[kMaxTermsPerLaunch];
+    int nt;
+    int n;
+    double tau;
+    uint64_t total;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) diag_evo_kernel(V<R> *__restrict__ psi,
+                                                       const __grid_constant__ DiagEvoP p) {
+    const uint64_t mask = (1ull << p.n) - 1ull;
+    for (uint64_t i = global_tid(); i < p.total; i += global_stride()) {
+        const uint64_t x = i & mask;
+        double e = 0.0;
+        for (int t = 0; t < p.nt; ++t) e += (__popcll(x & p.zb[t]) & 1) ? -p.c[t] : p.c[t];
+        double sn, cs;
+        sincos(-p.tau * e, &sn, &cs);
+        psi[i] = cmul<R>(psi[i], mkc<R>((R)cs, (R)sn));
+    }
+}
+
+qs_status k_diagonal_evolution(qs_state *s, const std::vector<double> &coeff,
+                               const std::vector<uint64_t> &zbits, double tau) {
+    ProfScope _ps(s->stream, KC_TROTTER_DIAG);
+    for (size_t c0 = 0; c0 < coeff.size(); c0 += kMaxTermsPerLaunch) {
+        DiagEvoP p;
+        std::memset(&p, 0, sizeof(p));
+        p.nt = (int)std::min<size_t>(kMaxTermsPerLaunch, coeff.size() - c0);
+        for (int j = 0; j < p.nt; ++j) {
+            p.c[j] = coeff[c0 + j];
+            p.zb[j] = zbits[c0 + j];
+        }
+        p.n = s->n;
+        p.tau = tau;
+        p.total = (uint64_t)s->batch << s->n;
+        const unsigned g = grid_for(s, p.total, 256);
+        if (s->dtype == QS_C64)
+            diag_evo_kernel<float><<<g, 256, 0, s->stream>>>((float2 *)s->data, p);
+        else
+            diag_evo_kernel<double><<<g, 256, 0, s->stream>>>((double2 *)s->data, p);
+        QS_CUDA_TRY(cudaGetLastError());
+    }
+    return QS_OK;
+}
+
+}  // namespace qsim
+
+namespace qsim {
+
+// ================================================================== batched-parameter rotations
+// A gate whose angle comes from a device table params[b * n_params + p] (one
+// row per batch member). The member's 2x2 matrix (or CU1 phase) is built once
+// per member in FP64 by param_matrix_kernel, then applied by dense/phase passes
+// that pick the member's entry.
+qs_status ensure_gtab(qs_state *s, size_t bytes) {
+    if (s->gtab_bytes >= bytes) return QS_OK;
+    if (s->gtab) {
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        cudaFree(s->gtab);
+        s->gtab = nullptr;
+        s->gtab_bytes = 0;
+    }
+    QS_CUDA_TRY(cudaMalloc(&s->gtab, bytes));
+    s->gtab_bytes = bytes;
+    return QS_OK;
+}
+
+template <typename R>
+__global__ void param_matrix_kernel(const double *__restrict__ params, int n_params, int pidx, int kind,
+                                    int batch, V<R> *__restrict__ mats) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const double th = params[(uint64_t)b * n_params + pidx];
+    double s, c;
+    sincos(0.5 * th, &s, &c);
+    V<R> *m = mats + 4 * (uint64_t)b;
+    switch (kind) {
+    case QS_GATE_RX:  // [[c, -is], [-is, c]]
+        m[0] = mkc<R>(c, 0); m[1] = mkc<R>(0, -s); m[2] = mkc<R>(0, -s); m[3] = mkc<R>(c, 0);
+        break;
+    case QS_GATE_RY:  // [[c, -s], [s, c]]
+        m[0] = mkc<R>(c, 0); m[1] = mkc<R>(-s, 0); m[2] = mkc<R>(s, 0); m[3] = mkc<R>(c, 0);
+        break;
+    case QS_GATE_RZ:  // diag(e^{-i th/2}, e^{i th/2})
+        m[0] = mkc<R>(c, -s); m[1] = mkc<R>(0, 0); m[2] = mkc<R>(0, 0); m[3] = mkc<R>(c, s);
+        break;
+    default: {        // U1 / CU1: phase e^{i th} on the all-ones block
+        double s2, c2;
+        sincos(th, &s2, &c2);
+        m[0] = mkc<R>(1, 0); m[1] = mkc<R>(0, 0); m[2] = mkc<R>(0, 0); m[3] = mkc<R>(c2, s2);
+    }
+    }
+}
+
+struct PDenseP {
+    uint64_t off1;     // target bit
+    uint64_t setmask;  // control bits (and, for phase gates, target bits)
+    InsertBits ib;
+    int n;
+    int n_free;
+    int phase_only;
+    uint64_t total;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) pdense_kernel(V<R> *__restrict__ psi, const V<R> *__restrict__ mats,
+                                                     const __grid_constant__ PDenseP p) {
+    const uint64_t fmask = (1ull << p.n_free) - 1ull;
+    for (uint64_t g = global_tid(); g < p.total; g += global_stride()) {
+        const uint64_t b = g >> p.n_free;
+        const uint64_t x = (b << p.n) | expand_bits(g & fmask, p.ib) | p.setmask;
+        const V<R> *m = mats + 4 * b;
+        if (p.phase_only) {
+            psi[x] = cmul<R>(psi[x], m[3]);
+        } else {
+            const V<R> a0 = psi[x], a1 = psi[x | p.off1];
+            psi[x] = cmadd<R>(m[1], a1, cmul<R>(m[0], a0));
+            psi[x | p.off1] = cmadd<R>(m[3], a1, cmul<R>(m[2], a0));
+        }
+    }
+}
+
+template <typename R>
+static qs_status apply_param_t(qs_state *s, const LGate &g, const double *params, int n_params) {
+    ProfScope _ps(s->stream, KC_PARAM);
+    QS_TRY(ensure_gtab(s, sizeof(V<R>) * 4 * (size_t)s->batch));
+    param_matrix_kernel<R><<<(s->batch + 127) / 128, 128, 0, s->stream>>>(params, n_params, g.param_index,
+                                                                          g.kind, s->batch, (V<R> *)s->gtab);
+    QS_CUDA_TRY(cudaGetLastError());
+    PDenseP p;
+    const bool phase = (g.kind == QS_GATE_U1 || g.kind == QS_GATE_CU1);
+    uint64_t tmask = 0;
+    for (int j = 0; j < g.k; ++j) tmask |= 1ull << g.tbit[j];
+    p.off1 = 1ull << g.tbit[0];
+    p.phase_only = phase ? 1 : 0;
+    p.setmask = g.cmask | (phase ? tmask : 0);
+    fill_insert(&p.ib, tmask | g.cmask);
+    p.n = s->n;
+    p.n_free = s->n - p.ib.count;
+    p.total = (uint64_t)s->batch << p.n_free;
+    pdense_kernel<R><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data,
+                                                                       (const V<R> *)s->gtab, p);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params, int n_params) {
+    return s->dtype == QS_C64 ? apply_param_t<float>(s, g, params, n_params)
+                              : apply_param_t<double>(s, g, params, n_params);
+}
+
+}  // namespace qsim

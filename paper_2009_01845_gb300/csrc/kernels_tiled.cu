@@ -1,0 +1,290 @@
+// Tiled multi-gate pass kernel (see tiled.h for the data layout).
+//
+// One CTA (256 threads) processes tiles of 2^k amplitudes in a grid-stride
+// loop. Per tile: load from HBM straight into registers (lane = the 5 lowest
+// index bits, so every warp-wide load is 32 consecutive amplitudes), run the
+// pass's stages (register/shuffle gate application, shared-memory transposes
+// between stages), and store back once. HBM traffic per pass: one read and one
+// write of the state, whatever the number of gates.
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.h"
+#include "prof.h"
+#include "tiled.h"
+
+namespace qsim {
+
+template <typename R> __device__ __forceinline__ V<R> shfl_xor_c(V<R> v, int m) {
+    V<R> o;
+    o.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+    o.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+    return o;
+}
+
+// 2x2 gate on register bit J for every register pair whose required register
+// bits (mr) are set.
+template <typename R, int RB, int J>
+__device__ __forceinline__ void dense1_reg(V<R> *a, V<R> m00, V<R> m01, V<R> m10, V<R> m11, uint32_t mr) {
+#pragma unroll
+    for (int r = 0; r < (1 << RB); ++r) {
+        if (r & (1 << J)) continue;
+        if ((r & mr) != mr) continue;
+        const V<R> x = a[r], y = a[r | (1 << J)];
+        a[r] = cmadd<R>(m01, y, cmul<R>(m00, x));
+        a[r | (1 << J)] = cmadd<R>(m11, y, cmul<R>(m10, x));
+    }
+}
+
+// 4x4 gate on register bits (A = local MSB, B), A != B
+template <typename R, int RB, int A, int B>
+__device__ __forceinline__ void dense2_reg(V<R> *a, const V<R> *m, uint32_t mr) {
+#pragma unroll
+    for (int r = 0; r < (1 << RB); ++r) {
+        if (r & ((1 << A) | (1 << B))) continue;
+        if ((r & mr) != mr) continue;
+        const int i[4] = {r, r | (1 << B), r | (1 << A), r | (1 << A) | (1 << B)};
+        V<R> x[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = a[i[c]];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            V<R> acc = cmul<R>(m[o * 4], x[0]);
+#pragma unroll
+            for (int c = 1; c < 4; ++c) acc = cmadd<R>(m[o * 4 + c], x[c], acc);
+            a[i[o]] = acc;
+        }
+    }
+}
+
+template <typename R, int RB, int A, int B>
+__device__ __forceinline__ void swap_reg(V<R> *a, uint32_t mr) {
+#pragma unroll
+    for (int r = 0; r < (1 << RB); ++r) {
+        if (!(r & (1 << A)) || (r & (1 << B))) continue;
+        if ((r & mr) != mr) continue;
+        const int q = r ^ (1 << A) ^ (1 << B);
+        const V<R> t = a[r];
+        a[r] = a[q];
+        a[q] = t;
+    }
+}
+
+template <typename R, int RB>
+__device__ __forceinline__ void dispatch_dense1(V<R> *a, int j, V<R> m00, V<R> m01, V<R> m10, V<R> m11,
+                                                uint32_t mr) {
+    switch (j) {
+    case 0: dense1_reg<R, RB, 0>(a, m00, m01, m10, m11, mr); break;
+    case 1: dense1_reg<R, RB, 1>(a, m00, m01, m10, m11, mr); break;
+    case 2: dense1_reg<R, RB, 2>(a, m00, m01, m10, m11, mr); break;
+    case 3: dense1_reg<R, RB, 3>(a, m00, m01, m10, m11, mr); break;
+    default:
+        if constexpr (RB > 4) dense1_reg<R, RB, 4>(a, m00, m01, m10, m11, mr);
+        break;
+    }
+}
+
+#define QS_PAIR_CASES(FN, ...)                                                  \
+    switch (A * 8 + B) {                                                        \
+    case 0 * 8 + 1: FN<R, RB, 0, 1>(__VA_ARGS__); break;                        \
+    case 0 * 8 + 2: FN<R, RB, 0, 2>(__VA_ARGS__); break;                        \
+    case 0 * 8 + 3: FN<R, RB, 0, 3>(__VA_ARGS__); break;                        \
+    case 1 * 8 + 2: FN<R, RB, 1, 2>(__VA_ARGS__); break;                        \
+    case 1 * 8 + 3: FN<R, RB, 1, 3>(__VA_ARGS__); break;                        \
+    case 2 * 8 + 3: FN<R, RB, 2, 3>(__VA_ARGS__); break;                        \
+    default:                                                                    \
+        if constexpr (RB > 4) {                                                 \
+            switch (A * 8 + B) {                                                \
+            case 0 * 8 + 4: FN<R, RB, 0, 4>(__VA_ARGS__); break;                \
+            case 1 * 8 + 4: FN<R, RB, 1, 4>(__VA_ARGS__); break;                \
+            case 2 * 8 + 4: FN<R, RB, 2, 4>(__VA_ARGS__); break;                \
+            case 3 * 8 + 4: FN<R, RB, 3, 4>(__VA_ARGS__); break;                \
+            default: break;                                                     \
+            }                                                                   \
+        }                                                                       \
+    }
+
+template <typename R, int RB>
+__device__ __forceinline__ void dispatch_dense2(V<R> *a, int A, int B, const V<R> *m, uint32_t mr) {
+    QS_PAIR_CASES(dense2_reg, a, m, mr)
+}
+
+template <typename R, int RB>
+__device__ __forceinline__ void dispatch_swap(V<R> *a, int A, int B, uint32_t mr) {
+    QS_PAIR_CASES(swap_reg, a, mr)
+}
+
+template <int RB>
+__device__ __forceinline__ uint64_t reg_offset(int r, const uint64_t *g) {
+    uint64_t o = 0;
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+        if ((r >> j) & 1) o |= g[j];
+    return o;
+}
+
+template <int RB>
+__device__ __forceinline__ uint32_t reg_local(int r, const uint32_t *l) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+        if ((r >> j) & 1) o |= l[j];
+    return o;
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
+    tiled_kernel(V<R> *__restrict__ psi, const __grid_constant__ TileParams<R> p) {
+    constexpr int NR = 1 << RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V<R> *sm = reinterpret_cast<V<R> *>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint64_t fmask = (1ull << p.n_free) - 1ull;
+    V<R> a[NR];
+
+    for (uint64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+        const uint64_t tbase = ((t >> p.n_free) << p.n) | expand_bits(t & fmask, p.tins);
+        // ---------------- load (stage 0 mapping)
+        {
+            const TileStage &s0 = p.st[0];
+            uint64_t gt = tbase | (uint64_t)lane;
+#pragma unroll
+            for (int w = 0; w < kTileWarpBits; ++w)
+                if ((warp >> w) & 1) gt |= 1ull << p.gbit[s0.wloc[w]];
+            uint64_t gr[RB];
+#pragma unroll
+            for (int j = 0; j < RB; ++j) gr[j] = 1ull << p.gbit[s0.rloc[j]];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) a[r] = psi[gt | reg_offset<RB>(r, gr)];
+        }
+        // ---------------- stages
+        for (int s = 0; s < p.n_stages; ++s) {
+            const TileStage &st = p.st[s];
+            if (s > 0) {
+                const TileStage &pv = p.st[s - 1];
+                uint32_t lt = (uint32_t)lane, lr[RB];
+#pragma unroll
+                for (int w = 0; w < kTileWarpBits; ++w)
+                    if ((warp >> w) & 1) lt |= 1u << pv.wloc[w];
+#pragma unroll
+                for (int j = 0; j < RB; ++j) lr[j] = 1u << pv.rloc[j];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) sm[lt | reg_local<RB>(r, lr)] = a[r];
+                __syncthreads();
+                lt = (uint32_t)lane;
+#pragma unroll
+                for (int w = 0; w < kTileWarpBits; ++w)
+                    if ((warp >> w) & 1) lt |= 1u << st.wloc[w];
+#pragma unroll
+                for (int j = 0; j < RB; ++j) lr[j] = 1u << st.rloc[j];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) a[r] = sm[lt | reg_local<RB>(r, lr)];
+                __syncthreads();
+            }
+            uint32_t lt = (uint32_t)lane;
+#pragma unroll
+            for (int w = 0; w < kTileWarpBits; ++w)
+                if ((warp >> w) & 1) lt |= 1u << st.wloc[w];
+            for (int o = st.op_begin; o < st.op_end; ++o) {
+                const TileOp &op = p.op[o];
+                const bool ok = ((tbase & op.mo) == op.mo) && ((lt & op.mt) == op.mt);
+                const uint32_t mr = op.mr;
+                switch (op.type) {
+                case TOP_DENSE1_L: {
+                    // every lane takes part in the shuffles; only `ok` lanes update
+                    const int bit = (lane >> op.a) & 1;
+                    const V<R> cs = bit ? p.mat[op.m + 3] : p.mat[op.m + 0];
+                    const V<R> co = bit ? p.mat[op.m + 2] : p.mat[op.m + 1];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const V<R> v = shfl_xor_c<R>(a[r], 1 << op.a);
+                        if (ok && (r & mr) == mr) a[r] = cmadd<R>(co, v, cmul<R>(cs, a[r]));
+                    }
+                    break;
+                }
+                case TOP_DENSE1_R:
+                    if (ok)
+                        dispatch_dense1<R, RB>(a, op.a, p.mat[op.m], p.mat[op.m + 1], p.mat[op.m + 2],
+                                               p.mat[op.m + 3], mr);
+                    break;
+                case TOP_PHASE:
+                    if (ok) {
+                        const V<R> ph = p.mat[op.m];
+#pragma unroll
+                        for (int r = 0; r < NR; ++r)
+                            if ((r & mr) == mr) a[r] = cmul<R>(a[r], ph);
+                    }
+                    break;
+                case TOP_DIAG1:
+                    if (ok) {
+                        const V<R> d0 = p.mat[op.m], d1 = p.mat[op.m + 1];
+                        if (op.tkind == TB_REG) {
+#pragma unroll
+                            for (int r = 0; r < NR; ++r)
+                                if ((r & mr) == mr) a[r] = cmul<R>(a[r], ((r >> op.a) & 1) ? d1 : d0);
+                        } else {
+                            const bool bit = op.tkind == TB_THREAD ? ((lt & (uint32_t)op.tmask) != 0)
+                                                                   : ((tbase & op.tmask) != 0);
+                            const V<R> d = bit ? d1 : d0;
+#pragma unroll
+                            for (int r = 0; r < NR; ++r)
+                                if ((r & mr) == mr) a[r] = cmul<R>(a[r], d);
+                        }
+                    }
+                    break;
+                case TOP_DENSE2_RR:
+                    if (ok) dispatch_dense2<R, RB>(a, op.a, op.b, &p.mat[op.m], mr);
+                    break;
+                case TOP_SWAP_RR:
+                    if (ok) dispatch_swap<R, RB>(a, op.a, op.b, mr);
+                    break;
+                default:
+                    break;
+                }
+            }
+        }
+        // ---------------- store (last stage mapping)
+        {
+            const TileStage &sl = p.st[p.n_stages - 1];
+            uint64_t gt = tbase | (uint64_t)lane;
+#pragma unroll
+            for (int w = 0; w < kTileWarpBits; ++w)
+                if ((warp >> w) & 1) gt |= 1ull << p.gbit[sl.wloc[w]];
+            uint64_t gr[RB];
+#pragma unroll
+            for (int j = 0; j < RB; ++j) gr[j] = 1ull << p.gbit[sl.rloc[j]];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) psi[gt | reg_offset<RB>(r, gr)] = a[r];
+        }
+    }
+}
+
+template <typename R>
+static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p) {
+    constexpr int RB = TileCfg<R>::RB;
+    const size_t smem = sizeof(V<R>) << p.k;
+    static int configured[64] = {0};
+    const int dev = (s->device >= 0 && s->device < 64) ? s->device : 0;
+    static int blocks_per_sm[64] = {0};
+    if (!configured[dev]) {
+        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        int bps = 0;
+        QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB>, kTileThreads, smem));
+        int sms = 0;
+        QS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        blocks_per_sm[dev] = std::max(1, bps) * sms;
+        configured[dev] = 1;
+    }
+    const uint64_t grid = std::min<uint64_t>(p.total_tiles, (uint64_t)blocks_per_sm[dev]);
+    ProfScope _ps(s->stream, KC_TILED);
+    tiled_kernel<R, RB><<<(unsigned)grid, kTileThreads, smem, s->stream>>>((V<R> *)s->data, p);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) { return launch_tiled_t<float>(s, p); }
+qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) { return launch_tiled_t<double>(s, p); }
+
+}  // namespace qsim

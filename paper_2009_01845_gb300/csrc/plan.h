@@ -1,0 +1,26 @@
+// Execution planning: turns a lowered gate queue into kernel passes.
+#pragma once
+
+#include "internal.h"
+
+namespace qsim {
+
+// Apply a lowered gate queue with the requested strategy. params_dev/n_params
+// drive gates with param_index >= 0 (batched parameters), else nullptr/0.
+qs_status run_gates(qs_state *s, std::vector<LGate> &gates, int mode, const qs_opts *opts,
+                    const double *params_dev, int n_params);
+
+// Trotter evolution (Sec. 2.6). With steps == 1 and s_fixed >= 0: one step at
+// s = s_fixed. With s_fixed < 0: `steps` steps of the linear schedule over
+// total time T, step k at s = (k + 1/2) dt / T, adjacent half diagonals merged.
+qs_status run_trotter(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                      size_t n_h1, double s_fixed, double dt, double T, int steps);
+
+// Tiled multi-gate passes (falls back to one pass per gate for gates a tile
+// cannot express and for states smaller than a tile).
+qs_status run_tiled(qs_state *s, const std::vector<LGate> &gates, const double *params_dev, int n_params);
+
+// Free anything cached per state.
+void plan_cache_release(qs_state *s);
+
+}  // namespace qsim

@@ -1,0 +1,41 @@
+// Launch accounting: when enabled, every kernel launch of the library is
+// bracketed by CUDA events on its stream, per kernel class.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace qsim {
+
+enum KClass {
+    KC_INIT = 0,
+    KC_DENSE,
+    KC_PHASE,
+    KC_DIAG,
+    KC_SWAP,
+    KC_PARAM,
+    KC_TILED,
+    KC_FUSED_TC,
+    KC_REDUCE,
+    KC_TROTTER_DIAG,
+    KC_ADJOINT,
+    KC_COUNT
+};
+
+bool prof_enabled();
+// record the start/end of one launch of class c on stream st
+void prof_begin(cudaStream_t st, int c);
+void prof_end(cudaStream_t st, int c);
+
+struct ProfScope {
+    cudaStream_t st;
+    int c;
+    bool on;
+    ProfScope(cudaStream_t s, int cls) : st(s), c(cls), on(prof_enabled()) {
+        if (on) prof_begin(st, c);
+    }
+    ~ProfScope() {
+        if (on) prof_end(st, c);
+    }
+};
+
+}  // namespace qsim

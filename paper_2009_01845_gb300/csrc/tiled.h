@@ -1,0 +1,91 @@
+// Tiled multi-gate pass: the pass description shared by the planner and the
+// kernel.
+//
+// A pass loads tiles of 2^k amplitudes whose indices vary over k chosen index
+// bits (the "tile bits": always the 5 lowest bits, for coalescing, plus k-5
+// others) with every other bit fixed per tile, applies a run of gates to the
+// tile while it is on chip, and writes it back once: one HBM round trip for
+// many gates (the grouping of local gates of Sec. 2.5, done per tile).
+//
+// Inside a CTA of 256 threads (8 warps) each thread holds 2^RB amplitudes in
+// registers. The tile's k = RB + 8 local bits are split, per stage, into
+//   L: local bits 0..4  -> lane index (fixed in every stage; coalesced),
+//   R: RB local bits    -> register index,
+//   W: 3 local bits     -> warp index.
+// Gates whose dense targets lie in R are applied in registers, targets in L
+// through warp shuffles; a new stage re-splits R/W through a shared-memory
+// transpose. Diagonal gates may act on any bits, inside or outside the tile.
+#pragma once
+
+#include <cstdint>
+
+#include "device.cuh"
+
+namespace qsim {
+
+constexpr int kTileThreads = 256;
+constexpr int kTileLaneBits = 5;
+constexpr int kTileWarpBits = 3;
+constexpr int kTileMaxStages = 48;
+constexpr int kTileMaxOps = 288;
+constexpr int kTileMaxMat = 640;   // complex entries in the matrix pool
+
+// register bits per thread for each precision (c64: 32 amplitudes, c128: 16)
+template <typename R> struct TileCfg;
+// kMinBlocks: resident CTAs per SM the register budget is sized for
+template <> struct TileCfg<float> { static constexpr int RB = 5, kMinBlocks = 2; };
+template <> struct TileCfg<double> { static constexpr int RB = 4, kMinBlocks = 1; };
+inline int tile_reg_bits(qs_dtype dt) { return dt == QS_C64 ? 5 : 4; }
+inline int tile_bits(qs_dtype dt) { return tile_reg_bits(dt) + kTileLaneBits + kTileWarpBits; }
+
+enum TileOpType : uint8_t {
+    TOP_PHASE = 0,   // multiply by mat[m] where all required bits are 1
+    TOP_DIAG1,       // multiply by mat[m + bit] (bit = the target's value), if required bits are 1
+    TOP_DENSE1_R,    // 2x2 on register bit a
+    TOP_DENSE1_L,    // 2x2 on lane bit a (warp shuffles)
+    TOP_DENSE2_RR,   // 4x4 on register bits (a = local MSB, b), a < b
+    TOP_SWAP_RR,     // swap register bits a < b
+};
+
+// Where a DIAG1 target bit lives in the current stage.
+enum TileBitKind : uint8_t { TB_REG = 0, TB_THREAD = 1, TB_OUTSIDE = 2 };
+
+// Every op may carry required bits (controls, or the bits of a phase gate),
+// split by where they live in the op's stage:
+//   mr: register-index bits, mt: thread-local (lane/warp) local-index bits,
+//   mo: global index bits outside the tile.
+struct TileOp {
+    uint8_t type;
+    uint8_t a, b;
+    uint8_t tkind;    // TOP_DIAG1: TileBitKind of the target
+    uint8_t mr;
+    uint8_t pad0[3];
+    uint32_t mt;
+    uint32_t m;       // first matrix-pool entry
+    uint64_t mo;
+    uint64_t tmask;   // TOP_DIAG1 target: thread-local mask (TB_THREAD) or global mask (TB_OUTSIDE)
+};
+
+struct TileStage {
+    uint8_t rloc[5];  // local bit of register bit j
+    uint8_t wloc[3];  // local bit of warp bit w
+    uint16_t op_begin, op_end;
+    uint32_t pad;
+};
+
+template <typename R> struct TileParams {
+    int n;            // qubits per member
+    int k;            // tile bits
+    int n_stages;
+    int n_free;       // n - k
+    uint64_t total_tiles;
+    InsertBits tins;  // sorted global positions of the tile bits
+    uint8_t gbit[16]; // global bit of local bit i
+    TileStage st[kTileMaxStages];
+    TileOp op[kTileMaxOps];
+    V<R> mat[kTileMaxMat];
+};
+
+static_assert(sizeof(TileParams<double>) <= 32000, "kernel parameter block too large");
+
+}  // namespace qsim

@@ -1,0 +1,313 @@
+"""Thin ctypes binding over the qsim C-ABI (``include/qsim.h``).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library ``libqsim_gb300.so``. PyTorch provides device memory (the state is a
+torch tensor wrapped by the library, which never frees it) and the stream the
+calls are ordered on. There is no CPU fallback: if the library is missing or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Iterable, Sequence
+
+import numpy as np
+
+from . import build as _build
+from .inputs import Gate
+
+_lock = threading.Lock()
+_lib = None
+
+KIND = {"H": 0, "X": 1, "Y": 2, "Z": 3, "S": 4, "SDG": 5, "T": 6, "TDG": 7, "RX": 8, "RY": 9,
+        "RZ": 10, "U1": 11, "U2": 12, "U3": 13, "CZ": 14, "CU1": 15, "SWAP": 16, "UNITARY": 17}
+MODE = {"auto": 0, "unfused": 1, "tiled": 2, "fused": 3}
+DTYPE = {"c64": 0, "c128": 1}
+STATUS = {0: "QS_OK", 1: "QS_ERR_ARG", 2: "QS_ERR_OOM", 3: "QS_ERR_CUDA", 4: "QS_ERR_UNSUPPORTED",
+          5: "QS_ERR_TIMEOUT"}
+
+
+class QsimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CGate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_targets", ctypes.c_int32),
+                ("targets", ctypes.c_int32 * 5), ("param_index", ctypes.c_int32),
+                ("control_mask", ctypes.c_uint64), ("params", ctypes.c_double * 3),
+                ("matrix", ctypes.c_void_p)]
+
+
+class CTerm(ctypes.Structure):
+    _fields_ = [("coeff", ctypes.c_double), ("x_mask", ctypes.c_uint64), ("z_mask", ctypes.c_uint64)]
+
+
+class COpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
+                ("fuse_qubits", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+# (name, argtypes) of every exported entry point; restype is qs_status unless noted
+P = ctypes.c_void_p
+_SIGS = {
+    "qs_last_error": ([], ctypes.c_char_p),
+    "qs_version": ([], ctypes.c_char_p),
+    "qs_state_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, P], None),
+    "qs_state_wrap": ([ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, P, P], None),
+    "qs_state_destroy": ([P], None),
+    "qs_state_data": ([P, P], None),
+    "qs_state_set_stream": ([P, P], None),
+    "qs_state_init_basis": ([P, ctypes.c_uint64], None),
+    "qs_state_init_plus": ([P], None),
+    "qs_state_set": ([P, P, ctypes.c_int], None),
+    "qs_state_get": ([P, P, ctypes.c_int], None),
+    "qs_apply_gates": ([P, P, ctypes.c_size_t, P], None),
+    "qs_apply_gates_batched": ([P, P, ctypes.c_size_t, P, ctypes.c_int, P], None),
+    "qs_probabilities": ([P, P, ctypes.c_int], None),
+    "qs_norm2": ([P, P], None),
+    "qs_expectation": ([P, P, ctypes.c_size_t, P, P], None),
+    "qs_trotter_step": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double,
+                         ctypes.c_double], None),
+    "qs_adiabatic_evolve": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_int], None),
+    "qs_profile_enable": ([ctypes.c_int], None),
+    "qs_profile_collect": ([P, P, ctypes.c_int], None),
+    "qs_profile_class_name": ([ctypes.c_int], ctypes.c_char_p),
+    "qs_profile_class_count": ([], ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Open libqsim_gb300.so; raise if it is not built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                if build_if_missing:
+                    _build.build()
+                else:
+                    raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res if res is not None else ctypes.c_int32
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise QsimError(status, load().qs_last_error().decode())
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ marshalling
+def marshal_gates(gates: Sequence[Gate], param_index: Sequence[int] | None = None):
+    """qs_gate array for a gate list; returns (array, keep-alive list)."""
+    arr = (CGate * max(1, len(gates)))()
+    keep = []
+    for i, g in enumerate(gates):
+        c = arr[i]
+        if g.kind not in KIND:
+            raise QsimError(1, f"gate {i}: unknown kind {g.kind!r}")
+        if not 1 <= len(g.targets) <= 5:
+            raise QsimError(1, f"gate {i}: {len(g.targets)} targets (1..5 supported)")
+        c.kind = KIND[g.kind]
+        c.n_targets = len(g.targets)
+        for j, q in enumerate(g.targets):
+            c.targets[j] = int(q)
+        mask = 0
+        for q in g.controls:
+            if not 0 <= int(q) < 64:
+                raise QsimError(1, f"gate {i}: control qubit {q} out of range")
+            mask |= 1 << int(q)
+        c.control_mask = mask
+        for j, v in enumerate(g.params[:3]):
+            c.params[j] = float(v)
+        c.param_index = -1 if param_index is None else int(param_index[i])
+        if g.matrix is not None:
+            m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128))
+            keep.append(m)
+            c.matrix = m.ctypes.data
+        else:
+            c.matrix = None
+    return arr, keep
+
+
+def marshal_terms(terms: Iterable):
+    terms = list(terms)
+    arr = (CTerm * max(1, len(terms)))()
+    for i, (c, xm, zm) in enumerate(terms):
+        arr[i].coeff = float(c)
+        arr[i].x_mask = int(xm)
+        arr[i].z_mask = int(zm)
+    return arr, len(terms)
+
+
+def opts(mode: str = "auto", tile_qubits: int = 0, fuse_qubits: int = 0) -> COpts:
+    return COpts(MODE[mode], int(tile_qubits), int(fuse_qubits), 0)
+
+
+# ------------------------------------------------------------------ state
+class State:
+    """A batch of n-qubit states in a torch CUDA tensor, wrapped by the library.
+
+    ``tensor`` (optional) must be a contiguous complex64/complex128 CUDA tensor
+    of batch * 2^n elements; otherwise one is allocated with torch.
+    """
+
+    def __init__(self, n: int, batch: int = 1, dtype: str = "c64", tensor=None, stream=None):
+        import torch
+        self.lib = load()
+        self.n, self.batch, self.dtype = int(n), int(batch), dtype
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        if tensor is None:
+            tensor = torch.empty(self.batch << self.n, dtype=tdt, device="cuda")
+        if tensor.dtype != tdt or not tensor.is_cuda or not tensor.is_contiguous() or \
+                tensor.numel() != (self.batch << self.n):
+            raise ValueError("state tensor must be a contiguous CUDA tensor of batch*2^n "
+                             f"{tdt} elements")
+        self.tensor = tensor
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(self.lib.qs_state_wrap(self.n, self.batch, DTYPE[dtype], ctypes.c_void_p(tensor.data_ptr()),
+                                      ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.qs_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(self.lib.qs_state_set_stream(self.handle, ctypes.c_void_p(_stream_handle(stream))))
+
+    # -- initialisation
+    def init_basis(self, x: int = 0):
+        _check(self.lib.qs_state_init_basis(self.handle, int(x)))
+        return self
+
+    def init_plus(self):
+        _check(self.lib.qs_state_init_plus(self.handle))
+        return self
+
+    def set(self, values):
+        """Copy amplitudes in from a numpy array (host) or a CUDA tensor (device)."""
+        import torch
+        if isinstance(values, torch.Tensor) and values.is_cuda:
+            src = values.contiguous()
+            _check(self.lib.qs_state_set(self.handle, ctypes.c_void_p(src.data_ptr()), 1))
+        else:
+            npdt = np.complex64 if self.dtype == "c64" else np.complex128
+            a = np.ascontiguousarray(np.asarray(values, dtype=npdt).reshape(-1))
+            if a.size != (self.batch << self.n):
+                raise ValueError("wrong number of amplitudes")
+            _check(self.lib.qs_state_set(self.handle, ctypes.c_void_p(a.ctypes.data), 0))
+        return self
+
+    def get(self) -> np.ndarray:
+        npdt = np.complex64 if self.dtype == "c64" else np.complex128
+        out = np.empty(self.batch << self.n, dtype=npdt)
+        _check(self.lib.qs_state_get(self.handle, ctypes.c_void_p(out.ctypes.data), 0))
+        return out.reshape(self.batch, 1 << self.n) if self.batch > 1 else out
+
+    # -- gates
+    def apply(self, gates: Sequence[Gate], mode: str = "auto", tile_qubits: int = 0,
+              fuse_qubits: int = 0):
+        arr, keep = marshal_gates(gates)
+        o = opts(mode, tile_qubits, fuse_qubits)
+        _check(self.lib.qs_apply_gates(self.handle, arr, len(gates), ctypes.byref(o)))
+        del keep
+        return self
+
+    def apply_batched(self, gates: Sequence[Gate], param_index: Sequence[int], params, mode: str = "auto"):
+        """``params``: CUDA float64 tensor (batch, n_params); gate i takes its angle
+        from column param_index[i] when that is >= 0."""
+        import torch
+        if not (isinstance(params, torch.Tensor) and params.is_cuda and params.dtype == torch.float64):
+            raise ValueError("params must be a CUDA float64 tensor")
+        params = params.contiguous()
+        if params.dim() != 2 or params.shape[0] != self.batch:
+            raise ValueError("params must have shape (batch, n_params)")
+        arr, keep = marshal_gates(gates, param_index)
+        o = opts(mode)
+        _check(self.lib.qs_apply_gates_batched(self.handle, arr, len(gates),
+                                               ctypes.c_void_p(params.data_ptr()),
+                                               int(params.shape[1]), ctypes.byref(o)))
+        del keep
+        return self
+
+    # -- read-out
+    def probabilities(self, on_device: bool = False):
+        if on_device:
+            import torch
+            out = torch.empty(self.batch << self.n, dtype=torch.float64, device=self.tensor.device)
+            _check(self.lib.qs_probabilities(self.handle, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        out = np.empty(self.batch << self.n, dtype=np.float64)
+        _check(self.lib.qs_probabilities(self.handle, ctypes.c_void_p(out.ctypes.data), 0))
+        return out.reshape(self.batch, 1 << self.n) if self.batch > 1 else out
+
+    def norm2(self) -> np.ndarray:
+        out = np.empty(self.batch, dtype=np.float64)
+        _check(self.lib.qs_norm2(self.handle, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def expectation(self, terms) -> np.ndarray:
+        arr, cnt = marshal_terms(terms)
+        re = np.empty(self.batch, dtype=np.float64)
+        im = np.empty(self.batch, dtype=np.float64)
+        _check(self.lib.qs_expectation(self.handle, arr, cnt, ctypes.c_void_p(re.ctypes.data),
+                                       ctypes.c_void_p(im.ctypes.data)))
+        return re + 1j * im
+
+    # -- Trotter (Sec. 2.6)
+    def trotter_step(self, h0, h1, s: float, dt: float):
+        a0, n0 = marshal_terms(h0)
+        a1, n1 = marshal_terms(h1)
+        _check(self.lib.qs_trotter_step(self.handle, a0, n0, a1, n1, float(s), float(dt)))
+        return self
+
+    def adiabatic_evolve(self, h0, h1, T: float, dt: float, steps: int = -1):
+        a0, n0 = marshal_terms(h0)
+        a1, n1 = marshal_terms(h1)
+        _check(self.lib.qs_adiabatic_evolve(self.handle, a0, n0, a1, n1, float(T), float(dt), int(steps)))
+        return self
+
+
+# ------------------------------------------------------------------ launch accounting
+def profile_enable(on: bool = True):
+    _check(load().qs_profile_enable(1 if on else 0))
+
+
+def profile_collect() -> dict:
+    """{class name: (total ms, launches)} since the last collect; resets."""
+    lib = load()
+    nc = lib.qs_profile_class_count()
+    ms = (ctypes.c_double * nc)()
+    cnt = (ctypes.c_longlong * nc)()
+    _check(lib.qs_profile_collect(ms, cnt, nc))
+    return {lib.qs_profile_class_name(c).decode(): (ms[c], cnt[c]) for c in range(nc)}
