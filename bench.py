@@ -121,6 +121,47 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# GB300: 152 SMs x 128 FP32 lanes x 2 flops per FMA per clock; FP64 ~1.2 TFLOP/s
+# (FP64 FMA microbenchmark on this pool: 1.19 TFLOP/s).
+SMS, FP32_LANES = 152, 128
+FP64_TFLOPS = 1.19
+
+
+def alu_peak_tflops(dtype: str, sm_mhz: float) -> float:
+    if dtype == "c64":
+        return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    return FP64_TFLOPS
+
+
+def roofline(name, rec, a, clk):
+    """Roofline of one kernel class: whichever of HBM time (algorithmic bytes /
+    measured copy bandwidth) and ALU time (algorithmic flops / peak of the
+    state's arithmetic type) is larger bounds it."""
+    tot_ms, launches, nbytes, nflops = rec
+    if not launches or tot_ms <= 0:
+        return None
+    bw, bw_src = measured_peaks()
+    sm = clk.get("sm_mhz") or 2070.0
+    alu = alu_peak_tflops(a.dtype, sm)
+    t = tot_ms / 1000.0
+    gbs = nbytes / t / 1e9
+    tfl = nflops / t / 1e12
+    f_hbm, f_alu = gbs / bw, tfl / alu
+    base = {"kernel": name, "launches_per_step": launches / a.steps, "avg_launch_ms": tot_ms / launches,
+            "bytes_per_launch": nbytes / launches, "flops_per_launch": nflops / launches,
+            "hbm": {"achieved": gbs, "peak": bw, "unit": "GB/s", "frac": f_hbm,
+                    "peak_source": f"{bw_src} (MEASURED_PEAKS hbm_gbs)"},
+            "alu": {"achieved": tfl, "peak": alu, "unit": "TFLOP/s", "frac": f_alu,
+                    "peak_source": ("FP32: 152 SMs x 128 lanes x 2 x median SM clock" if a.dtype == "c64"
+                                    else "FP64 FMA microbenchmark on GB300")},
+            "traffic": None}
+    if nbytes / (bw * 1e9) >= nflops / (alu * 1e12):
+        base.update({"bound": "hbm", "achieved": gbs, "peak": bw, "unit": "GB/s", "frac": f_hbm})
+    else:
+        base.update({"bound": "alu", "achieved": tfl, "peak": alu, "unit": "TFLOP/s", "frac": f_alu})
+    return base
+
+
 # ------------------------------------------------------------------ CPU oracle
 def oracle_sample(a, budget_s: float = 15.0):
     """Time the oracle (plain C complex128, one thread) on a bounded sample of
@@ -238,21 +279,10 @@ def run_ours(a):
         ms = float(t.item())
     value = world * len(gates) / (ms / 1000.0)
 
-    # roofline of the dominant kernel class (algorithmic bytes: one read and one
-    # write of the state per dense or tiled pass)
-    b = 8 if a.dtype == "c64" else 16
-    B = 2 * (1 << n) * b
+    # roofline of the dominant kernel class: algorithmic bytes and flops tallied
+    # by the library per launch, over the CUDA-event time of those launches
     dom = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (tot_ms, launches) = dom
-    per_launch_bytes = {"dense": B, "tiled": B, "fused_tc": B}.get(name)
-    peak, peak_kind = measured_peaks()
-    roof = None
-    if per_launch_bytes and launches:
-        ach = per_launch_bytes * launches / (tot_ms / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
-                "launches_per_step": launches / a.steps,
-                "avg_launch_ms": tot_ms / launches}
+    roof = roofline(dom[0], dom[1], a, clk)
     launches_total = int(sum(v[1] for v in prof.values()))
 
     # end to end through the public Python API with host inputs: marshal the
@@ -288,7 +318,8 @@ def run_ours(a):
                 "parallelism": "replicas" if world > 1 else "single",
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_total,
-                "kernels": {k: {"ms_per_step": v[0] / a.steps, "launches_per_step": v[1] / a.steps}
+                "kernels": {k: {"ms_per_step": v[0] / a.steps, "launches_per_step": v[1] / a.steps,
+                                "GB_per_step": v[2] / a.steps / 1e9, "GFLOP_per_step": v[3] / a.steps / 1e9}
                             for k, v in prof.items() if v[1]},
                 "energy_zz": float(out_re[0]), "norm2": float(out_n[0])}
         print(json.dumps(line), flush=True)

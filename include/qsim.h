@@ -200,9 +200,11 @@ qs_status qs_adiabatic_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
    by kernel class (dense, phase, diag, swap, param, tiled, fused_tc, reduce,
    trotter_diag, adjoint, init). Process-wide. */
 qs_status qs_profile_enable(int on);
-/* Wait for the recorded launches, write per-class total milliseconds and launch
-   counts into arrays of n_classes entries, and reset the record. */
-qs_status qs_profile_collect(double *total_ms, long long *launches, int n_classes);
+/* Wait for the recorded launches, write per-class total milliseconds, launch
+   counts, algorithmic bytes (the HBM reads + writes each operation needs) and
+   algorithmic flops into arrays of n_classes entries, and reset the record. */
+qs_status qs_profile_collect(double *total_ms, long long *launches, double *bytes, double *flops,
+                             int n_classes);
 /* Name of kernel class c ("" if out of range) and the number of classes. */
 const char *qs_profile_class_name(int c);
 int qs_profile_class_count(void);

@@ -59,9 +59,14 @@ __global__ void fill_kernel(V<R> *psi, uint64_t total, R re) {
 
 static size_t amp_bytes(const qs_state *s) { return s->dtype == QS_C64 ? 8 : 16; }
 
+// algorithmic work of a launch over `touched` amplitudes, each read and written once
+static void tally(int cls, const qs_state *s, double touched, double flops_per_amp) {
+    if (prof_enabled()) prof_add_work(cls, 2.0 * touched * (double)amp_bytes(s), touched * flops_per_amp);
+}
+
 qs_status k_init_basis(qs_state *s, uint64_t x) {
-    ProfScope _ps(s->stream, KC_INIT);
     const uint64_t total = (uint64_t)s->batch << s->n;
+    ProfScope _ps(s->stream, KC_INIT, (double)total * amp_bytes(s));
     QS_CUDA_TRY(cudaMemsetAsync(s->data, 0, total * amp_bytes(s), s->stream));
     const int thr = 128, blk = (s->batch + thr - 1) / thr;
     if (s->dtype == QS_C64)
@@ -73,8 +78,8 @@ qs_status k_init_basis(qs_state *s, uint64_t x) {
 }
 
 qs_status k_init_plus(qs_state *s) {
-    ProfScope _ps(s->stream, KC_INIT);
     const uint64_t total = (uint64_t)s->batch << s->n;
+    ProfScope _ps(s->stream, KC_INIT, (double)total * amp_bytes(s));
     const double a = std::pow(2.0, -0.5 * s->n);
     const unsigned g = grid_for(s, total, 256);
     if (s->dtype == QS_C64)
@@ -136,6 +141,7 @@ static qs_status launch_dense(qs_state *s, const LGate &g) {
     p.n = s->n;
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
+    tally(KC_DENSE, s, (double)p.total * D, 8.0 * D);
     dense_kernel<R, K><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
@@ -196,6 +202,7 @@ static qs_status launch_phase(qs_state *s, uint64_t setmask, std::complex<double
     p.n = s->n;
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
+    tally(KC_PHASE, s, (double)p.total, 6.0);
     phase_kernel<R><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
@@ -213,6 +220,7 @@ static qs_status launch_diag(qs_state *s, const LGate &g) {
     p.n = s->n;
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
+    tally(KC_DIAG, s, (double)p.total, 6.0);
     diag_kernel<R, K><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
@@ -251,6 +259,7 @@ static qs_status launch_swap(qs_state *s, const LGate &g) {
     p.n = s->n;
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
+    tally(KC_SWAP, s, 2.0 * (double)p.total, 0.0);
     swap_kernel<R><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
@@ -327,8 +336,8 @@ __global__ void probs_kernel(const V<R> *__restrict__ psi, double *__restrict__ 
 }
 
 qs_status k_probabilities(qs_state *s, double *out_dev) {
-    ProfScope _ps(s->stream, KC_REDUCE);
     const uint64_t total = (uint64_t)s->batch << s->n;
+    ProfScope _ps(s->stream, KC_REDUCE, (double)total * (amp_bytes(s) + 8), 3.0 * total);
     const unsigned g = grid_for(s, total, 256);
     if (s->dtype == QS_C64)
         probs_kernel<float><<<g, 256, 0, s->stream>>>((const float2 *)s->data, out_dev, total);
@@ -370,16 +379,28 @@ static int red_blocks_per_member(const qs_state *s) {
     return (int)std::min<uint64_t>(std::min<uint64_t>(want, cap), 4096);
 }
 
+// Each thread sums runs of kChunk amplitudes in the state's precision and adds
+// every run to an FP64 accumulator: FP64 carries the reduction across the
+// state, while the per-amplitude arithmetic stays on the FP32 pipes for
+// complex64 (GB300's FP64 rate is about 1/60 of its FP32 rate).
+constexpr int kChunk = 16;
+
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) norm2_partial_kernel(const V<R> *__restrict__ psi, int n,
                                                                     double2 *__restrict__ part) {
     const uint64_t per = 1ull << n;
     const V<R> *p = psi + (uint64_t)blockIdx.y * per;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     double acc = 0.0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const V<R> a = p[i];
-        acc += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    while (i < per) {
+        R run = 0;
+#pragma unroll 4
+        for (int c = 0; c < kChunk && i < per; ++c, i += stride) {
+            const V<R> a = p[i];
+            run = fma(a.x, a.x, fma(a.y, a.y, run));
+        }
+        acc += (double)run;
     }
     const double2 r = block_sum2(acc, 0.0);
     if (threadIdx.x == 0) part[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = r;
@@ -410,7 +431,8 @@ qs_status k_norm2(qs_state *s, double **out) {
     QS_TRY(ensure_scratch(s, (size_t)2 * P * s->batch + 2 * (size_t)s->batch));
     double *out_dev = s->scratch + (size_t)2 * P * s->batch;
     *out = out_dev;
-    ProfScope _ps(s->stream, KC_REDUCE);
+    ProfScope _ps(s->stream, KC_REDUCE, (double)((uint64_t)s->batch << s->n) * amp_bytes(s),
+                  4.0 * (double)((uint64_t)s->batch << s->n));
     dim3 grid(P, s->batch);
     if (s->dtype == QS_C64)
         norm2_partial_kernel<float><<<grid, kRedThreads, 0, s->stream>>>((const float2 *)s->data, s->n,
@@ -429,10 +451,13 @@ qs_status k_norm2(qs_state *s, double **out) {
 // and <psi|H|psi> = sum_m sum_x conj(psi[x ^ m]) f_m(x) psi[x].
 constexpr int kMaxTermsPerLaunch = 256;
 
-struct ExpP {
-    double cre[kMaxTermsPerLaunch];
-    double cim[kMaxTermsPerLaunch];
+template <typename R> struct ExpP {
+    R cre[kMaxTermsPerLaunch];
+    R cim[kMaxTermsPerLaunch];
     uint64_t zb[kMaxTermsPerLaunch];
+    int8_t za[kMaxTermsPerLaunch];   // first Z bit, or -1
+    int8_t zc[kMaxTermsPerLaunch];   // second Z bit, or -1
+    int8_t zn[kMaxTermsPerLaunch];   // number of Z bits: 0, 1, 2 or 3 (= more)
     int nt;
     uint64_t xb;      // X mask in index bits (0 for the diagonal group)
     int n;
@@ -441,49 +466,63 @@ struct ExpP {
     int accumulate;   // add to the partials instead of overwriting
 };
 
+// (-1)^{popcount(x & z_t)}, with shift-and-xor for one- and two-bit masks
+template <typename R>
+__device__ __forceinline__ bool term_odd(const ExpP<R> &p, int t, uint64_t x) {
+    switch (p.zn[t]) {
+    case 0: return false;
+    case 1: return (x >> p.za[t]) & 1ull;
+    case 2: return ((x >> p.za[t]) ^ (x >> p.zc[t])) & 1ull;
+    default: return __popcll(x & p.zb[t]) & 1;
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> *__restrict__ psi,
-                                                                     const __grid_constant__ ExpP p,
+                                                                     const __grid_constant__ ExpP<R> p,
                                                                      double2 *__restrict__ part) {
     const uint64_t per = 1ull << p.n;
     const V<R> *q = psi + (uint64_t)blockIdx.y * per;
     const uint64_t cnt = 1ull << p.n_free;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     double ar = 0.0, ai = 0.0;
+    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p.xb == 0) {
-        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < cnt;
-             x += (uint64_t)gridDim.x * blockDim.x) {
-            R f = 0;
-            for (int t = 0; t < p.nt; ++t) {
-                const R c = (R)p.cre[t];
-                f += (__popcll(x & p.zb[t]) & 1) ? -c : c;
+        while (j < cnt) {
+            R run = 0;
+            for (int c = 0; c < kChunk && j < cnt; ++c, j += stride) {
+                R f = 0;
+                for (int t = 0; t < p.nt; ++t) f += term_odd(p, t, j) ? -p.cre[t] : p.cre[t];
+                const V<R> a = q[j];
+                run = fma(f, fma(a.x, a.x, a.y * a.y), run);
             }
-            const V<R> a = q[x];
-            ar += (double)f * ((double)a.x * (double)a.x + (double)a.y * (double)a.y);
+            ar += (double)run;
         }
     } else {
         const uint64_t lo = (1ull << p.hb) - 1ull;
-        for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt;
-             j += (uint64_t)gridDim.x * blockDim.x) {
-            const uint64_t x = ((j >> p.hb) << (p.hb + 1)) | (j & lo);
-            const uint64_t y = x ^ p.xb;
-            R fxr = 0, fxi = 0, fyr = 0, fyi = 0;
-            for (int t = 0; t < p.nt; ++t) {
-                const R cr = (R)p.cre[t], ci = (R)p.cim[t];
-                const bool sx = __popcll(x & p.zb[t]) & 1, sy = __popcll(y & p.zb[t]) & 1;
-                fxr += sx ? -cr : cr;
-                fxi += sx ? -ci : ci;
-                fyr += sy ? -cr : cr;
-                fyi += sy ? -ci : ci;
+        while (j < cnt) {
+            R rr = 0, ri = 0;
+            for (int c = 0; c < kChunk && j < cnt; ++c, j += stride) {
+                const uint64_t x = ((j >> p.hb) << (p.hb + 1)) | (j & lo);
+                const uint64_t y = x ^ p.xb;
+                R fxr = 0, fxi = 0, fyr = 0, fyi = 0;
+                for (int t = 0; t < p.nt; ++t) {
+                    const R cr = p.cre[t], ci = p.cim[t];
+                    const bool sx = term_odd(p, t, x), sy = term_odd(p, t, y);
+                    fxr += sx ? -cr : cr;
+                    fxi += sx ? -ci : ci;
+                    fyr += sy ? -cr : cr;
+                    fyi += sy ? -ci : ci;
+                }
+                const V<R> a = q[x], b = q[y];
+                // conj(b) a f(x) + conj(a) b f(y), with conj(a) b = conj(conj(b) a)
+                const R abr = b.x * a.x + b.y * a.y;
+                const R abi = b.x * a.y - b.y * a.x;
+                rr += abr * (fxr + fyr) - abi * (fxi - fyi);
+                ri += abr * (fxi + fyi) + abi * (fxr - fyr);
             }
-            const V<R> a = q[x], b = q[y];
-            // conj(b) * a * f(x) + conj(a) * b * f(y)
-            const double abr = (double)b.x * a.x + (double)b.y * a.y;   // Re(conj(b) a)
-            const double abi = (double)b.x * a.y - (double)b.y * a.x;   // Im(conj(b) a)
-            ar += abr * fxr - abi * fxi;
-            ai += abr * fxi + abi * fxr;
-            // conj(a) b = conj(conj(b) a)
-            ar += abr * fyr + abi * fyi;
-            ai += abr * fyi - abi * fyr;
+            ar += (double)rr;
+            ai += (double)ri;
         }
     }
     const double2 r = block_sum2(ar, ai);
@@ -527,7 +566,7 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
     for (size_t gi = 0; gi < masks.size(); ++gi) {
         const auto &idx = groups[gi];
         for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxTermsPerLaunch) {
-            ExpP p;
+            ExpP<double> p;
             std::memset(&p, 0, sizeof(p));
             p.nt = (int)std::min<size_t>(kMaxTermsPerLaunch, idx.size() - c0);
             for (int j = 0; j < p.nt; ++j) {
@@ -542,6 +581,10 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
                 for (int q = 0; q < n; ++q)
                     if ((t.z_mask >> q) & 1ull) zb |= qbit(n, q);
                 p.zb[j] = zb;
+                const int nz = __builtin_popcountll(zb);
+                p.zn[j] = (int8_t)std::min(nz, 3);
+                p.za[j] = (int8_t)(nz ? __builtin_ctzll(zb) : -1);
+                p.zc[j] = (int8_t)(nz >= 2 ? 63 - __builtin_clzll(zb) : -1);
             }
             p.xb = masks[gi];
             p.n = n;
@@ -549,12 +592,31 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
             p.n_free = p.xb ? n - 1 : n;
             p.accumulate = first ? 0 : 1;
             first = false;
-            if (s->dtype == QS_C64)
+            if (prof_enabled())
+                prof_add_work(KC_REDUCE, (double)((uint64_t)s->batch << n) * amp_bytes(s),
+                              (double)((uint64_t)s->batch << n) * (2.0 * p.nt + 6.0));
+            if (s->dtype == QS_C64) {
+                ExpP<float> pf;
+                std::memcpy(&pf.zb, &p.zb, sizeof(p.zb));
+                std::memcpy(&pf.za, &p.za, sizeof(p.za));
+                std::memcpy(&pf.zc, &p.zc, sizeof(p.zc));
+                std::memcpy(&pf.zn, &p.zn, sizeof(p.zn));
+                for (int j = 0; j < kMaxTermsPerLaunch; ++j) {
+                    pf.cre[j] = (float)p.cre[j];
+                    pf.cim[j] = (float)p.cim[j];
+                }
+                pf.nt = p.nt;
+                pf.xb = p.xb;
+                pf.n = p.n;
+                pf.n_free = p.n_free;
+                pf.hb = p.hb;
+                pf.accumulate = p.accumulate;
                 expect_partial_kernel<float><<<grid, kRedThreads, 0, s->stream>>>(
-                    (const float2 *)s->data, p, (double2 *)s->scratch);
-            else
+                    (const float2 *)s->data, pf, (double2 *)s->scratch);
+            } else {
                 expect_partial_kernel<double><<<grid, kRedThreads, 0, s->stream>>>(
                     (const double2 *)s->data, p, (double2 *)s->scratch);
+            }
             QS_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -608,6 +670,7 @@ qs_status k_diagonal_evolution(qs_state *s, const std::vector<double> &coeff,
         p.n = s->n;
         p.tau = tau;
         p.total = (uint64_t)s->batch << s->n;
+        tally(KC_TROTTER_DIAG, s, (double)p.total, 2.0 * p.nt + 26.0);
         const unsigned g = grid_for(s, p.total, 256);
         if (s->dtype == QS_C64)
             diag_evo_kernel<float><<<g, 256, 0, s->stream>>>((float2 *)s->data, p);
@@ -713,6 +776,7 @@ static qs_status apply_param_t(qs_state *s, const LGate &g, const double *params
     p.n = s->n;
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
+    tally(KC_PARAM, s, (double)p.total * (phase ? 1 : 2), phase ? 6.0 : 16.0);
     pdense_kernel<R><<<grid_for(s, p.total, 256), 256, 0, s->stream>>>((V<R> *)s->data,
                                                                        (const V<R> *)s->gtab, p);
     QS_CUDA_TRY(cudaGetLastError());

@@ -16,6 +16,7 @@
 #include <limits>
 
 #include "plan.h"
+#include "prof.h"
 #include "tiled.h"
 
 namespace qsim {
@@ -258,6 +259,31 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     P.n_stages = nst;
     *consumed = taken;
     if (taken == 0) return QS_OK;
+    if (prof_enabled()) {
+        // algorithmic flops: per touched amplitude 16 for a 2x2 complex gate,
+        // 64 for 4x4, 6 for a diagonal factor, 0 for a swap; the touched
+        // fraction is 2^-(number of required bits)
+        const double amps = (double)((uint64_t)s->batch << n);
+        double fl = 0.0;
+        for (int i = 0; i < taken; ++i) {
+            const LGate &g = G[pp.gates[i]];
+            const GClass c = cls[pp.gates[i]];
+            int req = __builtin_popcountll(g.cmask);
+            double per = 0.0;
+            if (c == G_PHASE) {
+                req += g.k;
+                per = 6.0;
+            } else if (c == G_DIAG1) {
+                per = 6.0;
+            } else if (c == G_DENSE1) {
+                per = 16.0;
+            } else if (c == G_DENSE2) {
+                per = 64.0;
+            }
+            fl += amps * per / (double)(1ull << req);
+        }
+        prof_add_work(KC_TILED, 2.0 * amps * sizeof(V<R>), fl);
+    }
     if constexpr (sizeof(R) == 4)
         return k_tiled_pass_c64(s, P);
     else

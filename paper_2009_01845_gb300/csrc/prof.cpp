@@ -22,6 +22,8 @@ std::vector<cudaEvent_t> g_pool; // reusable events
 std::vector<cudaEvent_t> g_open; // started, not yet ended (per launch nesting)
 std::vector<int> g_open_cls;
 long long g_untimed[KC_COUNT];   // launches counted when events could not be made
+double g_bytes[KC_COUNT];
+double g_flops[KC_COUNT];
 
 const char *kNames[KC_COUNT] = {"init", "dense", "phase", "diag", "swap", "param",
                                 "tiled", "fused_tc", "reduce", "trotter_diag", "adjoint"};
@@ -39,6 +41,12 @@ cudaEvent_t take() {
 }  // namespace
 
 bool prof_enabled() { return g_on.load(std::memory_order_relaxed); }
+
+void prof_add_work(int c, double bytes, double flops) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_bytes[c] += bytes;
+    g_flops[c] += flops;
+}
 
 void prof_begin(cudaStream_t st, int c) {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -76,9 +84,10 @@ qs_status qs_profile_enable(int on) {
     return QS_OK;
 }
 
-qs_status qs_profile_collect(double *total_ms, long long *launches, int n_classes) {
+qs_status qs_profile_collect(double *total_ms, long long *launches, double *bytes, double *flops,
+                             int n_classes) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (n_classes < 0 || (n_classes > 0 && (!total_ms || !launches))) {
+    if (n_classes < 0 || (n_classes > 0 && (!total_ms || !launches || !bytes || !flops))) {
         set_error("bad output arrays");
         return QS_ERR_ARG;
     }
@@ -103,11 +112,15 @@ qs_status qs_profile_collect(double *total_ms, long long *launches, int n_classe
     for (int c = 0; c < n_classes && c < KC_COUNT; ++c) {
         total_ms[c] = ms[c];
         launches[c] = cnt[c];
+        bytes[c] = g_bytes[c];
+        flops[c] = g_flops[c];
     }
     for (int c = KC_COUNT; c < n_classes; ++c) {
         total_ms[c] = 0.0;
         launches[c] = 0;
+        bytes[c] = flops[c] = 0.0;
     }
+    for (int c = 0; c < KC_COUNT; ++c) g_bytes[c] = g_flops[c] = 0.0;
     return st;
 }
 

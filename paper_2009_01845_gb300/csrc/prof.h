@@ -25,13 +25,20 @@ bool prof_enabled();
 // record the start/end of one launch of class c on stream st
 void prof_begin(cudaStream_t st, int c);
 void prof_end(cudaStream_t st, int c);
+// add the algorithmic bytes (HBM reads + writes the operation needs) and
+// flops of the launches of class c
+void prof_add_work(int c, double bytes, double flops);
 
 struct ProfScope {
     cudaStream_t st;
     int c;
     bool on;
-    ProfScope(cudaStream_t s, int cls) : st(s), c(cls), on(prof_enabled()) {
-        if (on) prof_begin(st, c);
+    ProfScope(cudaStream_t s, int cls, double bytes = 0.0, double flops = 0.0)
+        : st(s), c(cls), on(prof_enabled()) {
+        if (on) {
+            prof_begin(st, c);
+            prof_add_work(c, bytes, flops);
+        }
     }
     ~ProfScope() {
         if (on) prof_end(st, c);

@@ -75,7 +75,7 @@ _SIGS = {
     "qs_adiabatic_evolve": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double,
                              ctypes.c_double, ctypes.c_int], None),
     "qs_profile_enable": ([ctypes.c_int], None),
-    "qs_profile_collect": ([P, P, ctypes.c_int], None),
+    "qs_profile_collect": ([P, P, P, P, ctypes.c_int], None),
     "qs_profile_class_name": ([ctypes.c_int], ctypes.c_char_p),
     "qs_profile_class_count": ([], ctypes.c_int),
 }
@@ -304,10 +304,13 @@ def profile_enable(on: bool = True):
 
 
 def profile_collect() -> dict:
-    """{class name: (total ms, launches)} since the last collect; resets."""
+    """{class name: (total ms, launches, algorithmic bytes, algorithmic flops)}
+    since the last collect; resets."""
     lib = load()
     nc = lib.qs_profile_class_count()
     ms = (ctypes.c_double * nc)()
     cnt = (ctypes.c_longlong * nc)()
-    _check(lib.qs_profile_collect(ms, cnt, nc))
-    return {lib.qs_profile_class_name(c).decode(): (ms[c], cnt[c]) for c in range(nc)}
+    by = (ctypes.c_double * nc)()
+    fl = (ctypes.c_double * nc)()
+    _check(lib.qs_profile_collect(ms, cnt, by, fl, nc))
+    return {lib.qs_profile_class_name(c).decode(): (ms[c], cnt[c], by[c], fl[c]) for c in range(nc)}

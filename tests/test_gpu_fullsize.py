@@ -10,7 +10,7 @@ from paper_2009_01845_gb300 import inputs as qi
 
 pytestmark = pytest.mark.gpu
 
-from test_gpu_parity import _inverse  # noqa: E402
+from circuit_utils import inverse_circuit as _inverse  # noqa: E402
 
 
 @pytest.fixture(scope="module")

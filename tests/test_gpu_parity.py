@@ -254,30 +254,3 @@ def test_tiled_batch_of_states(qs, dtype):
     got = st.get()
     for b in range(B):
         close(got[b], oracle.apply_circuit(psis[b].copy(), n, gates), dtype)
-
-
-def _inverse(gates):
-    inv = {"S": "SDG", "SDG": "S", "T": "TDG", "TDG": "T"}
-    out = []
-    for g in reversed(gates):
-        if g.kind == "U3":
-            th, ph, la = g.params
-            out.append(g._replace(params=(-th, -la, -ph)))
-        elif g.kind in ("RX", "RY", "RZ", "U1", "CU1"):
-            out.append(g._replace(params=(-g.params[0],)))
-        elif g.kind in inv:
-            out.append(g._replace(kind=inv[g.kind]))
-        elif g.kind == "UNITARY":
-            out.append(g._replace(matrix=np.conj(np.asarray(g.matrix)).T))
-        else:
-            out.append(g)
-    return out
-
-
-@pytest.mark.gpu
-def test_inverse_helper_against_oracle():
-    n = 6
-    gates = qi.random_mixed_circuit(n, 50, seed=3, max_controls=2, max_unitary_k=3)
-    psi = qi.random_state(n, 2)
-    back = oracle.apply_circuit(oracle.apply_circuit(psi.copy(), n, gates), n, _inverse(gates))
-    assert np.max(np.abs(back - psi)) < 1e-13
