@@ -379,11 +379,37 @@ static int red_blocks_per_member(const qs_state *s) {
     return (int)std::min<uint64_t>(std::min<uint64_t>(want, cap), 4096);
 }
 
-// Each thread sums runs of kChunk amplitudes in the state's precision and adds
-// every run to an FP64 accumulator: FP64 carries the reduction across the
-// state, while the per-amplitude arithmetic stays on the FP32 pipes for
-// complex64 (GB300's FP64 rate is about 1/60 of its FP32 rate).
+// Each thread sums runs of kChunk amplitudes and adds every run to an FP64
+// accumulator, so FP64 carries the reduction across the state while the
+// per-amplitude work stays off GB300's FP64 pipe (about 1/60 of the FP32
+// rate). For complex64 the run sum is error-free to float-float precision:
+// squares are split exactly with a fused multiply-add (x*x = p + e) and the
+// large parts are added with Knuth's TwoSum, so a run's value carries ~48
+// significant bits, like the FP64 sum it replaces.
 constexpr int kChunk = 16;
+
+template <typename R> struct RunSum {
+    R s = 0;
+    __device__ __forceinline__ void add_sq(R x, R y) { s = fma(x, x, fma(y, y, s)); }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+
+template <> struct RunSum<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void two_sum(float v) {
+        const float t = hi + v;
+        const float bv = t - hi;
+        lo += (hi - (t - bv)) + (v - bv);
+        hi = t;
+    }
+    __device__ __forceinline__ void add_sq(float x, float y) {
+        const float px = x * x, py = y * y;
+        lo += fmaf(x, x, -px) + fmaf(y, y, -py);
+        two_sum(px);
+        two_sum(py);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) norm2_partial_kernel(const V<R> *__restrict__ psi, int n,
@@ -394,13 +420,13 @@ __global__ void __launch_bounds__(kRedThreads) norm2_partial_kernel(const V<R> *
     double acc = 0.0;
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     while (i < per) {
-        R run = 0;
+        RunSum<R> run;
 #pragma unroll 4
         for (int c = 0; c < kChunk && i < per; ++c, i += stride) {
             const V<R> a = p[i];
-            run = fma(a.x, a.x, fma(a.y, a.y, run));
+            run.add_sq(a.x, a.y);
         }
-        acc += (double)run;
+        acc += run.value();
     }
     const double2 r = block_sum2(acc, 0.0);
     if (threadIdx.x == 0) part[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = r;
@@ -789,3 +815,4 @@ qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params, 
 }
 
 }  // namespace qsim
+
