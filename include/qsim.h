@@ -178,6 +178,29 @@ qs_status qs_norm2(qs_state *s, double *out);
 qs_status qs_expectation(qs_state *s, const qs_pauli_term *terms, size_t count,
                          double *out_re, double *out_im);
 
+/* Allocation-free variant of qs_expectation, for callers that cannot allocate
+   device memory: code running while a CUDA graph is being captured, an
+   allocator callback or an out-of-memory handler, a host that hands out only
+   memory it owns. The paper has no counterpart; it is a deployment aid.
+   psi_dev: device pointer to batch * 2^n amplitudes of `dtype` (read only);
+   out_dev: device pointer to 2 * batch doubles, written as (re, im) per member
+   in stream order on `cuda_stream` (NULL = legacy default stream). The call
+   needs no handle and calls no cudaMalloc/cudaFree or other allocator: its
+   partial sums live in one fixed device array of QS_NOALLOC_MAX_PARTIALS
+   (65536) double2 entries (1 MiB) that every GPU loading this library holds
+   until the process exits, so batch must be <= QS_NOALLOC_MAX_PARTIALS
+   (larger: QS_ERR_ARG). The first call on a device looks up that array's
+   device address (a runtime query, not an allocation); make that first call
+   before any stream capture. Every call shares the array and leaves its
+   partial sums in it (each call overwrites the slots it uses before summing
+   into them), so calls whose kernels overlap on the GPU -- e.g. on two
+   streams without ordering -- race and give wrong results. Asynchronous:
+   read out_dev after synchronising the stream. */
+#define QS_NOALLOC_MAX_PARTIALS 65536
+qs_status qs_expectation_noalloc(const void *psi_dev, int n, int batch, qs_dtype dtype,
+                                 const qs_pauli_term *terms, size_t count, double *out_dev,
+                                 void *cuda_stream);
+
 /* ---------------------------------------------------------------- Trotter (Sec. 2.6) */
 /* One second-order Trotter step of H(s) = (1-s) H0 + s H1 on every batch member:
      psi <- exp(-i dt/2 D(s)) exp(-i dt X(s)) exp(-i dt/2 D(s)) psi

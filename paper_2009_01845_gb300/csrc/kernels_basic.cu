@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "device.cuh"
 #include "internal.h"
@@ -816,3 +817,159 @@ qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params, 
 
 }  // namespace qsim
 
+// ================================================================== allocation-free expectation
+// qs_expectation_noalloc: the Pauli-sum expectation for callers that cannot
+// allocate device memory (see qsim.h). Its reduction scratch is a fixed
+// file-scope device array instead of the per-handle buffer of qs_expectation.
+namespace qsim {
+
+constexpr int kNoAllocMaxPartials = QS_NOALLOC_MAX_PARTIALS;
+
+// Shared by every call on a device, it keeps the last call's partial sums; each
+// call overwrites the slots it uses with its first launch before accumulating.
+static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocMaxPartials];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};  // device address of g_noalloc_partials, per device
+}  // namespace
+
+// Device address of the scratch array on the current device, looked up once per
+// device (host code may not use the symbol itself as a device pointer).
+static qs_status noalloc_scratch(int device, double2 **out) {
+    if (device < 0 || device >= 64) {
+        set_error("device ordinal %d not supported", device);
+        return QS_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_ptr[device] = p;
+    }
+    *out = (double2 *)g_noalloc_ptr[device];
+    return QS_OK;
+}
+
+template <typename R>
+static void fill_exp_params(ExpP<R> *p, int n, const qs_pauli_term *terms, size_t count, uint64_t xb,
+                            size_t *cursor) {
+    p->nt = 0;
+    for (; *cursor < count && p->nt < kMaxTermsPerLaunch; ++*cursor) {
+        const qs_pauli_term &t = terms[*cursor];
+        uint64_t tx = 0, zb = 0;
+        for (int q = 0; q < n; ++q) {
+            if ((t.x_mask >> q) & 1ull) tx |= qbit(n, q);
+            if ((t.z_mask >> q) & 1ull) zb |= qbit(n, q);
+        }
+        if (tx != xb) continue;
+        const int ny = __builtin_popcountll(t.x_mask & t.z_mask) & 3;
+        const double c = t.coeff;
+        const double re[4] = {c, 0.0, -c, 0.0}, im[4] = {0.0, c, 0.0, -c};
+        const int j = p->nt++;
+        p->cre[j] = (R)re[ny];
+        p->cim[j] = (R)im[ny];
+        p->zb[j] = zb;
+        const int nz = __builtin_popcountll(zb);
+        p->zn[j] = (int8_t)std::min(nz, 3);
+        p->za[j] = (int8_t)(nz ? __builtin_ctzll(zb) : -1);
+        p->zc[j] = (int8_t)(nz >= 2 ? 63 - __builtin_clzll(zb) : -1);
+    }
+}
+
+template <typename R>
+static qs_status expectation_noalloc_t(const V<R> *psi, int n, int batch, const qs_pauli_term *terms,
+                                       size_t count, double *out_dev, cudaStream_t stream, int device) {
+    double2 *part = nullptr;
+    QS_TRY(noalloc_scratch(device, &part));
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const uint64_t want = std::max<uint64_t>(1, (1ull << n) / (kRedThreads * 16));
+    const uint64_t cap = std::max<uint64_t>(1, (uint64_t)sms * 8 / batch);
+    const int P = (int)std::min<uint64_t>(std::min<uint64_t>(want, cap),
+                                          (uint64_t)(kNoAllocMaxPartials / batch));
+    const dim3 grid(P, batch);
+    bool first = true;
+    ExpP<R> p;  // on the host stack: passed by value as kernel parameters
+    for (size_t lead = 0; lead < count; ++lead) {
+        // one group per distinct X mask, handled at its first occurrence
+        uint64_t xb = 0;
+        for (int q = 0; q < n; ++q)
+            if ((terms[lead].x_mask >> q) & 1ull) xb |= qbit(n, q);
+        bool seen = false;
+        for (size_t e = 0; e < lead && !seen; ++e) {
+            uint64_t xe = 0;
+            for (int q = 0; q < n; ++q)
+                if ((terms[e].x_mask >> q) & 1ull) xe |= qbit(n, q);
+            seen = (xe == xb);
+        }
+        if (seen) continue;
+        size_t cursor = lead;
+        while (true) {
+            std::memset(&p, 0, sizeof(p));
+            fill_exp_params(&p, n, terms, count, xb, &cursor);
+            if (p.nt == 0) break;
+            p.xb = xb;
+            p.n = n;
+            p.hb = xb ? 63 - __builtin_clzll(xb) : 0;
+            p.n_free = xb ? n - 1 : n;
+            p.accumulate = first ? 0 : 1;
+            first = false;
+            expect_partial_kernel<R><<<grid, kRedThreads, 0, stream>>>(psi, p, part);
+            QS_CUDA_TRY(cudaGetLastError());
+            if (cursor >= count) break;
+        }
+    }
+    if (first) {
+        QS_CUDA_TRY(cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * batch, stream));
+        return QS_OK;
+    }
+    finalize_kernel<<<batch, kRedThreads, 0, stream>>>(part, P, out_dev, 1);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+}  // namespace qsim
+
+extern "C" qs_status qs_expectation_noalloc(const void *psi_dev, int n, int batch, qs_dtype dtype,
+                                            const qs_pauli_term *terms, size_t count, double *out_dev,
+                                            void *cuda_stream) {
+    using namespace qsim;
+    try {
+        clear_error();
+        if (!psi_dev || !out_dev || (count && !terms)) {
+            set_error("null pointer argument");
+            return QS_ERR_ARG;
+        }
+        if (n < 1 || n > QS_MAX_QUBITS || (dtype != QS_C64 && dtype != QS_C128)) {
+            set_error("bad n or dtype");
+            return QS_ERR_ARG;
+        }
+        if (batch < 1 || batch > kNoAllocMaxPartials) {
+            set_error("batch = %d outside [1, %d] (the fixed scratch holds %d partial sums)", batch,
+                      kNoAllocMaxPartials, kNoAllocMaxPartials);
+            return QS_ERR_ARG;
+        }
+        if ((uint64_t)batch > (1ull << (46 - n))) {
+            set_error("batch * 2^n too large");
+            return QS_ERR_ARG;
+        }
+        for (size_t i = 0; i < count; ++i)
+            if ((n < 64 && ((terms[i].x_mask | terms[i].z_mask) >> n) != 0) || !std::isfinite(terms[i].coeff)) {
+                set_error("term %zu names a qubit >= n or has a non-finite coefficient", i);
+                return QS_ERR_ARG;
+            }
+        int device = 0;
+        QS_CUDA_TRY(cudaGetDevice(&device));
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        if (dtype == QS_C64)
+            return expectation_noalloc_t<float>((const float2 *)psi_dev, n, batch, terms, count, out_dev, st,
+                                                device);
+        return expectation_noalloc_t<double>((const double2 *)psi_dev, n, batch, terms, count, out_dev, st,
+                                             device);
+    } catch (...) {
+        set_error("internal error");
+        return QS_ERR_CUDA;
+    }
+}

@@ -70,6 +70,8 @@ _SIGS = {
     "qs_probabilities": ([P, P, ctypes.c_int], None),
     "qs_norm2": ([P, P], None),
     "qs_expectation": ([P, P, ctypes.c_size_t, P, P], None),
+    "qs_expectation_noalloc": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, ctypes.c_size_t, P, P],
+                               None),
     "qs_trotter_step": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double,
                          ctypes.c_double], None),
     "qs_adiabatic_evolve": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double,
