@@ -13,10 +13,11 @@ What it computes, and where the Qibo paper defines it:
     Sec. 2.4), ``expectation``;
   * the second-order Trotter step of H(s) = (1-s) H0 + s H1 (Sec. 2.6, Eq. (4)),
     ``trotter_step`` and ``adiabatic_evolve``;
-  * the exact gradient of an energy with respect to rotation angles, by the
-    parameter-shift rule (``gradient_parameter_shift``), which the adjoint sweep
-    must reproduce (the paper differentiates through its native backends only,
-    Sec. 2.3);
+  * the exact gradient of an energy with respect to rotation angles, from the
+    product rule (``gradient_exact``, any controls) and by the parameter-shift
+    rule (``gradient_parameter_shift``, exact for uncontrolled rotations); the
+    adjoint sweep must reproduce them (the paper differentiates through its
+    native backends only, Sec. 2.3);
   * the fused matrix of a gate sequence on a qubit set (Sec. 2.4, "Gate
     fusion": the product of the gates' matrices), ``fused_matrix``.
 
@@ -273,6 +274,37 @@ def gradient_parameter_shift(n: int, gates, terms, psi0: np.ndarray | None = Non
             vals.append(energy(n, gs, terms, psi0))
         out[j] = 0.5 * (vals[0] - vals[1])
     return out
+
+
+def gradient_exact(n: int, gates, terms, psi0: np.ndarray | None = None) -> np.ndarray:
+    """dE/dtheta_j for every single-parameter gate j (RX, RY, RZ, U1, CU1, with
+    or without controls), in gate order, from the product rule:
+        dE/dtheta_j = 2 Re <psi|H|d_j psi>,
+        d_j psi = U_N .. U_{j+1} (dU_j/dtheta_j) U_{j-1} .. U_1 psi0,
+    where dU_j/dtheta_j is the derivative of the gate matrix on the block whose
+    controls are all 1 and zero elsewhere. Re <psi|H|chi> is taken by
+    polarisation, (<psi+chi|H|psi+chi> - <psi-chi|H|psi-chi>) / 4, which holds
+    for Hermitian H. Exact where the two-term shift rule is not (controlled
+    rotations have three generator eigenvalues)."""
+    gates = list(gates)
+    psi = run_circuit(n, gates, psi0)
+    out = []
+    for j, g in enumerate(gates):
+        if g.kind not in PARAMETRIC:
+            continue
+        phi = run_circuit(n, gates[:j], psi0)
+        if g.controls:
+            keep = np.ones(1 << n, dtype=bool)
+            idx = np.arange(1 << n)
+            for q in g.controls:
+                keep &= ((idx >> (n - 1 - q)) & 1) == 1
+            phi[~keep] = 0.0
+        apply_matrix(phi, n, g.targets, _gates.generator_derivative(g.kind, g.params), g.controls)
+        chi = apply_circuit(phi, n, gates[j + 1:])
+        plus = expectation(np.ascontiguousarray(psi + chi), n, terms).real
+        minus = expectation(np.ascontiguousarray(psi - chi), n, terms).real
+        out.append(2.0 * (plus - minus) / 4.0)
+    return np.array(out)
 
 
 # ---------------------------------------------------------------- fusion

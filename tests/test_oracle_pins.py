@@ -394,6 +394,36 @@ def test_parameter_shift_matches_finite_differences():
         assert abs(fd - g[j]) < 1e-7
 
 
+def test_exact_gradient_matches_shift_rule_and_finite_differences():
+    """gradient_exact equals the parameter-shift rule on uncontrolled rotations
+    and central finite differences everywhere, including controlled rotations
+    (where the two-term shift rule is not exact)."""
+    n = 5
+    r = qi.rng(21)
+    gates = []
+    for l in range(3):
+        for q in range(n):
+            kind = ["RX", "RY", "RZ", "U1"][int(r.integers(0, 4))]
+            ctrl = (int((q + 2) % n),) if l == 1 else ()
+            gates.append(qi.Gate(kind, (q,), ctrl, (float(r.uniform(0, 6.28)),)))
+        gates.append(qi.Gate("CU1", (l, l + 2), ((l + 4) % n,) if l == 2 else (), (float(r.uniform(0, 6.28)),)))
+        gates += [qi.Gate("H", (q,)) for q in range(0, n, 2)] + [qi.Gate("CZ", (i, i + 1)) for i in range(n - 1)]
+    terms = qi.tfim_terms(n, 0.8) + qi.random_pauli_terms(n, 3, 5)
+    g = oracle.gradient_exact(n, gates, terms)
+    ps = oracle.gradient_parameter_shift(n, gates, terms)
+    pidx = [i for i, gt in enumerate(gates) if gt.kind in oracle.PARAMETRIC]
+    h = 1e-4
+    for j, i in enumerate(pidx):
+        gp, gm = list(gates), list(gates)
+        gp[i] = gates[i]._replace(params=(gates[i].params[0] + h,))
+        gm[i] = gates[i]._replace(params=(gates[i].params[0] - h,))
+        fd = (oracle.energy(n, gp, terms) - oracle.energy(n, gm, terms)) / (2 * h)
+        assert abs(g[j] - fd) < 1e-7
+        if not gates[i].controls:
+            assert abs(g[j] - ps[j]) < 1e-12
+    assert any(abs(g[j] - ps[j]) > 1e-3 for j, i in enumerate(pidx) if gates[i].controls)
+
+
 # ------------------------------------------------------------------ fusion
 def test_fused_matrix_is_product_of_kronecker_operators():
     r = qi.rng(12)
