@@ -201,6 +201,40 @@ qs_status qs_expectation_noalloc(const void *psi_dev, int n, int batch, qs_dtype
                                  const qs_pauli_term *terms, size_t count, double *out_dev,
                                  void *cuda_stream);
 
+/* ---------------------------------------------------------------- adjoint gradient */
+/* Energies E_b(theta) = Re <psi_b|H|psi_b>, psi_b = U_N(theta_b) .. U_1(theta_b) psi0,
+   and their gradients dE_b/dtheta for a batch of parameter sets, by the adjoint
+   method: one forward pass, lambda = H psi, then one reverse sweep that undoes
+   each gate on (psi, lambda) with its inverse and reads the gradient of every
+   parametrised gate from <lambda|dU|psi>. The paper has no adjoint method (it
+   differentiates through its TensorFlow backends only, Sec. 2.3); the circuit
+   and H follow Sec. 2.3-2.4 and the variational ansatz of Sec. 3.2.
+   work: a handle of batch members of n + 1 qubits (batch * 2^(n+1) amplitudes)
+     for an n-qubit circuit; member b holds psi_b in its first 2^n amplitudes
+     and lambda_b in the next 2^n. Gate qubits refer to the n-qubit circuit.
+   gates: as in qs_apply_gates_batched; a gate with param_index p >= 0 (RX RY RZ
+     U1 CU1) takes its angle from params_dev[b * n_params + p] and receives a
+     gradient; other gates are fixed.
+   init_zero: 1 = psi0 = |0...0>, 0 = psi0 is what the first half holds.
+   energy_dev: batch doubles (device); grad_dev: batch * n_params doubles
+     (device, row-major), parameters used by no gate get 0; tied parameters
+     (several gates, one column) get the sum.
+   mode: QS_GRAD_FULL (forward, energy, sweep), QS_GRAD_FORWARD (forward and
+     energy only; psi and lambda stay in `work`), QS_GRAD_SWEEP (the sweep only,
+     continuing a QS_GRAD_FORWARD call on the same work buffer; needs
+     ckpt_every = 0).
+   ckpt_every > 0 (QS_GRAD_FULL): psi is checkpointed every ckpt_every gates in
+     the forward pass and restored at those boundaries of the sweep, bounding
+     the drift of uncomputing psi by inverse gates (extra memory: one psi copy
+     per checkpoint); 0 = pure uncompute.
+   Gradients are accumulated per tile and reduced in FP64 in a fixed order. */
+#define QS_GRAD_FULL 0
+#define QS_GRAD_FORWARD 1
+#define QS_GRAD_SWEEP 2
+qs_status qs_energy_gradient(qs_state *work, const qs_gate *gates, size_t count, const double *params_dev,
+                             int n_params, const qs_pauli_term *terms, size_t n_terms, int init_zero,
+                             double *energy_dev, double *grad_dev, int ckpt_every, int mode);
+
 /* ---------------------------------------------------------------- Trotter (Sec. 2.6) */
 /* One second-order Trotter step of H(s) = (1-s) H0 + s H1 on every batch member:
      psi <- exp(-i dt/2 D(s)) exp(-i dt X(s)) exp(-i dt/2 D(s)) psi

@@ -1,0 +1,56 @@
+// Adjoint gradient: shared declarations of its kernels and driver.
+#pragma once
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace qsim {
+
+// A (possibly strided) batch of n-qubit states: member b starts at amplitude b << ms.
+struct StateView {
+    void *data;
+    int n;
+    int ms;
+    int batch;
+    qs_dtype dtype;
+};
+
+constexpr int kPAMaxTerms = 384;
+constexpr int kPAMaxGroups = 64;
+
+template <typename R> struct PauliApplyP {
+    R cre[kPAMaxTerms];
+    R cim[kPAMaxTerms];
+    uint64_t zb[kPAMaxTerms];
+    uint64_t gx[kPAMaxGroups];
+    int gbeg[kPAMaxGroups + 1];
+    int ng;
+    int n;
+    int ms;
+    int accumulate;
+    uint64_t total;
+};
+
+constexpr int kGRMaxRows = 1024;   // parameters per reduction launch
+constexpr int kGRMaxSlots = 2048;  // gradient slots per reduction launch
+
+struct GradReduceP {
+    int beg[kGRMaxRows + 1];   // slot list of parameter row i: slot[beg[i] .. beg[i+1])
+    int slot[kGRMaxSlots];
+    float coef[kGRMaxSlots];   // 1 for rotations (Im<l|P|phi>), -2 for phase gates
+    uint64_t total_tiles;
+    uint64_t tiles_per_member;
+    int n_params;
+    int param0;                // first parameter row of this launch
+};
+
+qs_status k_pauli_apply(const StateView &src, const StateView &dst, const qs_pauli_term *terms, size_t count,
+                        cudaStream_t st);
+qs_status k_dot(const StateView &a, const StateView &b, double *scratch, size_t scratch_doubles, double *out,
+                cudaStream_t st);
+// gradient op on a small (phi, lambda) state: out[b] for every member b
+qs_status k_grad_small(qs_state *w, const LGate &g, double *out);
+qs_status k_grad_reduce(const double *part, const GradReduceP &p, int n_param_rows, int batch, double *grad,
+                        cudaStream_t st);
+
+}  // namespace qsim

@@ -11,6 +11,12 @@
 #include "plan.h"
 
 namespace qsim {
+qs_status energy_gradient(qs_state *w, const std::vector<LGate> &G, const double *params, int n_params,
+                          const qs_pauli_term *terms, size_t n_terms, int init_zero, double *energy,
+                          double *grad, int ckpt_every, int mode);
+}
+
+namespace qsim {
 const char *last_error();
 }
 
@@ -77,6 +83,7 @@ qs_status qs_state_create(int n, int batch, qs_dtype dtype, void *stream, qs_sta
     QS_TRY(check_shape(n, batch, dtype));
     qs_state *s = new qs_state();
     s->n = n;
+    s->ms = n;
     s->batch = batch;
     s->dtype = dtype;
     s->stream = (cudaStream_t)stream;
@@ -107,6 +114,7 @@ qs_status qs_state_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *s
     }
     qs_state *s = new qs_state();
     s->n = n;
+    s->ms = n;
     s->batch = batch;
     s->dtype = dtype;
     s->stream = (cudaStream_t)stream;
@@ -121,11 +129,12 @@ qs_status qs_state_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *s
 qs_status qs_state_destroy(qs_state *s) {
     QS_GUARD_BEGIN
     if (!s) return QS_OK;
-    if (s->owns || s->scratch || s->host_pinned || s->gtab) cudaStreamSynchronize(s->stream);
+    if (s->owns || s->scratch || s->host_pinned || s->gtab || s->ptab) cudaStreamSynchronize(s->stream);
     if (s->owns && s->data) cudaFree(s->data);
     if (s->scratch) cudaFree(s->scratch);
     if (s->host_pinned) cudaFreeHost(s->host_pinned);
     if (s->gtab) cudaFree(s->gtab);
+    if (s->ptab) cudaFree(s->ptab);
     plan_cache_release(s);
     delete s;
     return QS_OK;
@@ -347,6 +356,59 @@ qs_status qs_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, 
         if (out_im) out_im[b] = s->host_pinned[2 * b + 1];
     }
     return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_energy_gradient(qs_state *w, const qs_gate *gates, size_t count, const double *params_dev,
+                             int n_params, const qs_pauli_term *terms, size_t n_terms, int init_zero,
+                             double *energy_dev, double *grad_dev, int ckpt_every, int mode) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(w));
+    if (w->n < 2) {
+        set_error("the work handle needs n + 1 >= 2 qubits");
+        return QS_ERR_ARG;
+    }
+    if (mode != QS_GRAD_FULL && mode != QS_GRAD_FORWARD && mode != QS_GRAD_SWEEP) {
+        set_error("unknown mode %d", mode);
+        return QS_ERR_ARG;
+    }
+    if (mode != QS_GRAD_SWEEP && !energy_dev) {
+        set_error("null energy output");
+        return QS_ERR_ARG;
+    }
+    if (mode != QS_GRAD_FORWARD && !grad_dev) {
+        set_error("null gradient output");
+        return QS_ERR_ARG;
+    }
+    if (mode == QS_GRAD_SWEEP && ckpt_every != 0) {
+        set_error("checkpoints need the forward pass in the same call (mode QS_GRAD_FULL)");
+        return QS_ERR_ARG;
+    }
+    if (ckpt_every < 0 || n_params < 0) {
+        set_error("negative ckpt_every or n_params");
+        return QS_ERR_ARG;
+    }
+    qs_state circ = *w;   // lowering view: n-qubit circuit
+    circ.n = w->n - 1;
+    QS_TRY(check_terms(&circ, terms, n_terms));
+    std::vector<LGate> lg;
+    QS_TRY(lower_all(&circ, gates, count, &lg));
+    for (size_t i = 0; i < lg.size(); ++i) {
+        const int p = lg[i].param_index;
+        if (p < 0) continue;
+        if (p >= n_params || !params_dev) {
+            set_error("gate %zu: param_index %d outside [0, %d)", i, p, n_params);
+            return QS_ERR_ARG;
+        }
+        const int kd = lg[i].kind;
+        if (kd != QS_GATE_RX && kd != QS_GATE_RY && kd != QS_GATE_RZ && kd != QS_GATE_U1 && kd != QS_GATE_CU1) {
+            set_error("gate %zu: parametrised gates must be RX RY RZ U1 CU1", i);
+            return QS_ERR_ARG;
+        }
+    }
+    return energy_gradient(w, lg, params_dev, n_params, terms, n_terms, init_zero, energy_dev, grad_dev,
+                           ckpt_every, mode);
     QS_GUARD_END
 }
 

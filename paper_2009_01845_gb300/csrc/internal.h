@@ -13,6 +13,8 @@
 struct qs_state {
     int n = 0;              // qubits per batch member
     int batch = 1;          // number of members
+    int ms = 0;             // member b starts at amplitude b << ms (ms = n for a
+                            // contiguous batch; ms > n for internal strided views)
     qs_dtype dtype = QS_C64;
     void *data = nullptr;   // batch * 2^n amplitudes
     bool owns = false;
@@ -27,6 +29,9 @@ struct qs_state {
     // device table of per-member gate matrices (batched parameters)
     void *gtab = nullptr;
     size_t gtab_bytes = 0;
+    // per-member matrices of all batched-parameter gates of one tiled run
+    void *ptab = nullptr;
+    size_t ptab_bytes = 0;
 };
 
 namespace qsim {
@@ -64,8 +69,15 @@ struct LGate {
     bool phase_only = false;   // diagonal with all entries 1 but the last
     bool is_swap = false;      // the SWAP permutation
     int param_index = -1;      // batched parameter column, or -1
-    int kind = -1;             // QS_GATE_* of the source gate
+    int kind = -1;             // QS_GATE_* of the source gate, or kKindGrad
+    // adjoint sweep only (kind == kKindGrad): generator (GEN_X/Y/Z/PROJ) and
+    // the gradient slot the op accumulates into
+    int grad_gen = -1;
+    int grad_slot = -1;
 };
+
+// internal pseudo-kind of an adjoint-sweep gradient op
+constexpr int kKindGrad = 1000;
 
 // number of targets and parameters of a kind, or -1 if unknown
 int kind_targets(int kind);
@@ -86,8 +98,16 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count,
                         double **out_dev);               // 2 * batch doubles (re, im)
 qs_status ensure_scratch(qs_state *s, size_t doubles);
 qs_status ensure_gtab(qs_state *s, size_t bytes);
+// Per-member matrices of batched-parameter gates, 4 entries per slot: RX/RY the
+// row-major 2x2, RZ its diagonal (d0, d1), U1/CU1 the phase of the all-ones
+// block in entry 0. slot j uses column pidx[j] of the parameter
+// table, gate kind kind[j], angle sign * theta. Fills s->ptab as
+// [member][slot][4] in the state's precision; *stride = entries per member.
+qs_status k_param_table(qs_state *s, const std::vector<int> &pidx, const std::vector<int> &kind,
+                        const double *params_dev, int n_params, double sign, uint32_t *stride);
 // batched-parameter rotation (RX RY RZ U1 CU1) of one gate
-qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params_dev, int n_params);
+qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params_dev, int n_params,
+                             double sign = 1.0);
 qs_status ensure_host_pinned(qs_state *s, size_t doubles);
 
 // Trotter factors

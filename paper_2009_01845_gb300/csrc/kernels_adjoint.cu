@@ -1,0 +1,273 @@
+// Kernels of the adjoint gradient (no counterpart in the paper, which
+// differentiates through its TensorFlow backends only, Sec. 2.3):
+//   * pauli_apply_kernel: lambda = H phi for a Pauli sum H (the costate seed);
+//   * dot_partial_kernel: <phi|lambda> per member (the energy), FP64 across runs;
+//   * grad_reduce_kernel: per-tile gradient partials -> dE/dtheta, FP64, fixed order.
+// The reverse sweep itself runs in the tiled pass kernel (TOP_GRAD ops).
+#include <algorithm>
+#include <cstring>
+
+#include "adjoint.h"
+#include "device.cuh"
+#include "prof.h"
+
+namespace qsim {
+
+static unsigned grid_cap(uint64_t work, int threads) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t need = (work + threads - 1) / threads;
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sms * 32));
+}
+
+// ------------------------------------------------------------------ lambda = H phi
+// (P phi)[y] = i^{#Y} (-1)^{popcount((y ^ m) & z)} phi[y ^ m] for a term (c, m, z).
+template <typename R>
+__global__ void __launch_bounds__(256) pauli_apply_kernel(const V<R> *__restrict__ src, V<R> *__restrict__ dst,
+                                                          const __grid_constant__ PauliApplyP<R> p) {
+    const uint64_t mask = (1ull << p.n) - 1ull;
+    for (uint64_t i = global_tid(); i < p.total; i += global_stride()) {
+        const uint64_t y = i & mask;
+        const uint64_t mb = (i >> p.n) << p.ms;
+        V<R> acc = p.accumulate ? dst[mb | y] : mkc<R>(0, 0);
+        for (int g = 0; g < p.ng; ++g) {
+            const uint64_t x = y ^ p.gx[g];
+            R fr = 0, fi = 0;
+            for (int t = p.gbeg[g]; t < p.gbeg[g + 1]; ++t) {
+                const bool odd = __popcll(x & p.zb[t]) & 1;
+                fr += odd ? -p.cre[t] : p.cre[t];
+                fi += odd ? -p.cim[t] : p.cim[t];
+            }
+            acc = cmadd<R>(mkc<R>(fr, fi), src[mb | x], acc);
+        }
+        dst[mb | y] = acc;
+    }
+}
+
+template <typename R>
+static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const qs_pauli_term *terms, size_t count,
+                               cudaStream_t st) {
+    const int n = src.n;
+    // group by X mask, first-seen order
+    std::vector<uint64_t> masks;
+    std::vector<std::vector<size_t>> groups;
+    for (size_t t = 0; t < count; ++t) {
+        uint64_t xb = 0;
+        for (int q = 0; q < n; ++q)
+            if ((terms[t].x_mask >> q) & 1ull) xb |= 1ull << (n - 1 - q);
+        size_t gi = 0;
+        while (gi < masks.size() && masks[gi] != xb) ++gi;
+        if (gi == masks.size()) {
+            masks.push_back(xb);
+            groups.emplace_back();
+        }
+        groups[gi].push_back(t);
+    }
+    const uint64_t total = (uint64_t)src.batch << n;
+    ProfScope _ps(st, KC_ADJOINT, 2.0 * total * sizeof(V<R>), 8.0 * total * (double)count);
+    bool first = true;
+    size_t gi = 0;
+    while (gi < masks.size() || first) {
+        PauliApplyP<R> p;
+        std::memset(&p, 0, sizeof(p));
+        int nt = 0;
+        while (gi < masks.size() && p.ng < kPAMaxGroups &&
+               nt + (int)groups[gi].size() <= kPAMaxTerms) {
+            p.gx[p.ng] = masks[gi];
+            p.gbeg[p.ng] = nt;
+            for (size_t t : groups[gi]) {
+                const qs_pauli_term &tm = terms[t];
+                const int ny = __builtin_popcountll(tm.x_mask & tm.z_mask) & 3;
+                const double c = tm.coeff;
+                const double re[4] = {c, 0.0, -c, 0.0}, im[4] = {0.0, c, 0.0, -c};
+                p.cre[nt] = (R)re[ny];
+                p.cim[nt] = (R)im[ny];
+                uint64_t zb = 0;
+                for (int q = 0; q < n; ++q)
+                    if ((tm.z_mask >> q) & 1ull) zb |= 1ull << (n - 1 - q);
+                p.zb[nt] = zb;
+                ++nt;
+            }
+            ++p.ng;
+            ++gi;
+        }
+        if (p.ng == 0 && gi < masks.size()) {
+            set_error("a Pauli group has more than %d terms", kPAMaxTerms);
+            return QS_ERR_UNSUPPORTED;
+        }
+        p.gbeg[p.ng] = nt;
+        p.n = n;
+        p.ms = src.ms;
+        p.total = total;
+        p.accumulate = first ? 0 : 1;
+        first = false;
+        pauli_apply_kernel<R><<<grid_cap(total, 256), 256, 0, st>>>((const V<R> *)src.data, (V<R> *)dst.data, p);
+        QS_CUDA_TRY(cudaGetLastError());
+    }
+    return QS_OK;
+}
+
+qs_status k_pauli_apply(const StateView &src, const StateView &dst, const qs_pauli_term *terms, size_t count,
+                        cudaStream_t st) {
+    return src.dtype == QS_C64 ? pauli_apply_t<float>(src, dst, terms, count, st)
+                               : pauli_apply_t<double>(src, dst, terms, count, st);
+}
+
+// ------------------------------------------------------------------ <a|b> per member
+__device__ __forceinline__ double2 block_sum2_adj(double a, double b) {
+    __shared__ double2 sh[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = make_double2(a, b);
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        r = lane < nw ? sh[lane] : make_double2(0.0, 0.0);
+        for (int o = 16; o > 0; o >>= 1) {
+            r.x += __shfl_down_sync(0xffffffffu, r.x, o);
+            r.y += __shfl_down_sync(0xffffffffu, r.y, o);
+        }
+    }
+    __syncthreads();
+    return r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) dot_partial_kernel(const V<R> *__restrict__ a, const V<R> *__restrict__ b,
+                                                          int n, int ms, double2 *__restrict__ part) {
+    const uint64_t per = 1ull << n;
+    const V<R> *pa = a + ((uint64_t)blockIdx.y << ms);
+    const V<R> *pb = b + ((uint64_t)blockIdx.y << ms);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    double sr = 0.0, si = 0.0;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    while (i < per) {
+        R rr = 0, ri = 0;
+        for (int c = 0; c < 16 && i < per; ++c, i += stride) {
+            const V<R> x = pa[i], y = pb[i];
+            rr = fma(x.x, y.x, fma(x.y, y.y, rr));   // Re conj(x) y
+            ri = fma(x.x, y.y, fma(-x.y, y.x, ri));  // Im conj(x) y
+        }
+        sr += (double)rr;
+        si += (double)ri;
+    }
+    const double2 r = block_sum2_adj(sr, si);
+    if (threadIdx.x == 0) part[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = r;
+}
+
+__global__ void dot_finalize_kernel(const double2 *__restrict__ part, int per_member, double *__restrict__ out) {
+    const int b = blockIdx.x;
+    double x = 0.0, y = 0.0;
+    for (int i = threadIdx.x; i < per_member; i += blockDim.x) {
+        x += part[(uint64_t)b * per_member + i].x;
+        y += part[(uint64_t)b * per_member + i].y;
+    }
+    const double2 r = block_sum2_adj(x, y);
+    if (threadIdx.x == 0) {
+        out[2 * b] = r.x;
+        out[2 * b + 1] = r.y;
+    }
+}
+
+qs_status k_dot(const StateView &a, const StateView &b, double *scratch, size_t scratch_doubles, double *out,
+                cudaStream_t st) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t per = 1ull << a.n;
+    int P = (int)std::min<uint64_t>(std::max<uint64_t>(1, per / (256 * 16)),
+                                    std::max<uint64_t>(1, (uint64_t)sms * 8 / a.batch));
+    P = (int)std::min<size_t>((size_t)P, std::max<size_t>(1, scratch_doubles / (2 * (size_t)a.batch)));
+    ProfScope _ps(st, KC_ADJOINT, 2.0 * (double)((uint64_t)a.batch << a.n) * (a.dtype == QS_C64 ? 8 : 16),
+                  8.0 * (double)((uint64_t)a.batch << a.n));
+    dim3 grid(P, a.batch);
+    if (a.dtype == QS_C64)
+        dot_partial_kernel<float><<<grid, 256, 0, st>>>((const float2 *)a.data, (const float2 *)b.data, a.n, a.ms,
+                                                        (double2 *)scratch);
+    else
+        dot_partial_kernel<double><<<grid, 256, 0, st>>>((const double2 *)a.data, (const double2 *)b.data, a.n,
+                                                         a.ms, (double2 *)scratch);
+    QS_CUDA_TRY(cudaGetLastError());
+    dot_finalize_kernel<<<a.batch, 256, 0, st>>>((const double2 *)scratch, P, out);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------ gradient reduction
+// grad[b * n_params + p] = sum over the gradient slots s of parameter p of
+// coef[s] * sum over member b's tiles of part[s * total_tiles + tile], in a fixed
+// order (slot list order, then a block reduction over tiles).
+__global__ void __launch_bounds__(256) grad_reduce_kernel(const double *__restrict__ part,
+                                                          const __grid_constant__ GradReduceP p,
+                                                          double *__restrict__ grad) {
+    const int pi = blockIdx.x, b = blockIdx.y;
+    double total = 0.0;
+    for (int k = p.beg[pi]; k < p.beg[pi + 1]; ++k) {
+        const int s = p.slot[k];
+        const double *row = part + (uint64_t)s * p.total_tiles + (uint64_t)b * p.tiles_per_member;
+        double acc = 0.0;
+        for (uint64_t t = threadIdx.x; t < p.tiles_per_member; t += blockDim.x) acc += row[t];
+        const double2 r = block_sum2_adj(acc, 0.0);
+        total += p.coef[k] * r.x;   // thread 0 holds the block sum
+    }
+    if (threadIdx.x == 0) grad[(uint64_t)b * p.n_params + p.param0 + pi] = total;
+}
+
+qs_status k_grad_reduce(const double *part, const GradReduceP &p, int n_param_rows, int batch, double *grad,
+                        cudaStream_t st) {
+    if (n_param_rows <= 0) return QS_OK;
+    ProfScope _ps(st, KC_ADJOINT);
+    dim3 grid(n_param_rows, batch);
+    grad_reduce_kernel<<<grid, 256, 0, st>>>(part, p, grad);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------ small states
+// Gradient op for states too small for the sweep's tiles: one block per member
+// sums Im<lambda|P|phi> (see adjoint.cpp) over the member and writes out[b].
+template <typename R>
+__global__ void __launch_bounds__(256) grad_small_kernel(const V<R> *__restrict__ psi, int n, int gen, int tbit,
+                                                         uint64_t req, double *__restrict__ out) {
+    const int b = blockIdx.x;
+    const uint64_t half = 1ull << n;
+    const V<R> *ph = psi + ((uint64_t)b << (n + 1));
+    const V<R> *la = ph + half;
+    double acc = 0.0;
+    for (uint64_t x = threadIdx.x; x < half; x += blockDim.x) {
+        if ((x & req) != req) continue;
+        const bool tb = (x >> tbit) & 1ull;
+        const uint64_t xp = (gen == 0 || gen == 1) ? (x ^ (1ull << tbit)) : x;
+        const V<R> f = ph[xp], l = la[x];
+        const double im = (double)l.x * f.y - (double)l.y * f.x;
+        const double re = (double)l.x * f.x + (double)l.y * f.y;
+        if (gen == 0) acc += im;
+        else if (gen == 1) acc += tb ? re : -re;
+        else if (gen == 2) acc += tb ? -im : im;
+        else acc += im;
+    }
+    const double2 r = block_sum2_adj(acc, 0.0);
+    if (threadIdx.x == 0) out[b] = r.x;
+}
+
+qs_status k_grad_small(qs_state *w, const LGate &g, double *out) {
+    uint64_t req = g.cmask;
+    if (g.grad_gen == 3)
+        for (int j = 0; j < g.k; ++j) req |= 1ull << g.tbit[j];
+    ProfScope _ps(w->stream, KC_ADJOINT);
+    if (w->dtype == QS_C64)
+        grad_small_kernel<float><<<w->batch, 256, 0, w->stream>>>((const float2 *)w->data, w->n - 1, g.grad_gen,
+                                                                  g.tbit[0], req, out);
+    else
+        grad_small_kernel<double><<<w->batch, 256, 0, w->stream>>>((const double2 *)w->data, w->n - 1, g.grad_gen,
+                                                                   g.tbit[0], req, out);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+}  // namespace qsim

@@ -47,15 +47,14 @@ static void fill_insert(InsertBits *ib, uint64_t bits) {
 }
 
 // ================================================================== init
+// psi = (re, 0) everywhere, then 1 at index x of every member if x is valid
 template <typename R>
-__global__ void init_basis_kernel(V<R> *psi, int n, int batch, uint64_t x) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < batch) psi[((uint64_t)b << n) + x] = mkc<R>(1, 0);
-}
-
-template <typename R>
-__global__ void fill_kernel(V<R> *psi, uint64_t total, R re) {
-    for (uint64_t i = global_tid(); i < total; i += global_stride()) psi[i] = mkc<R>(re, 0);
+__global__ void fill_kernel(V<R> *psi, uint64_t total, int n, int ms, R re, uint64_t x) {
+    const uint64_t mask = (1ull << n) - 1ull;
+    for (uint64_t i = global_tid(); i < total; i += global_stride()) {
+        const uint64_t xi = i & mask;
+        psi[((i >> n) << ms) | xi] = mkc<R>(xi == x ? (R)1 : re, 0);
+    }
 }
 
 static size_t amp_bytes(const qs_state *s) { return s->dtype == QS_C64 ? 8 : 16; }
@@ -68,12 +67,11 @@ static void tally(int cls, const qs_state *s, double touched, double flops_per_a
 qs_status k_init_basis(qs_state *s, uint64_t x) {
     const uint64_t total = (uint64_t)s->batch << s->n;
     ProfScope _ps(s->stream, KC_INIT, (double)total * amp_bytes(s));
-    QS_CUDA_TRY(cudaMemsetAsync(s->data, 0, total * amp_bytes(s), s->stream));
-    const int thr = 128, blk = (s->batch + thr - 1) / thr;
+    const unsigned g = grid_for(s, total, 256);
     if (s->dtype == QS_C64)
-        init_basis_kernel<float><<<blk, thr, 0, s->stream>>>((float2 *)s->data, s->n, s->batch, x);
+        fill_kernel<float><<<g, 256, 0, s->stream>>>((float2 *)s->data, total, s->n, s->ms, 0.f, x);
     else
-        init_basis_kernel<double><<<blk, thr, 0, s->stream>>>((double2 *)s->data, s->n, s->batch, x);
+        fill_kernel<double><<<g, 256, 0, s->stream>>>((double2 *)s->data, total, s->n, s->ms, 0.0, x);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }
@@ -84,9 +82,9 @@ qs_status k_init_plus(qs_state *s) {
     const double a = std::pow(2.0, -0.5 * s->n);
     const unsigned g = grid_for(s, total, 256);
     if (s->dtype == QS_C64)
-        fill_kernel<float><<<g, 256, 0, s->stream>>>((float2 *)s->data, total, (float)a);
+        fill_kernel<float><<<g, 256, 0, s->stream>>>((float2 *)s->data, total, s->n, s->ms, (float)a, ~0ull);
     else
-        fill_kernel<double><<<g, 256, 0, s->stream>>>((double2 *)s->data, total, a);
+        fill_kernel<double><<<g, 256, 0, s->stream>>>((double2 *)s->data, total, s->n, s->ms, a, ~0ull);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }
@@ -139,7 +137,7 @@ static qs_status launch_dense(qs_state *s, const LGate &g) {
     }
     p.setmask = g.cmask;
     fill_insert(&p.ib, tmask | g.cmask);
-    p.n = s->n;
+    p.n = s->ms;  // member shift
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
     tally(KC_DENSE, s, (double)p.total * D, 8.0 * D);
@@ -200,7 +198,7 @@ static qs_status launch_phase(qs_state *s, uint64_t setmask, std::complex<double
     p.ph = mkc<R>((R)ph.real(), (R)ph.imag());
     p.setmask = setmask;
     fill_insert(&p.ib, setmask);
-    p.n = s->n;
+    p.n = s->ms;  // member shift
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
     tally(KC_PHASE, s, (double)p.total, 6.0);
@@ -218,7 +216,7 @@ static qs_status launch_diag(qs_state *s, const LGate &g) {
     for (int j = 0; j < K; ++j) p.tbit[j] = g.tbit[j];
     p.setmask = g.cmask;
     fill_insert(&p.ib, g.cmask);
-    p.n = s->n;
+    p.n = s->ms;  // member shift
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
     tally(KC_DIAG, s, (double)p.total, 6.0);
@@ -257,7 +255,7 @@ static qs_status launch_swap(qs_state *s, const LGate &g) {
     p.B = 1ull << g.tbit[1];
     p.setmask = g.cmask;
     fill_insert(&p.ib, p.A | p.B | g.cmask);
-    p.n = s->n;
+    p.n = s->ms;  // member shift
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
     tally(KC_SWAP, s, 2.0 * (double)p.total, 0.0);
@@ -413,10 +411,10 @@ template <> struct RunSum<float> {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads) norm2_partial_kernel(const V<R> *__restrict__ psi, int n,
+__global__ void __launch_bounds__(kRedThreads) norm2_partial_kernel(const V<R> *__restrict__ psi, int n, int ms,
                                                                     double2 *__restrict__ part) {
     const uint64_t per = 1ull << n;
-    const V<R> *p = psi + (uint64_t)blockIdx.y * per;
+    const V<R> *p = psi + ((uint64_t)blockIdx.y << ms);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     double acc = 0.0;
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,10 +460,10 @@ qs_status k_norm2(qs_state *s, double **out) {
                   4.0 * (double)((uint64_t)s->batch << s->n));
     dim3 grid(P, s->batch);
     if (s->dtype == QS_C64)
-        norm2_partial_kernel<float><<<grid, kRedThreads, 0, s->stream>>>((const float2 *)s->data, s->n,
+        norm2_partial_kernel<float><<<grid, kRedThreads, 0, s->stream>>>((const float2 *)s->data, s->n, s->ms,
                                                                           (double2 *)s->scratch);
     else
-        norm2_partial_kernel<double><<<grid, kRedThreads, 0, s->stream>>>((const double2 *)s->data, s->n,
+        norm2_partial_kernel<double><<<grid, kRedThreads, 0, s->stream>>>((const double2 *)s->data, s->n, s->ms,
                                                                            (double2 *)s->scratch);
     QS_CUDA_TRY(cudaGetLastError());
     finalize_kernel<<<s->batch, kRedThreads, 0, s->stream>>>((const double2 *)s->scratch, P, out_dev, 0);
@@ -488,6 +486,7 @@ template <typename R> struct ExpP {
     int nt;
     uint64_t xb;      // X mask in index bits (0 for the diagonal group)
     int n;
+    int ms;           // member shift
     int n_free;       // n (diagonal group) or n - 1 (pairs)
     int hb;           // highest bit of xb (pairs)
     int accumulate;   // add to the partials instead of overwriting
@@ -508,8 +507,7 @@ template <typename R>
 __global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> *__restrict__ psi,
                                                                      const __grid_constant__ ExpP<R> p,
                                                                      double2 *__restrict__ part) {
-    const uint64_t per = 1ull << p.n;
-    const V<R> *q = psi + (uint64_t)blockIdx.y * per;
+    const V<R> *q = psi + ((uint64_t)blockIdx.y << p.ms);
     const uint64_t cnt = 1ull << p.n_free;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     double ar = 0.0, ai = 0.0;
@@ -615,6 +613,7 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
             }
             p.xb = masks[gi];
             p.n = n;
+            p.ms = s->ms;
             p.hb = p.xb ? 63 - __builtin_clzll(p.xb) : 0;
             p.n_free = p.xb ? n - 1 : n;
             p.accumulate = first ? 0 : 1;
@@ -635,6 +634,7 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
                 pf.nt = p.nt;
                 pf.xb = p.xb;
                 pf.n = p.n;
+                pf.ms = p.ms;
                 pf.n_free = p.n_free;
                 pf.hb = p.hb;
                 pf.accumulate = p.accumulate;
@@ -665,6 +665,7 @@ struct DiagEvoP {
     uint64_t zb[kMaxTermsPerLaunch];
     int nt;
     int n;
+    int ms;
     double tau;
     uint64_t total;
 };
@@ -673,8 +674,9 @@ template <typename R>
 __global__ void __launch_bounds__(256) diag_evo_kernel(V<R> *__restrict__ psi,
                                                        const __grid_constant__ DiagEvoP p) {
     const uint64_t mask = (1ull << p.n) - 1ull;
-    for (uint64_t i = global_tid(); i < p.total; i += global_stride()) {
-        const uint64_t x = i & mask;
+    for (uint64_t i0 = global_tid(); i0 < p.total; i0 += global_stride()) {
+        const uint64_t x = i0 & mask;
+        const uint64_t i = ((i0 >> p.n) << p.ms) | x;
         double e = 0.0;
         for (int t = 0; t < p.nt; ++t) e += (__popcll(x & p.zb[t]) & 1) ? -p.c[t] : p.c[t];
         double sn, cs;
@@ -695,6 +697,7 @@ qs_status k_diagonal_evolution(qs_state *s, const std::vector<double> &coeff,
             p.zb[j] = zbits[c0 + j];
         }
         p.n = s->n;
+        p.ms = s->ms;
         p.tau = tau;
         p.total = (uint64_t)s->batch << s->n;
         tally(KC_TROTTER_DIAG, s, (double)p.total, 2.0 * p.nt + 26.0);
@@ -732,10 +735,10 @@ qs_status ensure_gtab(qs_state *s, size_t bytes) {
 
 template <typename R>
 __global__ void param_matrix_kernel(const double *__restrict__ params, int n_params, int pidx, int kind,
-                                    int batch, V<R> *__restrict__ mats) {
+                                    int batch, double sign, V<R> *__restrict__ mats) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
-    const double th = params[(uint64_t)b * n_params + pidx];
+    const double th = sign * params[(uint64_t)b * n_params + pidx];
     double s, c;
     sincos(0.5 * th, &s, &c);
     V<R> *m = mats + 4 * (uint64_t)b;
@@ -786,11 +789,11 @@ __global__ void __launch_bounds__(256) pdense_kernel(V<R> *__restrict__ psi, con
 }
 
 template <typename R>
-static qs_status apply_param_t(qs_state *s, const LGate &g, const double *params, int n_params) {
+static qs_status apply_param_t(qs_state *s, const LGate &g, const double *params, int n_params, double sign) {
     ProfScope _ps(s->stream, KC_PARAM);
     QS_TRY(ensure_gtab(s, sizeof(V<R>) * 4 * (size_t)s->batch));
     param_matrix_kernel<R><<<(s->batch + 127) / 128, 128, 0, s->stream>>>(params, n_params, g.param_index,
-                                                                          g.kind, s->batch, (V<R> *)s->gtab);
+                                                                          g.kind, s->batch, sign, (V<R> *)s->gtab);
     QS_CUDA_TRY(cudaGetLastError());
     PDenseP p;
     const bool phase = (g.kind == QS_GATE_U1 || g.kind == QS_GATE_CU1);
@@ -800,7 +803,7 @@ static qs_status apply_param_t(qs_state *s, const LGate &g, const double *params
     p.phase_only = phase ? 1 : 0;
     p.setmask = g.cmask | (phase ? tmask : 0);
     fill_insert(&p.ib, tmask | g.cmask);
-    p.n = s->n;
+    p.n = s->ms;  // member shift
     p.n_free = s->n - p.ib.count;
     p.total = (uint64_t)s->batch << p.n_free;
     tally(KC_PARAM, s, (double)p.total * (phase ? 1 : 2), phase ? 6.0 : 16.0);
@@ -810,9 +813,97 @@ static qs_status apply_param_t(qs_state *s, const LGate &g, const double *params
     return QS_OK;
 }
 
-qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params, int n_params) {
-    return s->dtype == QS_C64 ? apply_param_t<float>(s, g, params, n_params)
-                              : apply_param_t<double>(s, g, params, n_params);
+constexpr int kPTabSlotsPerLaunch = 512;
+struct PTabP {
+    int16_t pidx[kPTabSlotsPerLaunch];
+    int8_t kind[kPTabSlotsPerLaunch];
+    int n_slots;     // slots in this launch
+    int slot0;       // first slot index of this launch
+    int stride;      // entries per member
+    int n_params;
+    int batch;
+    double sign;
+};
+
+template <typename R>
+__global__ void param_table_kernel(const double *__restrict__ params, const __grid_constant__ PTabP p,
+                                   V<R> *__restrict__ tab) {
+    const uint64_t total = (uint64_t)p.batch * p.n_slots;
+    for (uint64_t i = global_tid(); i < total; i += global_stride()) {
+        const int b = (int)(i / p.n_slots), j = (int)(i % p.n_slots);
+        const double th = p.sign * params[(uint64_t)b * p.n_params + p.pidx[j]];
+        double sn, cs;
+        sincos(0.5 * th, &sn, &cs);
+        V<R> *m = tab + (uint64_t)b * p.stride + 4 * (uint64_t)(p.slot0 + j);
+        switch (p.kind[j]) {
+        case QS_GATE_RX:
+            m[0] = mkc<R>(cs, 0); m[1] = mkc<R>(0, -sn); m[2] = mkc<R>(0, -sn); m[3] = mkc<R>(cs, 0);
+            break;
+        case QS_GATE_RY:
+            m[0] = mkc<R>(cs, 0); m[1] = mkc<R>(-sn, 0); m[2] = mkc<R>(sn, 0); m[3] = mkc<R>(cs, 0);
+            break;
+        case QS_GATE_RZ:  // diagonal (d0, d1)
+            m[0] = mkc<R>(cs, -sn); m[1] = mkc<R>(cs, sn); m[2] = mkc<R>(0, 0); m[3] = mkc<R>(0, 0);
+            break;
+        default: {         // U1 / CU1: the phase on the all-ones block
+            double s2, c2;
+            sincos(th, &s2, &c2);
+            m[0] = mkc<R>(c2, s2); m[1] = mkc<R>(0, 0); m[2] = mkc<R>(0, 0); m[3] = mkc<R>(0, 0);
+        }
+        }
+    }
+}
+
+template <typename R>
+static qs_status param_table_t(qs_state *s, const std::vector<int> &pidx, const std::vector<int> &kind,
+                               const double *params, int n_params, double sign, uint32_t *stride) {
+    const int ns = (int)pidx.size();
+    const size_t need = sizeof(V<R>) * 4 * (size_t)ns * s->batch;
+    if (s->ptab_bytes < need) {
+        if (s->ptab) {
+            QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+            cudaFree(s->ptab);
+            s->ptab = nullptr;
+            s->ptab_bytes = 0;
+        }
+        QS_CUDA_TRY(cudaMalloc(&s->ptab, need));
+        s->ptab_bytes = need;
+    }
+    *stride = (uint32_t)(4 * ns);
+    ProfScope _ps(s->stream, KC_PARAM);
+    for (int j0 = 0; j0 < ns; j0 += kPTabSlotsPerLaunch) {
+        PTabP p;
+        std::memset(&p, 0, sizeof(p));
+        p.n_slots = std::min(kPTabSlotsPerLaunch, ns - j0);
+        for (int j = 0; j < p.n_slots; ++j) {
+            p.pidx[j] = (int16_t)pidx[j0 + j];
+            p.kind[j] = (int8_t)kind[j0 + j];
+        }
+        p.slot0 = j0;
+        p.stride = 4 * ns;
+        p.n_params = n_params;
+        p.batch = s->batch;
+        p.sign = sign;
+        const uint64_t total = (uint64_t)s->batch * p.n_slots;
+        param_table_kernel<R><<<grid_for(s, total, 256), 256, 0, s->stream>>>(params, p, (V<R> *)s->ptab);
+        QS_CUDA_TRY(cudaGetLastError());
+    }
+    return QS_OK;
+}
+
+qs_status k_param_table(qs_state *s, const std::vector<int> &pidx, const std::vector<int> &kind,
+                        const double *params, int n_params, double sign, uint32_t *stride) {
+    if (pidx.size() > 32767) {
+        set_error("too many batched-parameter gates");
+        return QS_ERR_ARG;
+    }
+    return s->dtype == QS_C64 ? param_table_t<float>(s, pidx, kind, params, n_params, sign, stride)
+                              : param_table_t<double>(s, pidx, kind, params, n_params, sign, stride);
+}
+
+qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params, int n_params, double sign) {
+    return s->dtype == QS_C64 ? apply_param_t<float>(s, g, params, n_params, sign)
+                              : apply_param_t<double>(s, g, params, n_params, sign);
 }
 
 }  // namespace qsim
@@ -912,6 +1003,7 @@ static qs_status expectation_noalloc_t(const V<R> *psi, int n, int batch, const 
             if (p.nt == 0) break;
             p.xb = xb;
             p.n = n;
+            p.ms = n;
             p.hb = xb ? 63 - __builtin_clzll(xb) : 0;
             p.n_free = xb ? n - 1 : n;
             p.accumulate = first ? 0 : 1;

@@ -114,6 +114,36 @@ __device__ __forceinline__ void dispatch_swap(V<R> *a, int A, int B, uint32_t mr
     QS_PAIR_CASES(swap_reg, a, mr)
 }
 
+// Im<lambda|P|phi> over this thread's registers for P = X or Y on register bit
+// J; phi in registers r < NR/2, lambda in r + NR/2 (the top register bit).
+template <typename R, int RB, int J>
+__device__ __forceinline__ R grad_xy_reg(const V<R> *a, int gen, uint32_t mr) {
+    constexpr int H = 1 << (RB - 1);
+    R acc = 0;
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+        if ((r & mr) != mr) continue;
+        const V<R> ph = a[r ^ (1 << J)], la = a[r + H];
+        // X: Im(conj(la) ph); Y: (r_J ? +1 : -1) * Re(conj(la) ph)
+        const R im = la.x * ph.y - la.y * ph.x;
+        const R re = la.x * ph.x + la.y * ph.y;
+        acc += gen == GEN_X ? im : (((r >> J) & 1) ? re : -re);
+    }
+    return acc;
+}
+
+template <typename R, int RB>
+__device__ __forceinline__ R dispatch_grad_xy(const V<R> *a, int j, int gen, uint32_t mr) {
+    switch (j) {
+    case 0: return grad_xy_reg<R, RB, 0>(a, gen, mr);
+    case 1: return grad_xy_reg<R, RB, 1>(a, gen, mr);
+    case 2: return grad_xy_reg<R, RB, 2>(a, gen, mr);
+    default:
+        if constexpr (RB > 4) return grad_xy_reg<R, RB, 3>(a, gen, mr);
+        return 0;
+    }
+}
+
 template <int RB>
 __device__ __forceinline__ uint64_t reg_offset(int r, const uint64_t *g) {
     uint64_t o = 0;
@@ -138,6 +168,7 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
     constexpr int NR = 1 << RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V<R> *sm = reinterpret_cast<V<R> *>(smem_raw);
+    __shared__ R gsm[kTileMaxGrad][kTileThreads / 32];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint64_t fmask = (1ull << p.n_free) - 1ull;
@@ -190,12 +221,13 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                 const TileOp &op = p.op[o];
                 const bool ok = ((tbase & op.mo) == op.mo) && ((lt & op.mt) == op.mt);
                 const uint32_t mr = op.mr;
+                const V<R> *M = op.pm ? (p.pmat + (t >> p.n_free) * p.pm_stride + op.m) : &p.mat[op.m];
                 switch (op.type) {
                 case TOP_DENSE1_L: {
                     // every lane takes part in the shuffles; only `ok` lanes update
                     const int bit = (lane >> op.a) & 1;
-                    const V<R> cs = bit ? p.mat[op.m + 3] : p.mat[op.m + 0];
-                    const V<R> co = bit ? p.mat[op.m + 2] : p.mat[op.m + 1];
+                    const V<R> cs = bit ? M[3] : M[0];
+                    const V<R> co = bit ? M[2] : M[1];
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
                         const V<R> v = shfl_xor_c<R>(a[r], 1 << op.a);
@@ -205,12 +237,11 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                 }
                 case TOP_DENSE1_R:
                     if (ok)
-                        dispatch_dense1<R, RB>(a, op.a, p.mat[op.m], p.mat[op.m + 1], p.mat[op.m + 2],
-                                               p.mat[op.m + 3], mr);
+                        dispatch_dense1<R, RB>(a, op.a, M[0], M[1], M[2], M[3], mr);
                     break;
                 case TOP_PHASE:
                     if (ok) {
-                        const V<R> ph = p.mat[op.m];
+                        const V<R> ph = M[0];
 #pragma unroll
                         for (int r = 0; r < NR; ++r)
                             if ((r & mr) == mr) a[r] = cmul<R>(a[r], ph);
@@ -218,7 +249,7 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                     break;
                 case TOP_DIAG1:
                     if (ok) {
-                        const V<R> d0 = p.mat[op.m], d1 = p.mat[op.m + 1];
+                        const V<R> d0 = M[0], d1 = M[1];
                         if (op.tkind == TB_REG) {
 #pragma unroll
                             for (int r = 0; r < NR; ++r)
@@ -234,11 +265,49 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                     }
                     break;
                 case TOP_DENSE2_RR:
-                    if (ok) dispatch_dense2<R, RB>(a, op.a, op.b, &p.mat[op.m], mr);
+                    if (ok) dispatch_dense2<R, RB>(a, op.a, op.b, M, mr);
                     break;
                 case TOP_SWAP_RR:
                     if (ok) dispatch_swap<R, RB>(a, op.a, op.b, mr);
                     break;
+                case TOP_GRAD: {
+                    constexpr int H = NR / 2;
+                    R acc = 0;
+                    if (op.b == GEN_X || op.b == GEN_Y) {
+                        if (op.tkind == TB_REG) {
+                            if (ok) acc = dispatch_grad_xy<R, RB>(a, op.a, op.b, mr);
+                        } else {
+                            // target on lane bit op.a: partner phi by shuffle
+                            const int bit = (lane >> op.a) & 1;
+#pragma unroll
+                            for (int r = 0; r < H; ++r) {
+                                const V<R> ph = shfl_xor_c<R>(a[r], 1 << op.a);
+                                const V<R> la = a[r + H];
+                                const R im = la.x * ph.y - la.y * ph.x;
+                                const R re = la.x * ph.x + la.y * ph.y;
+                                if (ok && (r & mr) == mr) acc += op.b == GEN_X ? im : (bit ? re : -re);
+                            }
+                        }
+                    } else if (ok) {
+                        // diagonal generator: Z on one bit, or the all-ones projector
+                        bool tz = false;
+                        if (op.b == GEN_Z && op.tkind != TB_REG)
+                            tz = op.tkind == TB_THREAD ? ((lt & (uint32_t)op.tmask) != 0) : ((tbase & op.tmask) != 0);
+#pragma unroll
+                        for (int r = 0; r < H; ++r) {
+                            if ((r & mr) != mr) continue;
+                            const V<R> ph = a[r], la = a[r + H];
+                            const R im = la.x * ph.y - la.y * ph.x;
+                            bool neg = false;
+                            if (op.b == GEN_Z) neg = op.tkind == TB_REG ? (((r >> op.a) & 1) != 0) : tz;
+                            acc += neg ? -im : im;
+                        }
+                    }
+#pragma unroll
+                    for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
+                    if (lane == 0) gsm[op.gl][warp] = acc;
+                    break;
+                }
                 default:
                     break;
                 }
@@ -256,6 +325,17 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
             for (int j = 0; j < RB; ++j) gr[j] = 1ull << p.gbit[sl.rloc[j]];
 #pragma unroll
             for (int r = 0; r < NR; ++r) psi[gt | reg_offset<RB>(r, gr)] = a[r];
+        }
+        // ---------------- gradient partials of this tile (fixed summation order)
+        if (p.n_grad > 0) {
+            __syncthreads();
+            if ((int)threadIdx.x < p.n_grad) {
+                double sum = 0.0;
+#pragma unroll
+                for (int w = 0; w < kTileThreads / 32; ++w) sum += (double)gsm[threadIdx.x][w];
+                p.gpart[(uint64_t)p.gslot[threadIdx.x] * p.total_tiles + t] = sum;
+            }
+            __syncthreads();
         }
     }
 }

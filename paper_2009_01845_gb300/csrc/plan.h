@@ -18,7 +18,11 @@ qs_status run_trotter(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const q
 
 // Tiled multi-gate passes (falls back to one pass per gate for gates a tile
 // cannot express and for states smaller than a tile).
-qs_status run_tiled(qs_state *s, const std::vector<LGate> &gates, const double *params_dev, int n_params);
+// force_bit >= 0 (adjoint sweep): that index bit is kept in every tile and
+// every stage's register set (it is the top register bit); gradient ops write
+// per-tile partials to gpart; batched-parameter gates use angle * param_sign.
+qs_status run_tiled(qs_state *s, const std::vector<LGate> &gates, const double *params_dev, int n_params,
+                    int force_bit = -1, double *gpart = nullptr, double param_sign = 1.0);
 
 // Free anything cached per state.
 void plan_cache_release(qs_state *s);

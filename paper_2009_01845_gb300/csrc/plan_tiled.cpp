@@ -26,10 +26,19 @@ qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p);
 
 namespace {
 
-enum GClass { G_PHASE, G_DIAG1, G_DENSE1, G_DENSE2, G_SWAP, G_SINGLE };
+enum GClass { G_PHASE, G_DIAG1, G_DENSE1, G_DENSE2, G_SWAP, G_GRAD, G_SINGLE };
 
 GClass classify(const LGate &g) {
-    if (g.param_index >= 0) return G_SINGLE;
+    if (g.kind == kKindGrad) return G_GRAD;
+    if (g.param_index >= 0) {
+        // batched parameters: the class follows the kind (the matrix differs per member)
+        switch (g.kind) {
+        case QS_GATE_RX: case QS_GATE_RY: return G_DENSE1;
+        case QS_GATE_RZ: return G_DIAG1;
+        case QS_GATE_U1: case QS_GATE_CU1: return G_PHASE;
+        default: return G_SINGLE;
+        }
+    }
     if (g.phase_only) return G_PHASE;
     if (g.diagonal) return g.k == 1 ? G_DIAG1 : G_SINGLE;
     if (g.is_swap) return (g.tbit[0] >= kTileLaneBits && g.tbit[1] >= kTileLaneBits) ? G_SWAP : G_SINGLE;
@@ -47,6 +56,8 @@ uint64_t qubit_bits(const LGate &g) {
 // high (non-lane) global bits a gate needs inside the tile
 uint64_t need_bits(const LGate &g, GClass c) {
     if (c == G_DENSE1) return g.tbit[0] >= kTileLaneBits ? (1ull << g.tbit[0]) : 0;
+    if (c == G_GRAD && (g.grad_gen == GEN_X || g.grad_gen == GEN_Y))
+        return g.tbit[0] >= kTileLaneBits ? (1ull << g.tbit[0]) : 0;
     if (c == G_DENSE2 || c == G_SWAP) return (1ull << g.tbit[0]) | (1ull << g.tbit[1]);
     return 0;
 }
@@ -68,9 +79,11 @@ struct PassPlan {
 
 }  // namespace
 
+// slot[i]: per-member table slot of gate i (batched parameters) or -1
 template <typename R>
 static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const std::vector<GClass> &cls,
-                              const PassPlan &pp, int *consumed) {
+                              const std::vector<int> &slot, uint32_t pm_stride, const PassPlan &pp,
+                              int force_bit, double *gpart, int *consumed) {
     const int n = s->n;
     const int RB = TileCfg<R>::RB;
     const int k = RB + kTileLaneBits + kTileWarpBits;
@@ -91,7 +104,9 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         for (int b = 0; b < 64; ++b)
             if ((nb >> b) & 1ull) needl[i] |= 1u << loc_of[b];
     }
+    const uint32_t force_loc = force_bit >= 0 ? (1u << loc_of[force_bit]) : 0u;
     auto choose = [&](int from, uint32_t forced) {
+        forced |= force_loc;
         // forced bits plus the high local bits used soonest from op `from` on
         std::vector<std::pair<int, int>> rank;  // (next use, local bit)
         for (int lb = kTileLaneBits; lb < k; ++lb) {
@@ -115,7 +130,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
 
     TileParams<R> P;
     std::memset(&P, 0, sizeof(P));
-    P.n = n;
+    P.n = s->ms;  // member shift: tiles of member b start at b << ms
     P.k = k;
     P.n_free = n - k;
     P.total_tiles = (uint64_t)s->batch << P.n_free;
@@ -127,6 +142,10 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             if ((tb >> b) & 1ull) P.tins.pos[P.tins.count++] = (int8_t)b;
     }
     for (int i = 0; i < k; ++i) P.gbit[i] = (uint8_t)gbit[i];
+    P.pmat = (const V<R> *)s->ptab;
+    P.pm_stride = pm_stride;
+    P.gpart = gpart;
+    int ngrad = 0;
 
     int nops = 0, nmat = 0, nst = 0, taken = 0;
     uint32_t cur = 0;
@@ -180,7 +199,9 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             if (nst >= kTileMaxStages) break;
             open_stage(choose(i, needl[i]));
         }
-        if (nops + ops_needed > kTileMaxOps || nmat + mat_entries(c) > kTileMaxMat) break;
+        const int sl = slot[pp.gates[i]];
+        if (nops + ops_needed > kTileMaxOps || nmat + (sl >= 0 ? 0 : mat_entries(c)) > kTileMaxMat) break;
+        if (c == G_GRAD && ngrad >= kTileMaxGrad) break;
         TileOp op;
         std::memset(&op, 0, sizeof(op));
         const int K = 1 << g.k;
@@ -190,8 +211,13 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             uint64_t req = g.cmask;
             for (int j = 0; j < g.k; ++j) req |= 1ull << g.tbit[j];
             split(req, &op.mr, &op.mt, &op.mo);
-            op.m = nmat;
-            put(g.m[(K - 1) * K + (K - 1)]);
+            if (sl >= 0) {
+                op.pm = 1;
+                op.m = 4 * sl;
+            } else {
+                op.m = nmat;
+                put(g.m[(K - 1) * K + (K - 1)]);
+            }
             break;
         }
         case G_DIAG1: {
@@ -209,9 +235,14 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 op.tkind = TB_THREAD;
                 op.tmask = 1ull << lb;
             }
-            op.m = nmat;
-            put(g.m[0]);
-            put(g.m[3]);
+            if (sl >= 0) {
+                op.pm = 1;
+                op.m = 4 * sl;
+            } else {
+                op.m = nmat;
+                put(g.m[0]);
+                put(g.m[3]);
+            }
             break;
         }
         case G_DENSE1: {
@@ -224,8 +255,13 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 op.a = (uint8_t)regidx(lb);
             }
             split(g.cmask, &op.mr, &op.mt, &op.mo);
-            op.m = nmat;
-            for (int e = 0; e < 4; ++e) put(g.m[e]);
+            if (sl >= 0) {
+                op.pm = 1;
+                op.m = 4 * sl;
+            } else {
+                op.m = nmat;
+                for (int e = 0; e < 4; ++e) put(g.m[e]);
+            }
             break;
         }
         case G_DENSE2:
@@ -249,6 +285,40 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             op.b = (uint8_t)B;
             break;
         }
+        case G_GRAD: {
+            op.type = TOP_GRAD;
+            op.b = (uint8_t)g.grad_gen;
+            op.gl = (uint8_t)ngrad;
+            P.gslot[ngrad++] = (uint16_t)g.grad_slot;
+            if (g.grad_gen == GEN_PROJ) {
+                uint64_t req = g.cmask;
+                for (int j = 0; j < g.k; ++j) req |= 1ull << g.tbit[j];
+                split(req, &op.mr, &op.mt, &op.mo);
+                break;
+            }
+            split(g.cmask, &op.mr, &op.mt, &op.mo);
+            const int b = g.tbit[0];
+            const int lb = loc_of[b];
+            if (g.grad_gen == GEN_Z) {
+                if (lb < 0) {
+                    op.tkind = TB_OUTSIDE;
+                    op.tmask = 1ull << b;
+                } else if (lb >= kTileLaneBits && ((cur >> lb) & 1u)) {
+                    op.tkind = TB_REG;
+                    op.a = (uint8_t)regidx(lb);
+                } else {
+                    op.tkind = TB_THREAD;
+                    op.tmask = 1ull << lb;
+                }
+            } else if (lb < kTileLaneBits) {
+                op.tkind = TB_THREAD;  // lane bit: shuffles
+                op.a = (uint8_t)lb;
+            } else {
+                op.tkind = TB_REG;
+                op.a = (uint8_t)regidx(lb);
+            }
+            break;
+        }
         default:
             break;
         }
@@ -257,6 +327,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         ++taken;
     }
     P.n_stages = nst;
+    P.n_grad = ngrad;
     *consumed = taken;
     if (taken == 0) return QS_OK;
     if (prof_enabled()) {
@@ -279,6 +350,8 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 per = 16.0;
             } else if (c == G_DENSE2) {
                 per = 64.0;
+            } else if (c == G_GRAD) {
+                per = 4.0;  // 8 per phi amplitude, phi is half the (phi, lambda) tile
             }
             fl += amps * per / (double)(1ull << req);
         }
@@ -290,10 +363,15 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         return k_tiled_pass_c128(s, P);
 }
 
-qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *params, int n_params) {
+qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *params, int n_params, int force_bit,
+                    double *gpart, double param_sign) {
     const int n = s->n;
     const int k = tile_bits(s->dtype);
     if (n < k) {
+        if (force_bit >= 0) {
+            set_error("adjoint sweep needs n + 1 >= %d", k);
+            return QS_ERR_UNSUPPORTED;
+        }
         for (const LGate &g : G) {
             if (g.param_index >= 0)
                 QS_TRY(k_apply_param_gate(s, g, params, n_params));
@@ -303,14 +381,26 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
         return QS_OK;
     }
     const int nh = k - kTileLaneBits;  // chosen high tile bits
+    const uint64_t force = force_bit >= 0 ? (1ull << force_bit) : 0ull;
     std::vector<GClass> cls(G.size());
     for (size_t i = 0; i < G.size(); ++i) cls[i] = classify(G[i]);
+    // per-member matrices of every batched-parameter gate, built once on the device
+    std::vector<int> slot(G.size(), -1), spidx, skind;
+    for (size_t i = 0; i < G.size(); ++i)
+        if (G[i].param_index >= 0 && cls[i] != G_SINGLE) {
+            slot[i] = (int)spidx.size();
+            spidx.push_back(G[i].param_index);
+            skind.push_back(G[i].kind);
+        }
+    uint32_t pm_stride = 0;
+    if (!spidx.empty()) QS_TRY(k_param_table(s, spidx, skind, params, n_params, param_sign, &pm_stride));
     std::vector<char> done(G.size(), 0);
     size_t first = 0;
     while (true) {
         while (first < G.size() && done[first]) ++first;
         if (first >= G.size()) break;
         PassPlan pp;
+        pp.high = force;
         uint64_t blocked = 0;
         for (size_t i = first; i < G.size(); ++i) {
             if (done[i]) continue;
@@ -334,9 +424,11 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
         }
         if (pp.gates.empty()) {
             // the front gate cannot run in a tile
+            // (in the adjoint sweep it acts on phi and lambda alike: neither the
+            // gate nor its controls touch the top bit that tells them apart)
             const LGate &g = G[first];
             if (g.param_index >= 0)
-                QS_TRY(k_apply_param_gate(s, g, params, n_params));
+                QS_TRY(k_apply_param_gate(s, g, params, n_params, param_sign));
             else
                 QS_TRY(k_apply_unfused(s, g));
             done[first] = 1;
@@ -346,9 +438,9 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
         for (int b = kTileLaneBits; b < n && __builtin_popcountll(pp.high) < nh; ++b) pp.high |= 1ull << b;
         int consumed = 0;
         if (s->dtype == QS_C64)
-            QS_TRY(emit_and_run<float>(s, G, cls, pp, &consumed));
+            QS_TRY(emit_and_run<float>(s, G, cls, slot, pm_stride, pp, force_bit, gpart, &consumed));
         else
-            QS_TRY(emit_and_run<double>(s, G, cls, pp, &consumed));
+            QS_TRY(emit_and_run<double>(s, G, cls, slot, pm_stride, pp, force_bit, gpart, &consumed));
         if (consumed <= 0) {
             set_error("tiled planner made no progress");
             return QS_ERR_CUDA;

@@ -29,6 +29,7 @@ constexpr int kTileWarpBits = 3;
 constexpr int kTileMaxStages = 48;
 constexpr int kTileMaxOps = 288;
 constexpr int kTileMaxMat = 640;   // complex entries in the matrix pool
+constexpr int kTileMaxGrad = 48;   // gradient ops per pass (adjoint sweep)
 
 // register bits per thread for each precision (c64: 32 amplitudes, c128: 16)
 template <typename R> struct TileCfg;
@@ -45,7 +46,12 @@ enum TileOpType : uint8_t {
     TOP_DENSE1_L,    // 2x2 on lane bit a (warp shuffles)
     TOP_DENSE2_RR,   // 4x4 on register bits (a = local MSB, b), a < b
     TOP_SWAP_RR,     // swap register bits a < b
+    TOP_GRAD,        // adjoint sweep: accumulate Im<lambda|P|phi> for a generator P
 };
+
+// Generators of TOP_GRAD (b field): Pauli X, Y, Z on one target, or the
+// projector on the all-ones block of the required bits (U1/CU1).
+enum TileGen : uint8_t { GEN_X = 0, GEN_Y = 1, GEN_Z = 2, GEN_PROJ = 3 };
 
 // Where a DIAG1 target bit lives in the current stage.
 enum TileBitKind : uint8_t { TB_REG = 0, TB_THREAD = 1, TB_OUTSIDE = 2 };
@@ -59,7 +65,9 @@ struct TileOp {
     uint8_t a, b;
     uint8_t tkind;    // TOP_DIAG1: TileBitKind of the target
     uint8_t mr;
-    uint8_t pad0[3];
+    uint8_t pm;       // 1: matrix entries come from the per-member table (pmat)
+    uint8_t gl;       // TOP_GRAD: row of this op in the pass's gradient table
+    uint8_t pad0;
     uint32_t mt;
     uint32_t m;       // first matrix-pool entry
     uint64_t mo;
@@ -74,13 +82,21 @@ struct TileStage {
 };
 
 template <typename R> struct TileParams {
-    int n;            // qubits per member
+    int n;            // member shift: member b starts at amplitude b << n
     int k;            // tile bits
     int n_stages;
     int n_free;       // n - k
     uint64_t total_tiles;
     InsertBits tins;  // sorted global positions of the tile bits
     uint8_t gbit[16]; // global bit of local bit i
+    const V<R> *pmat; // per-member matrices of batched-parameter gates, or null
+    uint32_t pm_stride;
+    // adjoint sweep: the state is (phi, lambda) per member, told apart by the
+    // member's top index bit, which is always the top register bit; gradient
+    // op g of this pass adds its per-tile partial to gpart[gslot[g] * total_tiles + tile]
+    int n_grad;
+    double *gpart;
+    uint16_t gslot[kTileMaxGrad];
     TileStage st[kTileMaxStages];
     TileOp op[kTileMaxOps];
     V<R> mat[kTileMaxMat];

@@ -72,6 +72,8 @@ _SIGS = {
     "qs_expectation": ([P, P, ctypes.c_size_t, P, P], None),
     "qs_expectation_noalloc": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, ctypes.c_size_t, P, P],
                                None),
+    "qs_energy_gradient": ([P, P, ctypes.c_size_t, P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int, P, P,
+                            ctypes.c_int, ctypes.c_int], None),
     "qs_trotter_step": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double,
                          ctypes.c_double], None),
     "qs_adiabatic_evolve": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double,
@@ -316,3 +318,75 @@ def profile_collect() -> dict:
     fl = (ctypes.c_double * nc)()
     _check(lib.qs_profile_collect(ms, cnt, by, fl, nc))
     return {lib.qs_profile_class_name(c).decode(): (ms[c], cnt[c], by[c], fl[c]) for c in range(nc)}
+
+
+# ------------------------------------------------------------------ adjoint gradient
+GRAD_MODE = {"full": 0, "forward": 1, "sweep": 2}
+
+
+def param_indices(gates, kinds=("RX", "RY", "RZ", "U1", "CU1")):
+    """param_index list giving every rotation of ``gates`` its own column, in order."""
+    out, c = [], 0
+    for g in gates:
+        if g.kind in kinds:
+            out.append(c)
+            c += 1
+        else:
+            out.append(-1)
+    return out, c
+
+
+class EnergyGradient:
+    """E_b(theta) = Re <psi_b|H|psi_b> and dE_b/dtheta for a batch of parameter
+    sets, through qs_energy_gradient. ``work`` holds (psi, lambda) per member:
+    a torch tensor of batch * 2^(n+1) amplitudes allocated here."""
+
+    def __init__(self, n: int, batch: int, gates, param_index, terms, dtype: str = "c64", stream=None):
+        import torch
+        self.n, self.batch, self.dtype = int(n), int(batch), dtype
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        self.work = torch.empty(self.batch << (self.n + 1), dtype=tdt, device="cuda")
+        self.state = State(self.n + 1, batch=self.batch, dtype=dtype, tensor=self.work, stream=stream)
+        self.lib = self.state.lib
+        self.gate_arr, self._keep = marshal_gates(gates, param_index)
+        self.count = len(gates)
+        self.term_arr, self.n_terms = marshal_terms(terms)
+
+    def run(self, params, mode: str = "full", init_zero: bool = True, ckpt_every: int = 0, energy=None,
+            grad=None):
+        import torch
+        if not (isinstance(params, torch.Tensor) and params.is_cuda and params.dtype == torch.float64):
+            raise ValueError("params must be a CUDA float64 tensor")
+        params = params.contiguous()
+        npar = int(params.shape[1]) if params.dim() == 2 else 0
+        if mode != "sweep" and energy is None:
+            energy = torch.empty(self.batch, dtype=torch.float64, device="cuda")
+        if mode != "forward" and grad is None:
+            grad = torch.empty(self.batch, npar, dtype=torch.float64, device="cuda")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(self.lib.qs_energy_gradient(self.state.handle, self.gate_arr, self.count, ptr(params), npar,
+                                           self.term_arr, self.n_terms, 1 if init_zero else 0, ptr(energy),
+                                           ptr(grad), int(ckpt_every), GRAD_MODE[mode]))
+        return energy, grad
+
+
+def energy_function():
+    """torch.autograd.Function computing E(theta) per batch member; backward
+    runs the adjoint reverse sweep (one sweep for all parameters)."""
+    import torch
+
+    class _Energy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params, engine):
+            energy, _ = engine.run(params, mode="forward")
+            ctx.engine = engine
+            ctx.save_for_backward(params)
+            return energy
+
+        @staticmethod
+        def backward(ctx, g_energy):
+            (params,) = ctx.saved_tensors
+            _, grad = ctx.engine.run(params, mode="sweep")
+            return g_energy[:, None] * grad, None
+
+    return _Energy
