@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--mode", default="auto", choices=["auto", "unfused", "tiled", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary workloads (variational adjoint)")
     return ap.parse_args()
 
 
@@ -206,6 +208,52 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ secondary workloads
+def _time_cuda(fn, steps: int, warmup: int = 2) -> float:
+    """Mean ms of fn() over `steps` calls, CUDA events on the current stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def variational_adjoint(steps: int = 5) -> dict:
+    """Variational ansatz n = 20, 10 layers of RY + CZ ladder, 256 parameter sets
+    (seed 4), complex64, TFIM energy g = 1: forward (incl. lambda = H psi and the
+    energy) vs forward + adjoint reverse sweep, through qs_energy_gradient."""
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    n, L, B = 20, 10, 256
+    th = qi.variational_params(B, L, n, seed=4)
+    tmpl = qi.variational_circuit(n, th[0])
+    pidx, P = qsim.param_indices(tmpl)
+    eng = qsim.EnergyGradient(n, B, tmpl, pidx, qi.tfim_terms(n, 1.0), dtype="c64")
+    params = torch.tensor(th.reshape(B, -1), device="cuda")
+    energy = torch.empty(B, dtype=torch.float64, device="cuda")
+    grad = torch.empty(B, P, dtype=torch.float64, device="cuda")
+    t_fwd = _time_cuda(lambda: eng.run(params, mode="forward", energy=energy), steps)
+    t_full = _time_cuda(lambda: eng.run(params, mode="full", energy=energy, grad=grad), steps)
+    qsim.profile_collect()
+    qsim.profile_enable(True)
+    eng.run(params, mode="full", energy=energy, grad=grad)
+    torch.cuda.synchronize()
+    qsim.profile_enable(False)
+    prof = qsim.profile_collect()
+    return {"workload": "variational n=20, 10 layers, batch 256, complex64, TFIM g=1",
+            "forward_ms": t_fwd, "forward_plus_adjoint_ms": t_full,
+            "adjoint_over_forward": (t_full - t_fwd) / t_fwd, "total_over_forward": t_full / t_fwd,
+            "gradients_per_s": B * P / (t_full / 1000.0),
+            "kernels_full_call": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(a):
     import torch
@@ -309,6 +357,12 @@ def run_ours(a):
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = oracle_sample(a)
+    secondary = {}
+    if not a.no_secondary:
+        st.close()
+        del st
+        torch.cuda.empty_cache()
+        secondary["variational_adjoint"] = variational_adjoint()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -321,9 +375,11 @@ def run_ours(a):
                 "kernels": {k: {"ms_per_step": v[0] / a.steps, "launches_per_step": v[1] / a.steps,
                                 "GB_per_step": v[2] / a.steps / 1e9, "GFLOP_per_step": v[3] / a.steps / 1e9}
                             for k, v in prof.items() if v[1]},
-                "energy_zz": float(out_re[0]), "norm2": float(out_n[0])}
+                "energy_zz": float(out_re[0]), "norm2": float(out_n[0]),
+                "secondary": secondary}
         print(json.dumps(line), flush=True)
-    st.close()
+    if a.no_secondary:
+        st.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -266,6 +266,16 @@ qs_status qs_profile_collect(double *total_ms, long long *launches, double *byte
 const char *qs_profile_class_name(int c);
 int qs_profile_class_count(void);
 
+/* Batched adiabatic evolution (Sec. 2.6, Eq. (4)) of a batch whose members have
+   their own H1: member b uses the h1_counts[b] terms that follow member b-1's in
+   `h1`; H0 is shared. Same schedule, splitting and step count as
+   qs_adiabatic_evolve. This fast form needs: no Z terms in H0, H1's Z terms
+   on at most two qubits (Ising form), the same X terms in every member's H1,
+   and n >= 13 (complex64) or 12 (complex128); otherwise QS_ERR_UNSUPPORTED.
+   Batch members of different widths are separate handles. */
+qs_status qs_adiabatic_evolve_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                                    const size_t *h1_counts, double T, double dt, int steps);
+
 #ifdef __cplusplus
 }
 #endif

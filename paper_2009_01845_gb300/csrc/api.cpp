@@ -129,12 +129,13 @@ qs_status qs_state_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *s
 qs_status qs_state_destroy(qs_state *s) {
     QS_GUARD_BEGIN
     if (!s) return QS_OK;
-    if (s->owns || s->scratch || s->host_pinned || s->gtab || s->ptab) cudaStreamSynchronize(s->stream);
+    if (s->owns || s->scratch || s->host_pinned || s->gtab || s->ptab || s->itab) cudaStreamSynchronize(s->stream);
     if (s->owns && s->data) cudaFree(s->data);
     if (s->scratch) cudaFree(s->scratch);
     if (s->host_pinned) cudaFreeHost(s->host_pinned);
     if (s->gtab) cudaFree(s->gtab);
     if (s->ptab) cudaFree(s->ptab);
+    if (s->itab) cudaFree(s->itab);
     plan_cache_release(s);
     delete s;
     return QS_OK;
@@ -444,7 +445,36 @@ qs_status qs_adiabatic_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
         return QS_ERR_ARG;
     }
     const long run = steps < 0 ? K : std::min<long>(K, steps);
+    if (run == 0) return QS_OK;
     return run_trotter(s, h0, n_h0, h1, n_h1, -1.0, dt, T, (int)run);
+    QS_GUARD_END
+}
+
+qs_status qs_adiabatic_evolve_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                                    const size_t *h1_counts, double T, double dt, int steps) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!h1_counts) {
+        set_error("null h1_counts");
+        return QS_ERR_ARG;
+    }
+    std::vector<size_t> off(s->batch + 1, 0);
+    for (int b = 0; b < s->batch; ++b) off[b + 1] = off[b] + h1_counts[b];
+    QS_TRY(check_terms(s, h0, n_h0));
+    QS_TRY(check_terms(s, h1, off[s->batch]));
+    if (!(T > 0) || !(dt > 0) || !std::isfinite(T) || !std::isfinite(dt)) {
+        set_error("T and dt must be positive and finite");
+        return QS_ERR_ARG;
+    }
+    const long K = std::lround(T / dt);
+    if (K < 1 || K > (1l << 30)) {
+        set_error("T/dt gives %ld steps", K);
+        return QS_ERR_ARG;
+    }
+    const long run = steps < 0 ? K : std::min<long>(K, steps);
+    if (run == 0) return QS_OK;
+    return run_adiabatic_batch(s, h0, n_h0, h1, off.data(), dt, T, (int)run);
     QS_GUARD_END
 }
 

@@ -32,6 +32,10 @@ struct qs_state {
     // per-member matrices of all batched-parameter gates of one tiled run
     void *ptab = nullptr;
     size_t ptab_bytes = 0;
+    // Ising coefficients of the Trotter diagonal (see tiled.h); stride 0 = shared
+    double *itab = nullptr;
+    size_t itab_bytes = 0;
+    uint32_t ising_stride = 0;
 };
 
 namespace qsim {
@@ -76,8 +80,10 @@ struct LGate {
     int grad_slot = -1;
 };
 
-// internal pseudo-kind of an adjoint-sweep gradient op
+// internal pseudo-kinds: an adjoint-sweep gradient op; an Ising phase
+// exp(-i tau E(x)) (tau in m[0].real(), coefficients in the state's ising table)
 constexpr int kKindGrad = 1000;
+constexpr int kKindIsing = 1001;
 
 // number of targets and parameters of a kind, or -1 if unknown
 int kind_targets(int kind);

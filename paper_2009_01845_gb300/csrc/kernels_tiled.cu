@@ -144,6 +144,122 @@ __device__ __forceinline__ R dispatch_grad_xy(const V<R> *a, int j, int gen, uin
     }
 }
 
+// exp(i angle) with the angle reduced to [-pi, pi] in FP64 first
+template <typename R> __device__ __forceinline__ V<R> expi(double angle) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const double a = angle - two_pi * rint(angle / two_pi);
+    if constexpr (sizeof(R) == 4) {
+        float sn, cs;
+        sincosf((float)a, &sn, &cs);
+        return mkc<float>(cs, sn);
+    } else {
+        double sn, cs;
+        sincos(a, &sn, &cs);
+        return mkc<double>(cs, sn);
+    }
+}
+
+template <typename R> __device__ __forceinline__ V<R> conjc(V<R> v) { return mkc<R>(v.x, -v.y); }
+
+// psi_x *= exp(-i tau E(x)) for an Ising energy E(x) = c + sum_i h_i z_i +
+// sum_{i<j} J_ij z_i z_j, z_i = 1 - 2 x_i. Split over the tile: the outside bits
+// and the thread's lane/warp bits give a per-thread constant C and per-register-
+// bit fields w_j (FP64), the register-register couplings a table Q[r]; then
+// E = C + sum_j w_j - 2 sum_{j: r_j = 1} w_j + Q[r] and the phase is a product
+// of per-thread factors, walked over the registers in Gray-code order.
+template <typename R, int RB>
+__device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, const TileOp &op, const TileStage &st,
+                                            uint64_t tbase, uint64_t member, int lane, int warp, double *s_g,
+                                            double *s_eo, V<R> *s_qp) {
+    constexpr int NR = 1 << RB;
+    const double tau = __longlong_as_double((long long)op.tmask);
+    const int nq = p.nq;
+    const double *J = p.ising + member * p.ising_stride;
+    const double *hv = J + (size_t)nq * nq;
+    const int tid = threadIdx.x;
+    if (tid < p.k) {
+        const int g = p.gbit[tid];
+        double acc = hv[g];
+        for (int o = 0; o < nq; ++o)
+            if (!((p.tile_mask >> o) & 1ull)) acc += ((tbase >> o) & 1ull) ? -J[g * nq + o] : J[g * nq + o];
+        s_g[tid] = acc;
+    } else if (tid >= 32 && tid < 64) {
+        double acc = 0.0;
+        for (int o = tid - 32; o < nq; o += 32) {
+            if ((p.tile_mask >> o) & 1ull) continue;
+            double row = hv[o];
+            for (int o2 = o + 1; o2 < nq; ++o2)
+                if (!((p.tile_mask >> o2) & 1ull)) row += ((tbase >> o2) & 1ull) ? -J[o * nq + o2] : J[o * nq + o2];
+            acc += ((tbase >> o) & 1ull) ? -row : row;
+        }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (tid == 32) *s_eo = acc + hv[nq];
+    } else if (tid >= 64 && tid < 64 + NR) {
+        const int r = tid - 64;
+        double q = 0.0;
+        for (int i = 0; i < RB; ++i)
+            for (int j = i + 1; j < RB; ++j) {
+                const double c = J[p.gbit[st.rloc[i]] * nq + p.gbit[st.rloc[j]]];
+                q += (((r >> i) ^ (r >> j)) & 1) ? -c : c;
+            }
+        s_qp[r] = expi<R>(-tau * q);
+    }
+    __syncthreads();
+    // the thread's 8 bits: lanes (local = global bits 0..4) and warp bits
+    int tg[8], tlc[8];
+    double tz[8];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        tg[i] = i;
+        tlc[i] = i;
+        tz[i] = ((lane >> i) & 1) ? -1.0 : 1.0;
+    }
+#pragma unroll
+    for (int w = 0; w < kTileWarpBits; ++w) {
+        tlc[5 + w] = st.wloc[w];
+        tg[5 + w] = p.gbit[st.wloc[w]];
+        tz[5 + w] = ((warp >> w) & 1) ? -1.0 : 1.0;
+    }
+    double C = *s_eo;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        C += s_g[tlc[i]] * tz[i];
+#pragma unroll
+        for (int j = i + 1; j < 8; ++j) C += J[tg[i] * nq + tg[j]] * tz[i] * tz[j];
+    }
+    double wsum = 0.0;
+    V<R> u[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+        const int gj = p.gbit[st.rloc[j]];
+        double wj = s_g[st.rloc[j]];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) wj += J[gj * nq + tg[i]] * tz[i];
+        wsum += wj;
+        u[j] = expi<R>(2.0 * tau * wj);
+    }
+    const V<R> base = expi<R>(-tau * (C + wsum));
+#pragma unroll
+    for (int hb = 0; hb < NR / 8; ++hb) {
+        V<R> q = base;
+#pragma unroll
+        for (int j = 3; j < RB; ++j)
+            if ((hb >> (j - 3)) & 1) q = cmul<R>(q, u[j]);
+#pragma unroll
+        for (int k8 = 0; k8 < 8; ++k8) {
+            const int gk = k8 ^ (k8 >> 1);
+            const int r = hb * 8 + gk;
+            a[r] = cmul<R>(a[r], cmul<R>(q, s_qp[r]));
+            if (k8 < 7) {
+                const int gn = (k8 + 1) ^ ((k8 + 1) >> 1);
+                const int bit = __ffs(gk ^ gn) - 1;
+                q = (gn >> bit) & 1 ? cmul<R>(q, u[bit]) : cmul<R>(q, conjc<R>(u[bit]));
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <int RB>
 __device__ __forceinline__ uint64_t reg_offset(int r, const uint64_t *g) {
     uint64_t o = 0;
@@ -169,6 +285,9 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V<R> *sm = reinterpret_cast<V<R> *>(smem_raw);
     __shared__ R gsm[kTileMaxGrad][kTileThreads / 32];
+    __shared__ double s_g[16];
+    __shared__ double s_eo;
+    __shared__ V<R> s_qp[NR];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint64_t fmask = (1ull << p.n_free) - 1ull;
@@ -269,6 +388,9 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                     break;
                 case TOP_SWAP_RR:
                     if (ok) dispatch_swap<R, RB>(a, op.a, op.b, mr);
+                    break;
+                case TOP_ISING:
+                    ising_phase<R, RB>(a, p, op, st, tbase, t >> p.n_free, lane, warp, s_g, &s_eo, s_qp);
                     break;
                 case TOP_GRAD: {
                     constexpr int H = NR / 2;

@@ -3,6 +3,9 @@
 #include <cstring>
 
 #include "plan.h"
+#include "tiled.h"
+
+#include <algorithm>
 
 namespace qsim {
 
@@ -96,11 +99,101 @@ static qs_status x_layer(qs_state *s, const TrotterTerms &tt, double sv, double 
     return QS_OK;
 }
 
+// Ising table of a diagonal Pauli sum (terms of at most two Z bits), in index
+// bits: J[a * n + b] (symmetric), h[n], constant. False if a term has more bits.
+static bool ising_table(int n, const std::vector<double> &d, const std::vector<uint64_t> &z, double *out) {
+    std::fill(out, out + (size_t)n * n + n + 1, 0.0);
+    for (size_t i = 0; i < d.size(); ++i) {
+        const int pc = __builtin_popcountll(z[i]);
+        if (pc == 0) {
+            out[(size_t)n * n + n] += d[i];
+        } else if (pc == 1) {
+            out[(size_t)n * n + __builtin_ctzll(z[i])] += d[i];
+        } else if (pc == 2) {
+            const int a = __builtin_ctzll(z[i]), b = 63 - __builtin_clzll(z[i]);
+            out[(size_t)a * n + b] += d[i];
+            out[(size_t)b * n + a] += d[i];
+        } else {
+            return false;
+        }
+    }
+    return true;
+}
+
+qs_status ensure_itab(qs_state *s, size_t doubles) {
+    if (s->itab_bytes >= doubles * sizeof(double)) return QS_OK;
+    if (s->itab) {
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        cudaFree(s->itab);
+        s->itab = nullptr;
+        s->itab_bytes = 0;
+    }
+    QS_CUDA_TRY(cudaMalloc(&s->itab, doubles * sizeof(double)));
+    s->itab_bytes = doubles * sizeof(double);
+    return QS_OK;
+}
+
+// The Trotter queue of tiled passes: Ising phases exp(-i tau E1(x)) and RX
+// layers. `taus[k]` precedes layer k; layer k rotates qubit q by 2 dt a_q(s_k).
+static qs_status trotter_tiled(qs_state *s, const TrotterTerms &tt, const std::vector<double> &taus,
+                               const std::vector<double> &svals, double dt) {
+    const int n = s->n;
+    std::vector<LGate> G;
+    G.reserve(taus.size() + svals.size() * n);
+    auto ising = [&](double tau) {
+        if (tau == 0.0 || tt.d1.empty()) return;
+        LGate g;
+        g.kind = kKindIsing;
+        g.k = 0;
+        g.diagonal = true;
+        g.m.assign(1, cd(tau, 0.0));
+        G.push_back(g);
+    };
+    for (size_t k = 0; k < svals.size(); ++k) {
+        ising(taus[k]);
+        for (int q = 0; q < n; ++q) {
+            const double a = (1.0 - svals[k]) * tt.a0[q] + svals[k] * tt.a1[q];
+            if (a == 0.0) continue;
+            qs_gate g;
+            std::memset(&g, 0, sizeof(g));
+            g.kind = QS_GATE_RX;
+            g.n_targets = 1;
+            g.targets[0] = q;
+            g.param_index = -1;
+            g.params[0] = 2.0 * dt * a;
+            LGate lg;
+            QS_TRY(lower_gate(n, g, &lg));
+            G.push_back(lg);
+        }
+    }
+    ising(taus[svals.size()]);
+    return run_tiled(s, G, nullptr, 0);
+}
+
 qs_status run_trotter(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1, size_t n_h1,
                       double s_fixed, double dt, double T, int steps) {
     TrotterTerms tt;
     QS_TRY(split_terms(s->n, h0, n_h0, &tt.d0, &tt.z0, &tt.a0));
     QS_TRY(split_terms(s->n, h1, n_h1, &tt.d1, &tt.z1, &tt.a1));
+    // tiled path: the state spans a tile, H0 has no diagonal part and H1's is Ising-form
+    std::vector<double> table((size_t)s->n * s->n + s->n + 1);
+    if (s->n >= tile_bits(s->dtype) && tt.d0.empty() && ising_table(s->n, tt.d1, tt.z1, table.data())) {
+        QS_TRY(ensure_itab(s, table.size()));
+        s->ising_stride = 0;
+        QS_CUDA_TRY(cudaMemcpyAsync(s->itab, table.data(), table.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                    s->stream));
+        std::vector<double> taus, svals;
+        if (s_fixed >= 0.0) {
+            svals = {s_fixed};
+            taus = {0.5 * dt * s_fixed, 0.5 * dt * s_fixed};
+        } else {
+            for (int k = 0; k < steps; ++k) svals.push_back((k + 0.5) * dt / T);
+            taus.push_back(0.5 * dt * svals[0]);
+            for (int k = 0; k + 1 < steps; ++k) taus.push_back(0.5 * dt * (svals[k] + svals[k + 1]));
+            taus.push_back(0.5 * dt * svals[steps - 1]);
+        }
+        return trotter_tiled(s, tt, taus, svals, dt);
+    }
     if (s_fixed >= 0.0) {
         const double sv = s_fixed;
         QS_TRY(diag_factor(s, tt, 1.0 - sv, sv, 0.5 * dt));
@@ -122,6 +215,54 @@ qs_status run_trotter(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const q
         }
     }
     return QS_OK;
+}
+
+// Batched adiabatic evolution: member b evolves under its own H1 (terms
+// h1[off[b] .. off[b+1])). Every member's X terms must agree (one RX layer for
+// the batch); the Ising diagonals are per member.
+qs_status run_adiabatic_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                              const size_t *off, double dt, double T, int steps) {
+    const int n = s->n;
+    const size_t stride = (size_t)n * n + n + 1;
+    TrotterTerms tt;
+    QS_TRY(split_terms(n, h0, n_h0, &tt.d0, &tt.z0, &tt.a0));
+    if (!tt.d0.empty()) {
+        set_error("batched evolution needs an H0 without Z terms");
+        return QS_ERR_UNSUPPORTED;
+    }
+    if (n < tile_bits(s->dtype)) {
+        set_error("batched evolution needs n >= %d", tile_bits(s->dtype));
+        return QS_ERR_UNSUPPORTED;
+    }
+    std::vector<double> tables(stride * s->batch);
+    for (int b = 0; b < s->batch; ++b) {
+        std::vector<double> d;
+        std::vector<uint64_t> z;
+        std::vector<double> a;
+        QS_TRY(split_terms(n, h1 + off[b], off[b + 1] - off[b], &d, &z, &a));
+        if (b == 0) {
+            tt.a1 = a;
+            tt.d1 = d;  // only its emptiness is used below
+        } else if (a != tt.a1) {
+            set_error("member %d: X terms of H1 differ from member 0", b);
+            return QS_ERR_UNSUPPORTED;
+        }
+        if (!d.empty()) tt.d1.assign(1, 1.0);
+        if (!ising_table(n, d, z, tables.data() + stride * b)) {
+            set_error("member %d: H1 has a Z term on more than two qubits", b);
+            return QS_ERR_UNSUPPORTED;
+        }
+    }
+    QS_TRY(ensure_itab(s, tables.size()));
+    s->ising_stride = (uint32_t)stride;
+    QS_CUDA_TRY(cudaMemcpyAsync(s->itab, tables.data(), tables.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                s->stream));
+    std::vector<double> taus, svals;
+    for (int k = 0; k < steps; ++k) svals.push_back((k + 0.5) * dt / T);
+    taus.push_back(0.5 * dt * svals[0]);
+    for (int k = 0; k + 1 < steps; ++k) taus.push_back(0.5 * dt * (svals[k] + svals[k + 1]));
+    taus.push_back(0.5 * dt * svals[steps - 1]);
+    return trotter_tiled(s, tt, taus, svals, dt);
 }
 
 }  // namespace qsim

@@ -24,6 +24,11 @@ qs_status run_trotter(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const q
 qs_status run_tiled(qs_state *s, const std::vector<LGate> &gates, const double *params_dev, int n_params,
                     int force_bit = -1, double *gpart = nullptr, double param_sign = 1.0);
 
+// Adiabatic evolution of a batch whose members have their own H1 (terms
+// h1[off[b] .. off[b+1]) for member b).
+qs_status run_adiabatic_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                              const size_t *off, double dt, double T, int steps);
+
 // Free anything cached per state.
 void plan_cache_release(qs_state *s);
 

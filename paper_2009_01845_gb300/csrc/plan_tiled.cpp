@@ -26,10 +26,11 @@ qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p);
 
 namespace {
 
-enum GClass { G_PHASE, G_DIAG1, G_DENSE1, G_DENSE2, G_SWAP, G_GRAD, G_SINGLE };
+enum GClass { G_PHASE, G_DIAG1, G_DENSE1, G_DENSE2, G_SWAP, G_GRAD, G_ISING, G_SINGLE };
 
 GClass classify(const LGate &g) {
     if (g.kind == kKindGrad) return G_GRAD;
+    if (g.kind == kKindIsing) return G_ISING;
     if (g.param_index >= 0) {
         // batched parameters: the class follows the kind (the matrix differs per member)
         switch (g.kind) {
@@ -145,6 +146,10 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     P.pmat = (const V<R> *)s->ptab;
     P.pm_stride = pm_stride;
     P.gpart = gpart;
+    P.ising = s->itab;
+    P.ising_stride = s->ising_stride;
+    P.nq = n;
+    for (int i = 0; i < k; ++i) P.tile_mask |= 1ull << gbit[i];
     int ngrad = 0;
 
     int nops = 0, nmat = 0, nst = 0, taken = 0;
@@ -285,6 +290,12 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             op.b = (uint8_t)B;
             break;
         }
+        case G_ISING: {
+            op.type = TOP_ISING;
+            const double tau = g.m[0].real();
+            std::memcpy(&op.tmask, &tau, sizeof(double));
+            break;
+        }
         case G_GRAD: {
             op.type = TOP_GRAD;
             op.b = (uint8_t)g.grad_gen;
@@ -352,6 +363,8 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 per = 64.0;
             } else if (c == G_GRAD) {
                 per = 4.0;  // 8 per phi amplitude, phi is half the (phi, lambda) tile
+            } else if (c == G_ISING) {
+                per = 18.0; // three complex products per amplitude
             }
             fl += amps * per / (double)(1ull << req);
         }
@@ -402,9 +415,11 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
         PassPlan pp;
         pp.high = force;
         uint64_t blocked = 0;
+        const uint64_t all_bits = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
         for (size_t i = first; i < G.size(); ++i) {
             if (done[i]) continue;
-            const uint64_t qb = qubit_bits(G[i]);
+            if (blocked == all_bits) break;  // nothing later can join this pass
+            const uint64_t qb = cls[i] == G_ISING ? all_bits : qubit_bits(G[i]);
             if (qb & blocked) {
                 blocked |= qb;
                 continue;

@@ -47,6 +47,7 @@ enum TileOpType : uint8_t {
     TOP_DENSE2_RR,   // 4x4 on register bits (a = local MSB, b), a < b
     TOP_SWAP_RR,     // swap register bits a < b
     TOP_GRAD,        // adjoint sweep: accumulate Im<lambda|P|phi> for a generator P
+    TOP_ISING,       // psi_x *= exp(-i tau E(x)), E an Ising energy (<= 2-body Z terms)
 };
 
 // Generators of TOP_GRAD (b field): Pauli X, Y, Z on one target, or the
@@ -97,6 +98,13 @@ template <typename R> struct TileParams {
     int n_grad;
     double *gpart;
     uint16_t gslot[kTileMaxGrad];
+    // TOP_ISING: per-member Ising coefficients in index bits, ising_stride
+    // doubles per member: J[a * nq + b] (symmetric, zero diagonal), then h[nq],
+    // then the constant; nq = qubits per member; tau in the op's tmask bits
+    const double *ising;
+    uint32_t ising_stride;
+    int nq;
+    uint64_t tile_mask;   // global bits of the tile
     TileStage st[kTileMaxStages];
     TileOp op[kTileMaxOps];
     V<R> mat[kTileMaxMat];

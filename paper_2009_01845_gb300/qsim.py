@@ -78,6 +78,8 @@ _SIGS = {
                          ctypes.c_double], None),
     "qs_adiabatic_evolve": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double,
                              ctypes.c_double, ctypes.c_int], None),
+    "qs_adiabatic_evolve_batch": ([P, P, ctypes.c_size_t, P, P, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int], None),
     "qs_profile_enable": ([ctypes.c_int], None),
     "qs_profile_collect": ([P, P, P, P, ctypes.c_int], None),
     "qs_profile_class_name": ([ctypes.c_int], ctypes.c_char_p),
@@ -299,6 +301,17 @@ class State:
         a0, n0 = marshal_terms(h0)
         a1, n1 = marshal_terms(h1)
         _check(self.lib.qs_adiabatic_evolve(self.handle, a0, n0, a1, n1, float(T), float(dt), int(steps)))
+        return self
+
+    def adiabatic_evolve_batch(self, h0, h1_per_member, T: float, dt: float, steps: int = -1):
+        """Member b evolves under its own H1 = h1_per_member[b]."""
+        if len(h1_per_member) != self.batch:
+            raise ValueError("one H1 per batch member")
+        a0, n0 = marshal_terms(h0)
+        flat = [t for h in h1_per_member for t in h]
+        a1, _ = marshal_terms(flat)
+        counts = (ctypes.c_size_t * self.batch)(*[len(h) for h in h1_per_member])
+        _check(self.lib.qs_adiabatic_evolve_batch(self.handle, a0, n0, a1, counts, float(T), float(dt), int(steps)))
         return self
 
 

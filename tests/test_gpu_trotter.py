@@ -1,0 +1,92 @@
+"""Trotterised adiabatic evolution (Sec. 2.6) on the tiled path: Ising phase
+ops fused with the RX layers, against the oracle's step-by-step evolution."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_01845_gb300 import inputs as qi
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-12, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2009_01845_gb300 import qsim
+    qsim.load(build_if_missing=True)
+    return qsim
+
+
+def tile_n(dtype):
+    return 13 if dtype == "c64" else 12
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_trotter_step_tiled(qs, dtype):
+    n = tile_n(dtype) + 1
+    h0 = qi.transverse_field_terms(n)
+    h1 = qi.random_ising_terms(n, qi.rng(3)) + [(0.4, 1 << 3, 0), (0.25, 0, 0)]
+    psi = qi.random_state(n, 5)
+    want = oracle.trotter_step(psi.copy(), n, h0, h1, 0.37, 0.05)
+    st = qs.State(n, dtype=dtype).set(psi).trotter_step(h0, h1, 0.37, 0.05)
+    assert np.max(np.abs(st.get() - want)) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_adiabatic_evolution_tiled(qs, dtype):
+    n, T, dt = tile_n(dtype), 1.0, 0.05
+    h0 = qi.transverse_field_terms(n)
+    h1 = qi.random_ising_terms(n, qi.rng(8))
+    want = oracle.adiabatic_evolve(oracle.plus_state(n), n, h0, h1, T, dt)
+    st = qs.State(n, dtype=dtype).init_plus().adiabatic_evolve(h0, h1, T, dt)
+    assert np.max(np.abs(st.get() - want)) < 10 * TOL[dtype]
+
+
+def test_tfim_example_of_sec2_6(qs):
+    """The paper's example: H0 = -sum X, H1 = TFIM (field terms in H1 too),
+    linear schedule; tiled complex128 evolution against the oracle."""
+    n, T, dt = 12, 3.0, 0.1
+    h0 = qi.transverse_field_terms(n)
+    h1 = qi.tfim_terms(n, 1.0)
+    want = oracle.adiabatic_evolve(oracle.plus_state(n), n, h0, h1, T, dt)
+    st = qs.State(n, dtype="c128").init_plus().adiabatic_evolve(h0, h1, T, dt)
+    assert np.max(np.abs(st.get() - want)) < 1e-11
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_adiabatic_batch_own_hamiltonians(qs, dtype):
+    n, B, T, dt = tile_n(dtype) + 1, 3, 0.5, 0.05
+    r = qi.rng(44)
+    h0 = qi.transverse_field_terms(n)
+    h1s = [qi.random_ising_terms(n, r) for _ in range(B)]
+    st = qs.State(n, batch=B, dtype=dtype).init_plus().adiabatic_evolve_batch(h0, h1s, T, dt)
+    got = st.get()
+    for b in range(B):
+        want = oracle.adiabatic_evolve(oracle.plus_state(n), n, h0, h1s[b], T, dt)
+        assert np.max(np.abs(got[b] - want)) < 10 * TOL[dtype]
+
+
+def test_three_body_terms_use_the_general_path(qs):
+    n = 13
+    h0 = qi.transverse_field_terms(n)
+    h1 = qi.random_ising_terms(n, qi.rng(2)) + [(0.3, 0, 0b1011)]
+    psi = qi.random_state(n, 6)
+    want = oracle.trotter_step(psi.copy(), n, h0, h1, 0.6, 0.1)
+    st = qs.State(n, dtype="c128").set(psi).trotter_step(h0, h1, 0.6, 0.1)
+    assert np.max(np.abs(st.get() - want)) < 1e-12
+    with pytest.raises(qs.QsimError) as e:
+        qs.State(n, batch=1, dtype="c128").init_plus().adiabatic_evolve_batch(h0, [h1], 1.0, 0.1)
+    assert e.value.status == 4
+
+
+def test_config5_smallest_instance_sampled_steps(qs):
+    """The adiabatic batch workload's first n = 16 instance (seed 5), complex64,
+    50 of its 1000 steps, against the oracle."""
+    inst = [x for x in qi.adiabatic_instances(64, seed=5) if x[0] == 16]
+    assert inst, "seed 5 draws at least one n = 16 instance"
+    n, h0, h1 = inst[0]
+    T, dt, steps = 10.0, 0.01, 50
+    want = oracle.adiabatic_evolve(oracle.plus_state(n), n, h0, h1, T, dt, steps=steps)
+    st = qs.State(n, dtype="c64").init_plus().adiabatic_evolve(h0, h1, T, dt, steps=steps)
+    assert np.max(np.abs(st.get() - want)) < 1e-5
