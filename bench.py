@@ -254,6 +254,65 @@ def variational_adjoint(steps: int = 5) -> dict:
             "kernels_full_call": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
 
 
+def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
+    """Adiabatic evolution batch: 64 instances, n ~ U{16..26} (seed 5), H0 = -sum X,
+    H1 = sum J_ij Z_i Z_j + sum h_i Z_i with J, h ~ N(0, 1), linear schedule,
+    T = 10, dt = 0.01, |+>^n. Timed on the first `steps` of the 1000 steps
+    (each step costs the same), grouped by width into one batched call per width
+    ("batched"), and instance by instance ("sequential"). Reports instance-steps/s;
+    also the final energy and the ground-state overlap of the smallest
+    instance after all 1000 steps (ground state by brute force over 2^16)."""
+    import numpy as np
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    inst = qi.adiabatic_instances(64, seed=5)
+    T, dt = 10.0, 0.01
+    widths = sorted({m for m, _, _ in inst})
+    groups = {w: [i for i, (m, _, _) in enumerate(inst) if m == w] for w in widths}
+    states = {w: qsim.State(w, batch=len(ix), dtype=dtype) for w, ix in groups.items()}
+
+    def batched():
+        for w, ix in groups.items():
+            states[w].init_plus().adiabatic_evolve_batch(inst[ix[0]][1], [inst[i][2] for i in ix], T, dt,
+                                                         steps=steps)
+
+    t_b = _time_cuda(batched, 1, warmup=1)
+    solo = {w: qsim.State(w, dtype=dtype) for w in widths}
+
+    def sequential():
+        for m, h0, h1 in inst:
+            solo[m].init_plus().adiabatic_evolve(h0, h1, T, dt, steps=steps)
+
+    t_s = _time_cuda(sequential, 1, warmup=1)
+    # the smallest instance, all 1000 steps: energy and ground-state overlap
+    m0, h0, h1 = inst[min(groups[widths[0]])]
+    st = qsim.State(m0, dtype=dtype).init_plus().adiabatic_evolve(h0, h1, T, dt)
+    e_final = float(st.expectation(h1)[0].real)
+    idx = np.arange(1 << m0)
+    E = np.zeros(1 << m0)
+    for c, _, zm in h1:
+        par = np.zeros(1 << m0, dtype=np.int64)
+        for q in range(m0):
+            if (zm >> q) & 1:
+                par ^= (idx >> (m0 - 1 - q)) & 1
+        E += c * (1 - 2 * par)
+    gmin = E.min()
+    ground = np.flatnonzero(np.isclose(E, gmin, rtol=0, atol=1e-12))
+    p = st.probabilities()
+    del states, solo
+    torch.cuda.empty_cache()
+    isteps = 64 * steps
+    return {"workload": f"adiabatic batch: 64 instances n in [16,26] (seed 5), T=10, dt=0.01, {dtype}, "
+                        f"first {steps} of 1000 second-order Trotter steps timed",
+            "batched_ms": t_b, "sequential_ms": t_s,
+            "instance_steps_per_s_batched": isteps / (t_b / 1000.0),
+            "instance_steps_per_s_sequential": isteps / (t_s / 1000.0),
+            "projected_full_run_s_batched": t_b / 1000.0 * 1000 / steps,
+            "smallest_instance": {"n": m0, "final_energy": e_final, "ground_energy": float(gmin),
+                                  "ground_state_overlap": float(p[ground].sum())}}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(a):
     import torch
@@ -363,6 +422,7 @@ def run_ours(a):
         del st
         torch.cuda.empty_cache()
         secondary["variational_adjoint"] = variational_adjoint()
+        secondary["adiabatic_batch"] = adiabatic_batch()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "fused.h"
 #include "plan.h"
 #include "tiled.h"
 
@@ -23,13 +24,13 @@ static qs_status run_unfused(qs_state *s, const std::vector<LGate> &gates, const
 
 qs_status run_gates(qs_state *s, std::vector<LGate> &gates, int mode, const qs_opts *opts,
                     const double *params_dev, int n_params) {
-    (void)opts;
     switch (mode) {
     case QS_MODE_UNFUSED:
         return run_unfused(s, gates, params_dev, n_params);
+    case QS_MODE_FUSED_TC:
+        return run_fused(s, gates, opts ? opts->fuse_qubits : 5, params_dev, n_params);
     case QS_MODE_AUTO:
     case QS_MODE_TILED:
-    case QS_MODE_FUSED_TC:
     default:
         return run_tiled(s, gates, params_dev, n_params);
     }
