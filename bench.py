@@ -313,6 +313,37 @@ def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
                                   "ground_state_overlap": float(p[ground].sum())}}
 
 
+def fused_tc(steps: int = 2) -> dict:
+    """Random-layer circuit (20 layers, seed 3) at n = 30 in complex64: gates fused
+    into 5-qubit blocks applied as 3xTF32 tensor-core contractions, against the
+    tiled CUDA-core passes on the same state."""
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    n = 30
+    gates = qi.random_layer_circuit(n, 20, seed=3)
+    st = qsim.State(n, dtype="c64")
+    out = {}
+    for mode in ("fused", "tiled"):
+        t = _time_cuda(lambda: st.init_basis(0).apply(gates, mode=mode), steps, warmup=1)
+        qsim.profile_collect()
+        qsim.profile_enable(True)
+        st.init_basis(0).apply(gates, mode=mode)
+        torch.cuda.synchronize()
+        qsim.profile_enable(False)
+        prof = qsim.profile_collect()
+        key = "fused_tc" if mode == "fused" else "tiled"
+        ms, launches, nbytes, nflops = prof[key]
+        out[mode] = {"ms_per_circuit": t, "gate_apps_per_s": len(gates) / (t / 1000.0),
+                     "passes": launches, "avg_pass_ms": ms / max(1, launches),
+                     "hbm_GBps": nbytes / (ms / 1000.0) / 1e9 if ms else None,
+                     "TFLOPs_algorithmic": nflops / (ms / 1000.0) / 1e12 if ms else None}
+    del st
+    torch.cuda.empty_cache()
+    out["workload"] = "random-layer circuit, 20 layers, seed 3, n=30, complex64"
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(a):
     import torch
@@ -423,6 +454,7 @@ def run_ours(a):
         torch.cuda.empty_cache()
         secondary["variational_adjoint"] = variational_adjoint()
         secondary["adiabatic_batch"] = adiabatic_batch()
+        secondary["fused_tc"] = fused_tc()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
