@@ -167,6 +167,28 @@ qs_status qs_apply_gates(qs_state *s, const qs_gate *gates, size_t count, const 
 qs_status qs_apply_gates_batched(qs_state *s, const qs_gate *gates, size_t count,
                                  const double *params_dev, int n_params, const qs_opts *opts);
 
+/* ---------------------------------------------------------------- plans (CUDA graphs) */
+/* A gate queue prepared for repeated execution on one state (no counterpart in
+   the paper, which dispatches every gate on every execution). The gates are
+   validated and lowered once; the strategy is opts->mode, or, with opts NULL
+   or QS_MODE_AUTO and autotune = 1, the fastest of the tiled passes, fused
+   tensor-core blocks (width 5 and 4; complex64, n >= 11) and the one-gate-
+   per-pass kernels, timed once on a scratch copy of the state (skipped, with
+   the tiled passes chosen, when no copy fits) and remembered per circuit
+   shape for the process. The kernel sequence is captured in a CUDA graph.
+   params_dev/n_params as in qs_apply_gates_batched (the pointer is captured:
+   execute reads the table's current contents). */
+typedef struct qs_plan qs_plan;
+qs_status qs_plan_create(qs_state *s, const qs_gate *gates, size_t count, const double *params_dev, int n_params,
+                         const qs_opts *opts, int autotune, qs_plan **out);
+/* Replay the captured graph on the state's stream (asynchronous). */
+qs_status qs_plan_execute(qs_plan *p);
+/* Chosen mode and fusion width, the autotuner's best time in ms (-1 if not
+   tuned) and the number of graph nodes; NULL outputs are skipped. */
+qs_status qs_plan_info(const qs_plan *p, int *mode, int *fuse_qubits, double *tuned_ms, size_t *graph_nodes);
+/* Release the plan (the state is not touched). NULL is a no-op. */
+qs_status qs_plan_destroy(qs_plan *p);
+
 /* ---------------------------------------------------------------- read-out */
 /* |psi_x|^2 for every batch member, FP64, index = b * 2^n + x (qubit 0 = MSB of x).
    out: host (on_device = 0) or device pointer to batch * 2^n doubles. */

@@ -7,6 +7,7 @@
 // between stages), and store back once. HBM traffic per pass: one read and one
 // write of the state, whatever the number of gates.
 #include <algorithm>
+#include <cstring>
 
 #include "device.cuh"
 #include "internal.h"
@@ -480,10 +481,24 @@ static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p) {
         configured[dev] = 1;
     }
     const uint64_t grid = std::min<uint64_t>(p.total_tiles, (uint64_t)blocks_per_sm[dev]);
+    if (grid == 0) return QS_OK;
     ProfScope _ps(s->stream, KC_TILED);
     tiled_kernel<R, RB><<<(unsigned)grid, kTileThreads, smem, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
+}
+
+// one-time per-device kernel attributes (done before any graph capture)
+qs_status tiled_configure(qs_state *s) {
+    TileParams<float> pf;
+    TileParams<double> pd;
+    std::memset(&pf, 0, sizeof(pf));
+    std::memset(&pd, 0, sizeof(pd));
+    pf.k = tile_bits(QS_C64);
+    pd.k = tile_bits(QS_C128);
+    // total_tiles = 0: the launches configure the attributes and do no work
+    QS_TRY(launch_tiled_t<float>(s, pf));
+    return launch_tiled_t<double>(s, pd);
 }
 
 qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) { return launch_tiled_t<float>(s, p); }

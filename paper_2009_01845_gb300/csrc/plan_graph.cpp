@@ -1,0 +1,296 @@
+// Execution plans: a gate queue lowered once, its strategy chosen by timing
+// (autotuner), and its kernel sequence captured in a CUDA graph that is
+// replayed on the state's stream. No counterpart in the paper (its circuits
+// are re-dispatched op by op); it removes host planning and launch overhead
+// from repeated executions.
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "plan.h"
+#include "prof.h"
+#include "tiled.h"
+
+struct qs_plan {
+    qs_state *s = nullptr;
+    std::vector<qsim::LGate> gates;
+    const double *params = nullptr;
+    int n_params = 0;
+    qs_opts opts{};
+    int mode = QS_MODE_TILED;
+    double tuned_ms = -1.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t nodes = 0;
+};
+
+namespace qsim {
+
+const char *last_error();
+qs_status tiled_configure(qs_state *s);
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune_cache;  // shape key -> (mode, fuse width)
+
+// a key for the circuit's shape: sizes, dtype, and every gate's kind and bits
+std::string shape_key(const qs_state *s, const std::vector<LGate> &G) {
+    std::string k = std::to_string(s->n) + "/" + std::to_string(s->batch) + "/" + std::to_string(s->dtype) + ":";
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        h ^= v;
+        h *= 1099511628211ull;
+    };
+    for (const LGate &g : G) {
+        mix((uint64_t)g.kind);
+        mix(g.cmask);
+        for (int j = 0; j < g.k; ++j) mix((uint64_t)g.tbit[j]);
+        mix((uint64_t)(g.param_index + 1));
+    }
+    return k + std::to_string(G.size()) + ":" + std::to_string(h);
+}
+
+size_t ptab_need(const qs_state *s, const std::vector<LGate> &G) {
+    size_t np = 0;
+    for (const LGate &g : G) np += g.param_index >= 0;
+    return (s->dtype == QS_C64 ? 8 : 16) * 4 * np * (size_t)s->batch;
+}
+
+qs_status run_mode(qs_state *s, std::vector<LGate> &G, int mode, int width, const double *params, int n_params) {
+    qs_opts o{};
+    o.mode = mode;
+    o.fuse_qubits = width;
+    return run_gates(s, G, mode, &o, params, n_params);
+}
+
+// time one strategy on a scratch state holding a copy of s's amplitudes
+qs_status time_mode(qs_state *scratch, std::vector<LGate> &G, int mode, int width, const double *params,
+                    int n_params, double *ms) {
+    cudaEvent_t a, b;
+    QS_CUDA_TRY(cudaEventCreate(&a));
+    QS_CUDA_TRY(cudaEventCreate(&b));
+    qs_status st = run_mode(scratch, G, mode, width, params, n_params);  // warm-up (and buffers)
+    if (st == QS_OK) {
+        cudaEventRecord(a, scratch->stream);
+        st = run_mode(scratch, G, mode, width, params, n_params);
+        cudaEventRecord(b, scratch->stream);
+        cudaError_t e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e != cudaSuccess && st == QS_OK) st = cuda_status(e, "autotune timing");
+        *ms = t;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+}  // namespace
+
+static qs_status autotune(qs_plan *p) {
+    qs_state *s = p->s;
+    const std::string key = shape_key(s, p->gates);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->mode = it->second.first;
+            p->opts.fuse_qubits = it->second.second;
+            return QS_OK;
+        }
+    }
+    // candidates: tiled passes; fused tensor-core blocks of width 5 and 4
+    // (complex64, n >= 11); the one-gate-per-pass baseline
+    std::vector<std::pair<int, int>> cand = {{QS_MODE_TILED, 0}, {QS_MODE_UNFUSED, 0}};
+    if (s->dtype == QS_C64 && s->n >= 11) {
+        cand.push_back({QS_MODE_FUSED_TC, 5});
+        cand.push_back({QS_MODE_FUSED_TC, 4});
+    }
+    const size_t bytes = ((size_t)s->batch << s->n) * (s->dtype == QS_C64 ? 8 : 16);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    if (bytes > free_b / 2) {  // no room for a scratch copy: keep the tiled default
+        p->mode = QS_MODE_TILED;
+        return QS_OK;
+    }
+    qs_state scratch = *s;
+    scratch.owns = false;
+    scratch.scratch = nullptr;
+    scratch.scratch_doubles = 0;
+    scratch.host_pinned = nullptr;
+    scratch.host_pinned_doubles = 0;
+    scratch.gtab = nullptr;
+    scratch.gtab_bytes = 0;
+    scratch.ptab = nullptr;
+    scratch.ptab_bytes = 0;
+    scratch.itab = nullptr;
+    scratch.itab_bytes = 0;
+    scratch.ms = s->n;
+    QS_CUDA_TRY(cudaMalloc(&scratch.data, bytes));
+    qs_status st = QS_OK;
+    if (s->ms == s->n) {
+        const cudaError_t e = cudaMemcpyAsync(scratch.data, s->data, bytes, cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) st = cuda_status(e, "autotune copy");
+    }
+    double best = 1e300;
+    int best_mode = QS_MODE_TILED, best_w = 0;
+    for (auto &c : cand) {
+        if (st != QS_OK) break;
+        double ms = 0.0;
+        st = time_mode(&scratch, p->gates, c.first, c.second, p->params, p->n_params, &ms);
+        if (st == QS_OK && ms < best) {
+            best = ms;
+            best_mode = c.first;
+            best_w = c.second;
+        }
+    }
+    cudaStreamSynchronize(s->stream);
+    cudaFree(scratch.data);
+    if (scratch.scratch) cudaFree(scratch.scratch);
+    if (scratch.gtab) cudaFree(scratch.gtab);
+    if (scratch.ptab) cudaFree(scratch.ptab);
+    if (scratch.host_pinned) cudaFreeHost(scratch.host_pinned);
+    if (scratch.itab) cudaFree(scratch.itab);
+    if (st != QS_OK) return st;
+    p->mode = best_mode;
+    p->opts.fuse_qubits = best_w;
+    p->tuned_ms = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {best_mode, best_w};
+    return QS_OK;
+}
+
+static qs_status capture(qs_plan *p) {
+    qs_state *s = p->s;
+    // size the per-member table before capturing (no allocation while capturing)
+    const size_t need = ptab_need(s, p->gates);
+    if (need && s->ptab_bytes < need) {
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (s->ptab) cudaFree(s->ptab);
+        s->ptab = nullptr;
+        s->ptab_bytes = 0;
+        QS_CUDA_TRY(cudaMalloc(&s->ptab, need));
+        s->ptab_bytes = need;
+    }
+    if (need) QS_TRY(ensure_gtab(s, (s->dtype == QS_C64 ? 8 : 16) * 4 * (size_t)s->batch));
+    QS_TRY(tiled_configure(s));
+    cudaStream_t cap = nullptr;
+    QS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = s->stream;
+    s->stream = cap;
+    prof_suspend(true);
+    qs_status st = QS_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        st = cuda_status(e, "cudaStreamBeginCapture");
+    } else {
+        st = run_mode(s, p->gates, p->mode, p->opts.fuse_qubits, p->params, p->n_params);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        if (st == QS_OK && e != cudaSuccess) st = cuda_status(e, "cudaStreamEndCapture");
+        if (st == QS_OK) {
+            p->graph = g;
+            e = cudaGraphInstantiate(&p->exec, g, 0);
+            if (e != cudaSuccess) st = cuda_status(e, "cudaGraphInstantiate");
+            cudaGraphGetNodes(g, nullptr, &p->nodes);
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    prof_suspend(false);
+    s->stream = saved;
+    cudaStreamDestroy(cap);
+    return st;
+}
+
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" {
+
+qs_status qs_plan_create(qs_state *s, const qs_gate *gates, size_t count, const double *params_dev, int n_params,
+                         const qs_opts *opts, int autotune_flag, qs_plan **out) {
+    try {
+        clear_error();
+        if (!s || !out) {
+            set_error("null state or output");
+            return QS_ERR_ARG;
+        }
+        *out = nullptr;
+        if (count && !gates) {
+            set_error("null gate array");
+            return QS_ERR_ARG;
+        }
+        qs_plan *p = new qs_plan();
+        p->s = s;
+        p->params = params_dev;
+        p->n_params = n_params;
+        if (opts) p->opts = *opts;
+        p->mode = opts && opts->mode != QS_MODE_AUTO ? opts->mode : QS_MODE_TILED;
+        p->gates.resize(count);
+        qs_status st = QS_OK;
+        for (size_t i = 0; i < count && st == QS_OK; ++i) {
+            st = lower_gate(s->n, gates[i], &p->gates[i]);
+            const int pi = p->gates[i].param_index;
+            if (st == QS_OK && pi >= 0) {
+                const int kd = p->gates[i].kind;
+                if (!params_dev || pi >= n_params ||
+                    (kd != QS_GATE_RX && kd != QS_GATE_RY && kd != QS_GATE_RZ && kd != QS_GATE_U1 &&
+                     kd != QS_GATE_CU1)) {
+                    set_error("gate %zu: bad batched parameter", i);
+                    st = QS_ERR_ARG;
+                }
+            }
+        }
+        if (st == QS_OK && autotune_flag && (!opts || opts->mode == QS_MODE_AUTO)) st = autotune(p);
+        if (st == QS_OK) st = capture(p);
+        if (st != QS_OK) {
+            if (p->exec) cudaGraphExecDestroy(p->exec);
+            if (p->graph) cudaGraphDestroy(p->graph);
+            delete p;
+            return st;
+        }
+        *out = p;
+        return QS_OK;
+    } catch (...) {
+        set_error("internal error");
+        return QS_ERR_CUDA;
+    }
+}
+
+qs_status qs_plan_execute(qs_plan *p) {
+    if (!p || !p->exec) {
+        set_error("null plan");
+        return QS_ERR_ARG;
+    }
+    QS_CUDA_TRY(cudaGraphLaunch(p->exec, p->s->stream));
+    return QS_OK;
+}
+
+qs_status qs_plan_info(const qs_plan *p, int *mode, int *fuse_qubits, double *tuned_ms, size_t *graph_nodes) {
+    if (!p) {
+        set_error("null plan");
+        return QS_ERR_ARG;
+    }
+    if (mode) *mode = p->mode;
+    if (fuse_qubits) *fuse_qubits = p->opts.fuse_qubits;
+    if (tuned_ms) *tuned_ms = p->tuned_ms;
+    if (graph_nodes) *graph_nodes = p->nodes;
+    return QS_OK;
+}
+
+qs_status qs_plan_destroy(qs_plan *p) {
+    if (!p) return QS_OK;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    delete p;
+    return QS_OK;
+}
+
+}  // extern "C"

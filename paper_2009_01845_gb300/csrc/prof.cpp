@@ -40,7 +40,9 @@ cudaEvent_t take() {
 }
 }  // namespace
 
-bool prof_enabled() { return g_on.load(std::memory_order_relaxed); }
+thread_local bool t_suspended = false;
+bool prof_enabled() { return g_on.load(std::memory_order_relaxed) && !t_suspended; }
+void prof_suspend(bool on) { t_suspended = on; }
 
 void prof_add_work(int c, double bytes, double flops) {
     std::lock_guard<std::mutex> lk(g_mu);

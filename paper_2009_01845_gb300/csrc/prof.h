@@ -22,6 +22,8 @@ enum KClass {
 };
 
 bool prof_enabled();
+// suspend launch accounting on this thread (while a CUDA graph is captured)
+void prof_suspend(bool on);
 // record the start/end of one launch of class c on stream st
 void prof_begin(cudaStream_t st, int c);
 void prof_end(cudaStream_t st, int c);

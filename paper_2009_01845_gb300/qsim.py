@@ -80,6 +80,10 @@ _SIGS = {
                              ctypes.c_double, ctypes.c_int], None),
     "qs_adiabatic_evolve_batch": ([P, P, ctypes.c_size_t, P, P, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int], None),
+    "qs_plan_create": ([P, P, ctypes.c_size_t, P, ctypes.c_int, P, ctypes.c_int, P], None),
+    "qs_plan_execute": ([P], None),
+    "qs_plan_info": ([P, P, P, P, P], None),
+    "qs_plan_destroy": ([P], None),
     "qs_profile_enable": ([ctypes.c_int], None),
     "qs_profile_collect": ([P, P, P, P, ctypes.c_int], None),
     "qs_profile_class_name": ([ctypes.c_int], ctypes.c_char_p),
@@ -403,3 +407,45 @@ def energy_function():
             return g_energy[:, None] * grad, None
 
     return _Energy
+
+
+# ------------------------------------------------------------------ plans
+class Plan:
+    """A gate queue captured in a CUDA graph for one state (qs_plan_*)."""
+
+    def __init__(self, state: State, gates, mode: str = "auto", autotune: bool = True, fuse_qubits: int = 0,
+                 param_index=None, params=None):
+        self.state = state
+        self.lib = state.lib
+        arr, keep = marshal_gates(gates, param_index)
+        o = opts(mode, 0, fuse_qubits)
+        pp = ctypes.c_void_p(params.data_ptr()) if params is not None else None
+        npar = int(params.shape[1]) if params is not None else 0
+        self._params = params
+        h = ctypes.c_void_p()
+        _check(self.lib.qs_plan_create(state.handle, arr, len(gates), pp, npar, ctypes.byref(o),
+                                       1 if autotune else 0, ctypes.byref(h)))
+        del keep
+        self.handle = h
+
+    def execute(self):
+        _check(self.lib.qs_plan_execute(self.handle))
+        return self.state
+
+    def info(self) -> dict:
+        m, w, t, nodes = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_size_t()
+        _check(self.lib.qs_plan_info(self.handle, ctypes.byref(m), ctypes.byref(w), ctypes.byref(t),
+                                     ctypes.byref(nodes)))
+        name = {v: k for k, v in MODE.items()}[m.value]
+        return {"mode": name, "fuse_qubits": w.value, "tuned_ms": t.value, "graph_nodes": nodes.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.qs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
