@@ -261,6 +261,148 @@ __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, con
     __syncthreads();
 }
 
+// acc + c * v on both components: one packed FMA for float pairs
+__device__ __forceinline__ float2 fma_c2(float c, float2 v, float2 acc) {
+    uint64_t out;
+    const float2 cc = make_float2(c, c);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(out)
+        : "l"(*reinterpret_cast<const uint64_t *>(&cc)), "l"(*reinterpret_cast<const uint64_t *>(&v)),
+          "l"(*reinterpret_cast<const uint64_t *>(&acc)));
+    return *reinterpret_cast<float2 *>(&out);
+}
+__device__ __forceinline__ double2 fma_c2(double c, double2 v, double2 acc) {
+    return make_double2(fma(c, v.x, acc.x), fma(c, v.y, acc.y));
+}
+
+// scaled real rotation on register bit J (see TileRotForm)
+template <typename R, int RB, int J>
+__device__ __forceinline__ void rot_reg(V<R> *a, R c, int form) {
+    if (form == ROT_TAN) {
+#pragma unroll
+        for (int r = 0; r < (1 << RB); ++r) {
+            if (r & (1 << J)) continue;
+            const V<R> x = a[r], y = a[r | (1 << J)];
+            a[r] = fma_c2(-c, y, x);
+            a[r | (1 << J)] = fma_c2(c, x, y);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < (1 << RB); ++r) {
+            if (r & (1 << J)) continue;
+            const V<R> x = a[r], y = a[r | (1 << J)];
+            a[r] = fma_c2(-c, x, y);
+            a[r | (1 << J)] = fma_c2(c, y, x);
+        }
+    }
+}
+
+template <typename R, int RB>
+__device__ __forceinline__ void dispatch_rot(V<R> *a, int j, R c, int form) {
+    switch (j) {
+    case 0: rot_reg<R, RB, 0>(a, c, form); break;
+    case 1: rot_reg<R, RB, 1>(a, c, form); break;
+    case 2: rot_reg<R, RB, 2>(a, c, form); break;
+    case 3: rot_reg<R, RB, 3>(a, c, form); break;
+    default:
+        if constexpr (RB > 4) rot_reg<R, RB, 4>(a, c, form);
+        break;
+    }
+}
+
+// Value of an outside-only factor for this tile.
+template <typename R>
+__device__ __forceinline__ V<R> outside_factor(const TileDFac<R> &d, uint64_t tbase) {
+    if (d.type == DF_BIT) return (tbase & d.tmask) ? d.v1 : d.v0;
+    return (tbase & d.mo) == d.mo ? d.v0 : mkc<R>(1, 0);
+}
+
+// A diagonal block (TOP_DBLOCK). The planner folded the factors on register
+// bits alone into constants C[0] (base) and C[1 + j] (ratio applied when
+// register bit j is 1) and a register flip mask; the factor table holds, in
+// order, `no` factors on outside bits alone (a per-tile product, computed by
+// warp 0), factors involving thread bits, and `np` factors on two or more
+// register bits. Per thread: base and ratios, then each register's phase as
+// base times the ratios of its set bits (prefix products shared by the
+// compiler), times sign flips, times the remaining pair factors.
+template <typename R, int RB>
+__device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, const TileOp &op, uint64_t tbase,
+                                           uint32_t lt, V<R> *s_out, int parity) {
+    constexpr int NR = 1 << RB;
+    const V<R> *C = &p.mat[op.m];
+    const int f0 = (int)op.mo, nf = op.b, np = op.a, no = op.gl;
+    V<R> base = C[0];
+    V<R> u[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) u[j] = C[1 + j];
+    uint32_t flip = (uint32_t)op.tmask;
+    if (no > 0) {
+        const int lane = threadIdx.x & 31;
+        if ((threadIdx.x >> 5) == 0) {
+            V<R> v = mkc<R>(1, 0);
+            for (int f = f0 + lane; f < f0 + no; f += 32) v = cmul<R>(v, outside_factor<R>(p.dfac[f], tbase));
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                V<R> w;
+                w.x = __shfl_down_sync(0xffffffffu, v.x, off);
+                w.y = __shfl_down_sync(0xffffffffu, v.y, off);
+                v = cmul<R>(v, w);
+            }
+            if (lane == 0) s_out[parity] = v;
+        }
+        __syncthreads();
+        base = cmul<R>(base, s_out[parity]);
+    }
+    // thread and mixed factors (two independent product chains)
+    V<R> b2 = mkc<R>(1, 0);
+    bool general = false;
+    for (int f = f0 + no; f < f0 + nf; ++f) {
+        const TileDFac<R> &d = p.dfac[f];
+        if (d.type == DF_BIT) {
+            const V<R> v = (lt & (uint32_t)d.tmask) ? d.v1 : d.v0;
+            if ((f - f0) & 1) b2 = cmul<R>(b2, v);
+            else base = cmul<R>(base, v);
+            continue;
+        }
+        if ((tbase & d.mo) != d.mo || (lt & d.mt) != d.mt) continue;
+        if (f >= f0 + nf - np) {                  // two or more register bits
+            if (d.a) flip ^= (uint32_t)d.tmask;
+            else general = true;
+        } else if (d.mr == 0) {
+            if ((f - f0) & 1) b2 = cmul<R>(b2, d.v0);
+            else base = cmul<R>(base, d.v0);
+        } else {
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+                if (d.mr == (1u << j)) u[j] = cmul<R>(u[j], d.v0);
+        }
+    }
+    base = cmul<R>(base, b2);
+#pragma unroll
+    for (int hb = 0; hb < NR / 8; ++hb) {
+        V<R> q = base;
+#pragma unroll
+        for (int j = 3; j < RB; ++j)
+            if ((hb >> (j - 3)) & 1) q = cmul<R>(q, u[j]);
+#pragma unroll
+        for (int lo = 0; lo < 8; ++lo) {
+            const int r = hb * 8 + lo;
+            V<R> ph = q;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if ((lo >> j) & 1) ph = cmul<R>(ph, u[j]);
+            if ((flip >> r) & 1u) ph = mkc<R>(-ph.x, -ph.y);
+            if (general)
+                for (int f = f0 + nf - np; f < f0 + nf; ++f) {
+                    const TileDFac<R> &d = p.dfac[f];
+                    if (!d.a && ((d.tmask >> r) & 1ull) && (tbase & d.mo) == d.mo && (lt & d.mt) == d.mt)
+                        ph = cmul<R>(ph, d.v0);
+                }
+            a[r] = cmul<R>(a[r], ph);
+        }
+    }
+}
+
 template <int RB>
 __device__ __forceinline__ uint64_t reg_offset(int r, const uint64_t *g) {
     uint64_t o = 0;
@@ -279,7 +421,9 @@ __device__ __forceinline__ uint32_t reg_local(int r, const uint32_t *l) {
     return o;
 }
 
-template <typename R, int RB>
+// FULL = false compiles a lean kernel without the rarely used ops (4x4 gates,
+// swaps, Ising phases, gradients): less code, fewer instruction-fetch stalls.
+template <typename R, int RB, bool FULL>
 __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
     tiled_kernel(V<R> *__restrict__ psi, const __grid_constant__ TileParams<R> p) {
     constexpr int NR = 1 << RB;
@@ -289,10 +433,12 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
     __shared__ double s_g[16];
     __shared__ double s_eo;
     __shared__ V<R> s_qp[NR];
+    __shared__ V<R> s_dout[2];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint64_t fmask = (1ull << p.n_free) - 1ull;
     V<R> a[NR];
+    int dblocks = 0;
 
     for (uint64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
         const uint64_t tbase = ((t >> p.n_free) << p.n) | expand_bits(t & fmask, p.tins);
@@ -385,15 +531,67 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                     }
                     break;
                 case TOP_DENSE2_RR:
-                    if (ok) dispatch_dense2<R, RB>(a, op.a, op.b, M, mr);
+                    if constexpr (FULL)
+                        if (ok) dispatch_dense2<R, RB>(a, op.a, op.b, M, mr);
                     break;
                 case TOP_SWAP_RR:
-                    if (ok) dispatch_swap<R, RB>(a, op.a, op.b, mr);
+                    if constexpr (FULL)
+                        if (ok) dispatch_swap<R, RB>(a, op.a, op.b, mr);
                     break;
                 case TOP_ISING:
-                    ising_phase<R, RB>(a, p, op, st, tbase, t >> p.n_free, lane, warp, s_g, &s_eo, s_qp);
+                    if constexpr (FULL)
+                        ising_phase<R, RB>(a, p, op, st, tbase, t >> p.n_free, lane, warp, s_g, &s_eo, s_qp);
+                    break;
+                case TOP_ROTS_R: {
+                    // rotations on distinct register bits (they commute)
+#pragma unroll
+                    for (int j = 0; j < RB; ++j) {
+                        const V<R> cf = M[j];
+                        if (cf.y == (R)(ROT_TAN + 1)) {
+                            switch (j) {
+                            case 0: rot_reg<R, RB, 0>(a, cf.x, ROT_TAN); break;
+                            case 1: rot_reg<R, RB, 1>(a, cf.x, ROT_TAN); break;
+                            case 2: rot_reg<R, RB, 2>(a, cf.x, ROT_TAN); break;
+                            case 3: rot_reg<R, RB, 3>(a, cf.x, ROT_TAN); break;
+                            default: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, cf.x, ROT_TAN);
+                            }
+                        } else if (cf.y == (R)(ROT_COT + 1)) {
+                            switch (j) {
+                            case 0: rot_reg<R, RB, 0>(a, cf.x, ROT_COT); break;
+                            case 1: rot_reg<R, RB, 1>(a, cf.x, ROT_COT); break;
+                            case 2: rot_reg<R, RB, 2>(a, cf.x, ROT_COT); break;
+                            case 3: rot_reg<R, RB, 3>(a, cf.x, ROT_COT); break;
+                            default: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, cf.x, ROT_COT);
+                            }
+                        }
+                    }
+                    break;
+                }
+                case TOP_ROTS_L: {
+                    // own value in row `bit`, partner value v from lane ^ (1 << j)
+#pragma unroll
+                    for (int j = 0; j < kTileLaneBits; ++j) {
+                        const V<R> cf = M[j];
+                        if (cf.y == (R)0) continue;
+                        const int bit = (lane >> j) & 1;
+                        const R cc = bit ? cf.x : -cf.x;
+                        const bool tan_form = cf.y == (R)(ROT_TAN + 1);
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            const V<R> v = shfl_xor_c<R>(a[r], 1 << j);
+                            a[r] = tan_form ? fma_c2(cc, v, a[r]) : fma_c2(cc, a[r], v);
+                        }
+                    }
+                    break;
+                }
+                case TOP_DBLOCK:
+                    // the tile product alternates between two slots, so a block's
+                    // writer never overtakes readers of the block before
+                    diag_block<R, RB>(a, p, op, tbase, lt, s_dout, dblocks & 1);
+                    ++dblocks;
                     break;
                 case TOP_GRAD: {
+                    if constexpr (!FULL) break;
                     constexpr int H = NR / 2;
                     R acc = 0;
                     if (op.b == GEN_X || op.b == GEN_Y) {
@@ -450,7 +648,7 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
             for (int r = 0; r < NR; ++r) psi[gt | reg_offset<RB>(r, gr)] = a[r];
         }
         // ---------------- gradient partials of this tile (fixed summation order)
-        if (p.n_grad > 0) {
+        if (FULL && p.n_grad > 0) {
             __syncthreads();
             if ((int)threadIdx.x < p.n_grad) {
                 double sum = 0.0;
@@ -464,17 +662,20 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
 }
 
 template <typename R>
-static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p) {
+static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) {
     constexpr int RB = TileCfg<R>::RB;
     const size_t smem = sizeof(V<R>) << p.k;
     static int configured[64] = {0};
     const int dev = (s->device >= 0 && s->device < 64) ? s->device : 0;
     static int blocks_per_sm[64] = {0};
     if (!configured[dev]) {
-        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
         int bps = 0;
-        QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB>, kTileThreads, smem));
+        QS_CUDA_TRY(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB, true>, kTileThreads, smem));
         int sms = 0;
         QS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         blocks_per_sm[dev] = std::max(1, bps) * sms;
@@ -483,7 +684,10 @@ static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p) {
     const uint64_t grid = std::min<uint64_t>(p.total_tiles, (uint64_t)blocks_per_sm[dev]);
     if (grid == 0) return QS_OK;
     ProfScope _ps(s->stream, KC_TILED);
-    tiled_kernel<R, RB><<<(unsigned)grid, kTileThreads, smem, s->stream>>>((V<R> *)s->data, p);
+    if (full)
+        tiled_kernel<R, RB, true><<<(unsigned)grid, kTileThreads, smem, s->stream>>>((V<R> *)s->data, p);
+    else
+        tiled_kernel<R, RB, false><<<(unsigned)grid, kTileThreads, smem, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }
@@ -497,11 +701,25 @@ qs_status tiled_configure(qs_state *s) {
     pf.k = tile_bits(QS_C64);
     pd.k = tile_bits(QS_C128);
     // total_tiles = 0: the launches configure the attributes and do no work
-    QS_TRY(launch_tiled_t<float>(s, pf));
-    return launch_tiled_t<double>(s, pd);
+    QS_TRY(launch_tiled_t<float>(s, pf, true));
+    return launch_tiled_t<double>(s, pd, true);
 }
 
-qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) { return launch_tiled_t<float>(s, p); }
-qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) { return launch_tiled_t<double>(s, p); }
+// a pass needs the full kernel if it holds a 4x4 gate, a swap, an Ising phase or a gradient op
+template <typename R> static bool needs_full(const TileParams<R> &p) {
+    for (int st = 0; st < p.n_stages; ++st)
+        for (int o = p.st[st].op_begin; o < p.st[st].op_end; ++o) {
+            const int t = p.op[o].type;
+            if (t == TOP_DENSE2_RR || t == TOP_SWAP_RR || t == TOP_ISING || t == TOP_GRAD) return true;
+        }
+    return p.n_grad > 0;
+}
+
+qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) {
+    return launch_tiled_t<float>(s, p, needs_full(p));
+}
+qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) {
+    return launch_tiled_t<double>(s, p, needs_full(p));
+}
 
 }  // namespace qsim

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstring>
 #include <limits>
+#include <memory>
 
 #include "plan.h"
 #include "prof.h"
@@ -80,14 +81,189 @@ struct PassPlan {
 
 }  // namespace
 
-// slot[i]: per-member table slot of gate i (batched parameters) or -1
+// ------------------------------------------------------------------ entries
+// A pass is emitted from a list of entries: original gates, scaled rotations
+// (the real rotation of an uncontrolled one-qubit gate, see split_1q), and
+// diagonal blocks (products of one-bit diagonals and phase factors).
+namespace {
+
+enum EKind { E_GATE, E_ROT, E_BLOCK };
+
+struct Factor {
+    int type;        // DF_BIT or DF_PHASE
+    int bit;         // DF_BIT: index bit
+    uint64_t mask;   // DF_PHASE: required index bits
+    cd v0, v1;       // DF_BIT: diag(v0, v1); DF_PHASE: v0
+};
+
+struct Entry {
+    EKind kind;
+    int gi = -1;              // E_GATE: gate index
+    int bit = -1;             // E_ROT: index bit
+    int form = 0;             // E_ROT: ROT_TAN / ROT_COT
+    double coef = 0.0;        // E_ROT: t or u
+    std::vector<Factor> fac;  // E_BLOCK
+};
+
+// U = D_L R D_R with R = [[cos h, -sin h], [sin h, cos h]], 0 <= h <= pi/2,
+// D_R = diag(1, e^{i b1}), D_L = diag(e^{i a0}, e^{i a1}). Then
+//   h <= pi/4: R = cos h * K_tan(t = tan h),  K_tan (a, b) = (a - t b, b + t a);
+//   h >  pi/4: R = sin h * diag(-1, 1) * K_cot(u = cot h), K_cot (a, b) = (b - u a, a + u b);
+// and the scalars and signs join D_L. Returns false if U is diagonal.
+bool split_1q(const std::vector<cd> &m, cd *dr, cd *dl, int *form, double *coef) {
+    const double cg = std::abs(m[0]), sg = std::abs(m[2]);
+    if (sg == 0.0) return false;
+    const double a0 = cg > 0.0 ? std::arg(m[0]) : 0.0;
+    const double a1 = std::arg(m[2]);
+    const double b1 = std::arg(-m[1]) - a0;
+    dr[0] = 1.0;
+    dr[1] = std::polar(1.0, b1);
+    const cd l0 = std::polar(1.0, a0), l1 = std::polar(1.0, a1);
+    if (cg >= sg) {
+        *form = ROT_TAN;
+        *coef = sg / cg;
+        dl[0] = cg * l0;
+        dl[1] = cg * l1;
+    } else {
+        *form = ROT_COT;
+        *coef = cg / sg;
+        dl[0] = -sg * l0;
+        dl[1] = sg * l1;
+    }
+    return true;
+}
+
+uint64_t factor_bits(const Factor &f) { return f.type == DF_BIT ? (1ull << f.bit) : f.mask; }
+
+}  // namespace
+
+// Build the entry list of a pass. With `algebra`, uncontrolled one-qubit gates
+// become D_R, a scaled rotation and D_L; those diagonals, uncontrolled one-bit
+// diagonal gates and phase gates become factors, each placed anywhere between
+// the last and the next entry that does not commute with it (a rotation or a
+// dense gate on one of its bits), at as few points as possible (greedy interval
+// stabbing: sort by right end, cut at the first right end, repeat).
+static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::vector<GClass> &cls,
+                                        const std::vector<int> &slot, const std::vector<int> &gates, bool algebra) {
+    std::vector<Entry> base;                  // non-factor entries in order
+    std::vector<uint64_t> blocks_bits;        // bits each base entry does not commute on
+    struct PF { Factor f; int pos; };         // factor and the base position it precedes
+    std::vector<PF> pf;
+    for (int gi : gates) {
+        const LGate &g = G[gi];
+        const GClass c = cls[gi];
+        const bool plain = algebra && slot[gi] < 0 && g.cmask == 0;
+        if (plain && c == G_DENSE1) {
+            cd dr[2], dl[2];
+            int form = 0;
+            double coef = 0.0;
+            if (!split_1q(g.m, dr, dl, &form, &coef)) {
+                pf.push_back({Factor{DF_BIT, g.tbit[0], 0, g.m[0], g.m[3]}, (int)base.size()});
+                continue;
+            }
+            pf.push_back({Factor{DF_BIT, g.tbit[0], 0, dr[0], dr[1]}, (int)base.size()});
+            Entry e{E_ROT};
+            e.gi = gi;
+            e.bit = g.tbit[0];
+            e.form = form;
+            e.coef = coef;
+            base.push_back(e);
+            blocks_bits.push_back(1ull << g.tbit[0]);
+            pf.push_back({Factor{DF_BIT, g.tbit[0], 0, dl[0], dl[1]}, (int)base.size()});
+            continue;
+        }
+        if (plain && c == G_DIAG1) {
+            pf.push_back({Factor{DF_BIT, g.tbit[0], 0, g.m[0], g.m[3]}, (int)base.size()});
+            continue;
+        }
+        if (algebra && slot[gi] < 0 && c == G_PHASE) {
+            uint64_t req = g.cmask;
+            for (int j = 0; j < g.k; ++j) req |= 1ull << g.tbit[j];
+            const int K = 1 << g.k;
+            pf.push_back({Factor{DF_PHASE, -1, req, g.m[(K - 1) * K + K - 1], 0.0}, (int)base.size()});
+            continue;
+        }
+        Entry e{E_GATE};
+        e.gi = gi;
+        base.push_back(e);
+        uint64_t nb = 0;
+        if (c == G_DENSE1 || c == G_DENSE2 || c == G_SWAP)
+            for (int j = 0; j < g.k; ++j) nb |= 1ull << g.tbit[j];
+        if (c == G_GRAD || c == G_SINGLE) nb = ~0ull;  // barrier
+        blocks_bits.push_back(nb);
+    }
+    if (pf.empty()) return base;
+    // valid cut points for factor f: base positions p in (left, right], where a
+    // cut at p means "just before base[p]" (p = base.size(): after the last)
+    const int nbase = (int)base.size();
+    std::vector<std::pair<int, int>> iv(pf.size());
+    for (size_t i = 0; i < pf.size(); ++i) {
+        const uint64_t fb = factor_bits(pf[i].f);
+        int left = -1, right = nbase;
+        for (int p = pf[i].pos - 1; p >= 0; --p)
+            if (blocks_bits[p] & fb) {
+                left = p;
+                break;
+            }
+        for (int p = pf[i].pos; p < nbase; ++p)
+            if (blocks_bits[p] & fb) {
+                right = p;
+                break;
+            }
+        iv[i] = {left, right};
+    }
+    std::vector<int> order(pf.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return iv[a].second < iv[b].second; });
+    std::vector<int> cut_of(pf.size(), -1);
+    std::vector<int> cuts;
+    for (int i : order) {
+        if (cut_of[i] >= 0) continue;
+        const int c = iv[i].second;
+        cuts.push_back(c);
+        for (size_t j = 0; j < pf.size(); ++j)
+            if (cut_of[j] < 0 && iv[j].first < c && c <= iv[j].second) cut_of[j] = c;
+    }
+    std::sort(cuts.begin(), cuts.end());
+    cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+    std::vector<Entry> out;
+    size_t ci = 0;
+    for (int p = 0; p <= nbase; ++p) {
+        if (ci < cuts.size() && cuts[ci] == p) {
+            Entry b{E_BLOCK};
+            for (size_t j = 0; j < pf.size(); ++j) {  // factors in queue order
+                if (cut_of[j] != p) continue;
+                const Factor &f = pf[j].f;
+                bool merged = false;
+                if (f.type == DF_BIT)  // one-bit diagonals on the same bit multiply
+                    for (Factor &g : b.fac)
+                        if (g.type == DF_BIT && g.bit == f.bit) {
+                            g.v0 *= f.v0;
+                            g.v1 *= f.v1;
+                            merged = true;
+                            break;
+                        }
+                if (!merged) b.fac.push_back(f);
+            }
+            out.push_back(std::move(b));
+            ++ci;
+        }
+        if (p < nbase) out.push_back(std::move(base[p]));
+    }
+    return out;
+}
+
+// slot[i]: per-member table slot of gate i (batched parameters) or -1.
+// Emits one tiled pass for the gates pp.gates; *fits = false (nothing launched)
+// when the pass exceeds the descriptor's capacity.
 template <typename R>
 static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const std::vector<GClass> &cls,
                               const std::vector<int> &slot, uint32_t pm_stride, const PassPlan &pp,
-                              int force_bit, double *gpart, int *consumed) {
+                              int force_bit, double *gpart, bool *fits) {
     const int n = s->n;
     const int RB = TileCfg<R>::RB;
     const int k = RB + kTileLaneBits + kTileWarpBits;
+    *fits = true;
     // local <-> global bit maps
     int gbit[16], loc_of[64];
     for (int i = 0; i < 64; ++i) loc_of[i] = -1;
@@ -97,23 +273,26 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         if ((pp.high >> b) & 1ull) gbit[nl++] = b;
     for (int i = 0; i < k; ++i) loc_of[gbit[i]] = i;
 
-    // per-gate needed local register bits
-    const int ng = (int)pp.gates.size();
-    std::vector<uint32_t> needl(ng, 0);
-    for (int i = 0; i < ng; ++i) {
-        const uint64_t nb = need_bits(G[pp.gates[i]], cls[pp.gates[i]]);
+    const std::vector<Entry> ent = build_entries(G, cls, slot, pp.gates, force_bit < 0);
+    // per-entry needed local register bits
+    const int ne = (int)ent.size();
+    std::vector<uint32_t> needl(ne, 0);
+    for (int i = 0; i < ne; ++i) {
+        uint64_t nb = 0;
+        if (ent[i].kind == E_GATE) nb = need_bits(G[ent[i].gi], cls[ent[i].gi]);
+        if (ent[i].kind == E_ROT && ent[i].bit >= kTileLaneBits) nb = 1ull << ent[i].bit;
         for (int b = 0; b < 64; ++b)
             if ((nb >> b) & 1ull) needl[i] |= 1u << loc_of[b];
     }
     const uint32_t force_loc = force_bit >= 0 ? (1u << loc_of[force_bit]) : 0u;
     auto choose = [&](int from, uint32_t forced) {
         forced |= force_loc;
-        // forced bits plus the high local bits used soonest from op `from` on
+        // forced bits plus the high local bits used soonest from entry `from` on
         std::vector<std::pair<int, int>> rank;  // (next use, local bit)
         for (int lb = kTileLaneBits; lb < k; ++lb) {
             if ((forced >> lb) & 1u) continue;
             int nu = std::numeric_limits<int>::max();
-            for (int i = from; i < ng; ++i)
+            for (int i = from; i < ne; ++i)
                 if ((needl[i] >> lb) & 1u) {
                     nu = i;
                     break;
@@ -129,7 +308,8 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         return r;
     };
 
-    TileParams<R> P;
+    TileParams<R> &P = *new TileParams<R>();
+    std::unique_ptr<TileParams<R>> hold(&P);
     std::memset(&P, 0, sizeof(P));
     P.n = s->ms;  // member shift: tiles of member b start at b << ms
     P.k = k;
@@ -150,9 +330,9 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     P.ising_stride = s->ising_stride;
     P.nq = n;
     for (int i = 0; i < k; ++i) P.tile_mask |= 1ull << gbit[i];
-    int ngrad = 0;
+    int ngrad = 0, ndf = 0;
 
-    int nops = 0, nmat = 0, nst = 0, taken = 0;
+    int nops = 0, nmat = 0, nst = 0;
     uint32_t cur = 0;
     const uint32_t highmask = ((1u << k) - 1u) & ~((1u << kTileLaneBits) - 1u);
     auto open_stage = [&](uint32_t rset) {
@@ -194,162 +374,252 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     auto put = [&](const std::complex<double> &v) {
         P.mat[nmat++] = mkc<R>((R)v.real(), (R)v.imag());
     };
+    auto locate = [&](int b, uint8_t *tkind, uint8_t *a, uint64_t *tmask) {
+        const int lb = loc_of[b];
+        if (lb < 0) {
+            *tkind = TB_OUTSIDE;
+            *tmask = 1ull << b;
+        } else if (lb >= kTileLaneBits && ((cur >> lb) & 1u)) {
+            *tkind = TB_REG;
+            *a = (uint8_t)regidx(lb);
+        } else {
+            *tkind = TB_THREAD;
+            *tmask = 1ull << lb;
+        }
+    };
+    auto overflow = [&]() {
+        *fits = false;
+        return QS_OK;
+    };
 
-    open_stage(choose(0, needl.empty() ? 0u : needl[0]) & highmask);
-    for (int i = 0; i < ng; ++i) {
-        const LGate &g = G[pp.gates[i]];
-        const GClass c = cls[pp.gates[i]];
-        const int ops_needed = 1;
+    open_stage(choose(0, ne ? needl[0] : 0u) & highmask);
+    for (int i = 0; i < ne; ++i) {
+        const Entry &e = ent[i];
         if ((needl[i] & ~cur) != 0) {
-            if (nst >= kTileMaxStages) break;
+            if (nst >= kTileMaxStages) return overflow();
             open_stage(choose(i, needl[i]));
         }
-        const int sl = slot[pp.gates[i]];
-        if (nops + ops_needed > kTileMaxOps || nmat + (sl >= 0 ? 0 : mat_entries(c)) > kTileMaxMat) break;
-        if (c == G_GRAD && ngrad >= kTileMaxGrad) break;
+        if (nops + 1 > kTileMaxOps) return overflow();
         TileOp op;
         std::memset(&op, 0, sizeof(op));
-        const int K = 1 << g.k;
-        switch (c) {
-        case G_PHASE: {
-            op.type = TOP_PHASE;
-            uint64_t req = g.cmask;
-            for (int j = 0; j < g.k; ++j) req |= 1ull << g.tbit[j];
-            split(req, &op.mr, &op.mt, &op.mo);
-            if (sl >= 0) {
-                op.pm = 1;
-                op.m = 4 * sl;
-            } else {
-                op.m = nmat;
-                put(g.m[(K - 1) * K + (K - 1)]);
+        if (e.kind == E_ROT) {
+            // rotations on distinct bits commute: consecutive ones of one stage
+            // share an op (register bits or lane bits)
+            const int lb = loc_of[e.bit];
+            const bool lane = lb < kTileLaneBits;
+            const int j = lane ? lb : regidx(lb);
+            const uint8_t want = lane ? TOP_ROTS_L : TOP_ROTS_R;
+            const int width = lane ? kTileLaneBits : RB;
+            if (nops > P.st[nst - 1].op_begin && P.op[nops - 1].type == want &&
+                P.mat[P.op[nops - 1].m + j].y == (R)0) {
+                P.mat[P.op[nops - 1].m + j] = mkc<R>((R)e.coef, (R)(e.form + 1));
+                continue;
             }
-            break;
-        }
-        case G_DIAG1: {
-            op.type = TOP_DIAG1;
-            split(g.cmask, &op.mr, &op.mt, &op.mo);
-            const int b = g.tbit[0];
-            const int lb = loc_of[b];
-            if (lb < 0) {
-                op.tkind = TB_OUTSIDE;
-                op.tmask = 1ull << b;
-            } else if (lb >= kTileLaneBits && ((cur >> lb) & 1u)) {
-                op.tkind = TB_REG;
-                op.a = (uint8_t)regidx(lb);
-            } else {
-                op.tkind = TB_THREAD;
-                op.tmask = 1ull << lb;
-            }
-            if (sl >= 0) {
-                op.pm = 1;
-                op.m = 4 * sl;
-            } else {
-                op.m = nmat;
-                put(g.m[0]);
-                put(g.m[3]);
-            }
-            break;
-        }
-        case G_DENSE1: {
-            const int lb = loc_of[g.tbit[0]];
-            if (lb < kTileLaneBits) {
-                op.type = TOP_DENSE1_L;
-                op.a = (uint8_t)lb;
-            } else {
-                op.type = TOP_DENSE1_R;
-                op.a = (uint8_t)regidx(lb);
-            }
-            split(g.cmask, &op.mr, &op.mt, &op.mo);
-            if (sl >= 0) {
-                op.pm = 1;
-                op.m = 4 * sl;
-            } else {
-                op.m = nmat;
-                for (int e = 0; e < 4; ++e) put(g.m[e]);
-            }
-            break;
-        }
-        case G_DENSE2:
-        case G_SWAP: {
-            int A = regidx(loc_of[g.tbit[0]]), B = regidx(loc_of[g.tbit[1]]);
-            op.type = c == G_SWAP ? TOP_SWAP_RR : TOP_DENSE2_RR;
-            split(g.cmask, &op.mr, &op.mt, &op.mo);
-            if (c == G_DENSE2) {
-                // local index l = 2*bit(A) + bit(B); with A > B swap the roles
-                // by exchanging local indices 1 and 2 on both sides
-                op.m = nmat;
-                const bool sw = A > B;
-                for (int r = 0; r < 4; ++r)
-                    for (int cc = 0; cc < 4; ++cc) {
-                        auto perm = [&](int l) { return sw ? (((l & 1) << 1) | (l >> 1)) : l; };
-                        put(g.m[perm(r) * 4 + perm(cc)]);
+            if (nmat + width > kTileMaxMat) return overflow();
+            op.type = want;
+            op.m = nmat;
+            for (int x = 0; x < width; ++x) put(cd(0.0, 0.0));
+            P.mat[op.m + j] = mkc<R>((R)e.coef, (R)(e.form + 1));
+        } else if (e.kind == E_BLOCK) {
+            // constants (base, per-register-bit ratios, register flip mask) for
+            // the factors on register bits alone; the others go to the factor
+            // table: outside-only first, then thread/mixed, pairs last
+            cd cbase = 1.0;
+            std::vector<cd> cu(RB, cd(1.0));
+            uint32_t cflip = 0;
+            std::vector<TileDFac<R>> outside, single, pair;
+            auto reg_pattern = [&](uint8_t mr) {
+                uint64_t pat = 0;
+                for (int r = 0; r < (1 << RB); ++r)
+                    if ((r & mr) == mr) pat |= 1ull << r;
+                return pat;
+            };
+            for (const Factor &f : e.fac) {
+                TileDFac<R> d;
+                std::memset(&d, 0, sizeof(d));
+                d.type = (uint8_t)f.type;
+                if (f.type == DF_BIT) {
+                    locate(f.bit, &d.tkind, &d.a, &d.tmask);
+                    if (d.tkind == TB_REG) {
+                        cbase *= f.v0;
+                        cu[d.a] *= f.v1 / f.v0;
+                        continue;
                     }
+                    d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
+                    d.v1 = mkc<R>((R)f.v1.real(), (R)f.v1.imag());
+                    (d.tkind == TB_OUTSIDE ? outside : single).push_back(d);
+                } else {
+                    split(f.mask, &d.mr, &d.mt, &d.mo);
+                    const int nr = __builtin_popcount(d.mr);
+                    if (d.mt == 0 && d.mo == 0) {        // register bits alone
+                        if (nr == 0) {
+                            cbase *= f.v0;
+                        } else if (nr == 1) {
+                            cu[__builtin_ctz(d.mr)] *= f.v0;
+                        } else if (f.v0 == cd(-1.0, 0.0)) {
+                            cflip ^= (uint32_t)reg_pattern(d.mr);
+                        } else {
+                            d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
+                            d.tmask = reg_pattern(d.mr);
+                            pair.push_back(d);
+                        }
+                        continue;
+                    }
+                    d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
+                    if (d.mr == 0 && d.mt == 0) {         // outside bits alone
+                        outside.push_back(d);
+                        continue;
+                    }
+                    d.tmask = reg_pattern(d.mr);
+                    d.a = f.v0 == cd(-1.0, 0.0) ? 1 : 0;  // a sign flip
+                    (nr >= 2 ? pair : single).push_back(d);
+                }
             }
-            if (A > B) std::swap(A, B);
-            op.a = (uint8_t)A;
-            op.b = (uint8_t)B;
-            break;
-        }
-        case G_ISING: {
-            op.type = TOP_ISING;
-            const double tau = g.m[0].real();
-            std::memcpy(&op.tmask, &tau, sizeof(double));
-            break;
-        }
-        case G_GRAD: {
-            op.type = TOP_GRAD;
-            op.b = (uint8_t)g.grad_gen;
-            op.gl = (uint8_t)ngrad;
-            P.gslot[ngrad++] = (uint16_t)g.grad_slot;
-            if (g.grad_gen == GEN_PROJ) {
+            const int nf = (int)(outside.size() + single.size() + pair.size());
+            if (ndf + nf > kTileMaxDFac || nf > 255 || (int)outside.size() > 255) return overflow();
+            if (nmat + 1 + RB > kTileMaxMat) return overflow();
+            op.type = TOP_DBLOCK;
+            op.m = nmat;                     // constants: base, ratios u[0..RB)
+            put(cbase);
+            for (int x = 0; x < RB; ++x) put(cu[x]);
+            op.tmask = cflip;
+            op.mo = (uint64_t)ndf;           // first factor
+            op.b = (uint8_t)nf;
+            op.a = (uint8_t)pair.size();
+            op.gl = (uint8_t)outside.size();
+            for (auto &d : outside) P.dfac[ndf++] = d;
+            for (auto &d : single) P.dfac[ndf++] = d;
+            for (auto &d : pair) P.dfac[ndf++] = d;
+        } else {
+            const LGate &g = G[e.gi];
+            const GClass c = cls[e.gi];
+            const int sl = slot[e.gi];
+            if (nmat + (sl >= 0 ? 0 : mat_entries(c)) > kTileMaxMat) return overflow();
+            if (c == G_GRAD && ngrad >= kTileMaxGrad) return overflow();
+            const int K = 1 << g.k;
+            switch (c) {
+            case G_PHASE: {
+                op.type = TOP_PHASE;
                 uint64_t req = g.cmask;
                 for (int j = 0; j < g.k; ++j) req |= 1ull << g.tbit[j];
                 split(req, &op.mr, &op.mt, &op.mo);
+                if (sl >= 0) {
+                    op.pm = 1;
+                    op.m = 4 * sl;
+                } else {
+                    op.m = nmat;
+                    put(g.m[(K - 1) * K + (K - 1)]);
+                }
                 break;
             }
-            split(g.cmask, &op.mr, &op.mt, &op.mo);
-            const int b = g.tbit[0];
-            const int lb = loc_of[b];
-            if (g.grad_gen == GEN_Z) {
-                if (lb < 0) {
-                    op.tkind = TB_OUTSIDE;
-                    op.tmask = 1ull << b;
-                } else if (lb >= kTileLaneBits && ((cur >> lb) & 1u)) {
+            case G_DIAG1: {
+                op.type = TOP_DIAG1;
+                split(g.cmask, &op.mr, &op.mt, &op.mo);
+                locate(g.tbit[0], &op.tkind, &op.a, &op.tmask);
+                if (sl >= 0) {
+                    op.pm = 1;
+                    op.m = 4 * sl;
+                } else {
+                    op.m = nmat;
+                    put(g.m[0]);
+                    put(g.m[3]);
+                }
+                break;
+            }
+            case G_DENSE1: {
+                const int lb = loc_of[g.tbit[0]];
+                if (lb < kTileLaneBits) {
+                    op.type = TOP_DENSE1_L;
+                    op.a = (uint8_t)lb;
+                } else {
+                    op.type = TOP_DENSE1_R;
+                    op.a = (uint8_t)regidx(lb);
+                }
+                split(g.cmask, &op.mr, &op.mt, &op.mo);
+                if (sl >= 0) {
+                    op.pm = 1;
+                    op.m = 4 * sl;
+                } else {
+                    op.m = nmat;
+                    for (int x = 0; x < 4; ++x) put(g.m[x]);
+                }
+                break;
+            }
+            case G_DENSE2:
+            case G_SWAP: {
+                int A = regidx(loc_of[g.tbit[0]]), B = regidx(loc_of[g.tbit[1]]);
+                op.type = c == G_SWAP ? TOP_SWAP_RR : TOP_DENSE2_RR;
+                split(g.cmask, &op.mr, &op.mt, &op.mo);
+                if (c == G_DENSE2) {
+                    // local index l = 2*bit(A) + bit(B); with A > B swap the roles
+                    // by exchanging local indices 1 and 2 on both sides
+                    op.m = nmat;
+                    const bool sw = A > B;
+                    auto perm = [&](int l) { return sw ? (((l & 1) << 1) | (l >> 1)) : l; };
+                    for (int r = 0; r < 4; ++r)
+                        for (int cc = 0; cc < 4; ++cc) put(g.m[perm(r) * 4 + perm(cc)]);
+                }
+                if (A > B) std::swap(A, B);
+                op.a = (uint8_t)A;
+                op.b = (uint8_t)B;
+                break;
+            }
+            case G_ISING: {
+                op.type = TOP_ISING;
+                const double tau = g.m[0].real();
+                std::memcpy(&op.tmask, &tau, sizeof(double));
+                break;
+            }
+            case G_GRAD: {
+                op.type = TOP_GRAD;
+                op.b = (uint8_t)g.grad_gen;
+                op.gl = (uint8_t)ngrad;
+                P.gslot[ngrad++] = (uint16_t)g.grad_slot;
+                if (g.grad_gen == GEN_PROJ) {
+                    uint64_t req = g.cmask;
+                    for (int j = 0; j < g.k; ++j) req |= 1ull << g.tbit[j];
+                    split(req, &op.mr, &op.mt, &op.mo);
+                    break;
+                }
+                split(g.cmask, &op.mr, &op.mt, &op.mo);
+                const int lb = loc_of[g.tbit[0]];
+                if (g.grad_gen == GEN_Z) {
+                    locate(g.tbit[0], &op.tkind, &op.a, &op.tmask);
+                } else if (lb < kTileLaneBits) {
+                    op.tkind = TB_THREAD;  // lane bit: shuffles
+                    op.a = (uint8_t)lb;
+                } else {
                     op.tkind = TB_REG;
                     op.a = (uint8_t)regidx(lb);
-                } else {
-                    op.tkind = TB_THREAD;
-                    op.tmask = 1ull << lb;
                 }
-            } else if (lb < kTileLaneBits) {
-                op.tkind = TB_THREAD;  // lane bit: shuffles
-                op.a = (uint8_t)lb;
-            } else {
-                op.tkind = TB_REG;
-                op.a = (uint8_t)regidx(lb);
+                break;
             }
-            break;
-        }
-        default:
-            break;
+            default:
+                break;
+            }
         }
         P.op[nops++] = op;
         P.st[nst - 1].op_end = (uint16_t)nops;
-        ++taken;
     }
     P.n_stages = nst;
     P.n_grad = ngrad;
-    *consumed = taken;
-    if (taken == 0) return QS_OK;
     if (prof_enabled()) {
-        // algorithmic flops: per touched amplitude 16 for a 2x2 complex gate,
-        // 64 for 4x4, 6 for a diagonal factor, 0 for a swap; the touched
-        // fraction is 2^-(number of required bits)
+        // algorithmic flops per amplitude: 16 for a 2x2 complex gate, 64 for 4x4,
+        // 6 for a diagonal factor, 4 for a scaled rotation, 12 for a diagonal
+        // block; scaled by the touched fraction 2^-(required bits)
         const double amps = (double)((uint64_t)s->batch << n);
         double fl = 0.0;
-        for (int i = 0; i < taken; ++i) {
-            const LGate &g = G[pp.gates[i]];
-            const GClass c = cls[pp.gates[i]];
+        for (int i = 0; i < ne; ++i) {
+            if (ent[i].kind == E_ROT) {
+                fl += 4.0 * amps;
+                continue;
+            }
+            if (ent[i].kind == E_BLOCK) {
+                fl += 12.0 * amps;
+                continue;
+            }
+            const LGate &g = G[ent[i].gi];
+            const GClass c = cls[ent[i].gi];
             int req = __builtin_popcountll(g.cmask);
             double per = 0.0;
             if (c == G_PHASE) {
@@ -451,16 +721,22 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
         }
         // complete the tile with unused high bits
         for (int b = kTileLaneBits; b < n && __builtin_popcountll(pp.high) < nh; ++b) pp.high |= 1ull << b;
-        int consumed = 0;
-        if (s->dtype == QS_C64)
-            QS_TRY(emit_and_run<float>(s, G, cls, slot, pm_stride, pp, force_bit, gpart, &consumed));
-        else
-            QS_TRY(emit_and_run<double>(s, G, cls, slot, pm_stride, pp, force_bit, gpart, &consumed));
-        if (consumed <= 0) {
-            set_error("tiled planner made no progress");
-            return QS_ERR_CUDA;
+        // emit; a pass over the descriptor's capacity is retried with a prefix of
+        // its gates (a prefix keeps every dependency)
+        while (true) {
+            bool fits = true;
+            if (s->dtype == QS_C64)
+                QS_TRY(emit_and_run<float>(s, G, cls, slot, pm_stride, pp, force_bit, gpart, &fits));
+            else
+                QS_TRY(emit_and_run<double>(s, G, cls, slot, pm_stride, pp, force_bit, gpart, &fits));
+            if (fits) break;
+            if (pp.gates.size() <= 1) {
+                set_error("tiled planner cannot fit a single gate");
+                return QS_ERR_CUDA;
+            }
+            pp.gates.resize(pp.gates.size() * 3 / 4);
         }
-        for (int i = 0; i < consumed; ++i) done[pp.gates[i]] = 1;
+        for (int gi : pp.gates) done[gi] = 1;
     }
     return QS_OK;
 }

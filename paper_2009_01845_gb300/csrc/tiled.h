@@ -30,6 +30,7 @@ constexpr int kTileMaxStages = 48;
 constexpr int kTileMaxOps = 288;
 constexpr int kTileMaxMat = 640;   // complex entries in the matrix pool
 constexpr int kTileMaxGrad = 48;   // gradient ops per pass (adjoint sweep)
+constexpr int kTileMaxDFac = 96;   // diagonal-block factors per pass
 
 // register bits per thread for each precision (c64: 32 amplitudes, c128: 16)
 template <typename R> struct TileCfg;
@@ -48,7 +49,25 @@ enum TileOpType : uint8_t {
     TOP_SWAP_RR,     // swap register bits a < b
     TOP_GRAD,        // adjoint sweep: accumulate Im<lambda|P|phi> for a generator P
     TOP_ISING,       // psi_x *= exp(-i tau E(x)), E an Ising energy (<= 2-body Z terms)
+    TOP_ROTS_R,      // scaled real rotations on register bits: mat[m + j] = (coef, form + 1) or (0, 0)
+    TOP_ROTS_L,      // the same on the 5 lane bits (warp shuffles)
+    TOP_DBLOCK,      // product of diagonal factors (see diag_block)
 };
+
+// Scaled real rotations: form 0: (a, b) <- (a - t b, b + t a) with |t| <= 1;
+// form 1: (a, b) <- (b - u a, a + u b) with |u| <= 1. The planner moves the
+// scalar and sign that make these equal to the rotation into diagonal factors.
+enum TileRotForm : uint8_t { ROT_TAN = 0, ROT_COT = 1 };
+
+// One factor of a diagonal block, located in the block's stage:
+//   DF_BIT: diag(v0, v1) on one thread bit (kind TB_THREAD, local mask tmask)
+//           or one outside bit (TB_OUTSIDE, global mask tmask);
+//   DF_PHASE: v0 where all required bits (mr register, mt thread, mo outside)
+//           are 1; for two or more register bits tmask holds the registers
+//           covered and a = 1 marks a sign flip (v0 = -1).
+// Factors on register bits alone are folded by the planner into the block's
+// constants (a base value, one ratio per register bit, a register flip mask).
+enum TileDFacType : uint8_t { DF_BIT = 0, DF_PHASE = 1 };
 
 // Generators of TOP_GRAD (b field): Pauli X, Y, Z on one target, or the
 // projector on the all-ones block of the required bits (U1/CU1).
@@ -73,6 +92,17 @@ struct TileOp {
     uint32_t m;       // first matrix-pool entry
     uint64_t mo;
     uint64_t tmask;   // TOP_DIAG1 target: thread-local mask (TB_THREAD) or global mask (TB_OUTSIDE)
+};
+
+template <typename R> struct TileDFac {
+    uint8_t type;
+    uint8_t tkind;
+    uint8_t a;
+    uint8_t mr;
+    uint32_t mt;
+    uint64_t mo;
+    uint64_t tmask;
+    V<R> v0, v1, v2;
 };
 
 struct TileStage {
@@ -105,11 +135,12 @@ template <typename R> struct TileParams {
     uint32_t ising_stride;
     int nq;
     uint64_t tile_mask;   // global bits of the tile
+    TileDFac<R> dfac[kTileMaxDFac];
     TileStage st[kTileMaxStages];
     TileOp op[kTileMaxOps];
     V<R> mat[kTileMaxMat];
 };
 
-static_assert(sizeof(TileParams<double>) <= 32000, "kernel parameter block too large");
+static_assert(sizeof(TileParams<double>) <= 32700, "kernel parameter block too large");
 
 }  // namespace qsim
