@@ -79,8 +79,11 @@ __device__ __forceinline__ void dispatch_dense1(V<R> *a, int j, V<R> m00, V<R> m
     case 1: dense1_reg<R, RB, 1>(a, m00, m01, m10, m11, mr); break;
     case 2: dense1_reg<R, RB, 2>(a, m00, m01, m10, m11, mr); break;
     case 3: dense1_reg<R, RB, 3>(a, m00, m01, m10, m11, mr); break;
+    case 4:
+        if constexpr (RB > 4) dense1_reg<R, RB, (RB > 4 ? 4 : 0)>(a, m00, m01, m10, m11, mr);
+        break;
     default:
-        if constexpr (RB > 4) dense1_reg<R, RB, 4>(a, m00, m01, m10, m11, mr);
+        if constexpr (RB > 5) dense1_reg<R, RB, (RB > 5 ? 5 : 0)>(a, m00, m01, m10, m11, mr);
         break;
     }
 }
@@ -95,12 +98,25 @@ __device__ __forceinline__ void dispatch_dense1(V<R> *a, int j, V<R> m00, V<R> m
     case 2 * 8 + 3: FN<R, RB, 2, 3>(__VA_ARGS__); break;                        \
     default:                                                                    \
         if constexpr (RB > 4) {                                                 \
+            constexpr int F = RB > 4 ? 4 : 1;                                   \
             switch (A * 8 + B) {                                                \
-            case 0 * 8 + 4: FN<R, RB, 0, 4>(__VA_ARGS__); break;                \
-            case 1 * 8 + 4: FN<R, RB, 1, 4>(__VA_ARGS__); break;                \
-            case 2 * 8 + 4: FN<R, RB, 2, 4>(__VA_ARGS__); break;                \
-            case 3 * 8 + 4: FN<R, RB, 3, 4>(__VA_ARGS__); break;                \
-            default: break;                                                     \
+            case 0 * 8 + 4: FN<R, RB, 0, F>(__VA_ARGS__); break;                \
+            case 1 * 8 + 4: FN<R, RB, 1, F>(__VA_ARGS__); break;                \
+            case 2 * 8 + 4: FN<R, RB, 2, F>(__VA_ARGS__); break;                \
+            case 3 * 8 + 4: FN<R, RB, 3, F>(__VA_ARGS__); break;                \
+            default:                                                            \
+                if constexpr (RB > 5) {                                         \
+                    constexpr int S = RB > 5 ? 5 : 2;                           \
+                    switch (A * 8 + B) {                                        \
+                    case 0 * 8 + 5: FN<R, RB, 0, S>(__VA_ARGS__); break;        \
+                    case 1 * 8 + 5: FN<R, RB, 1, S>(__VA_ARGS__); break;        \
+                    case 2 * 8 + 5: FN<R, RB, 2, S>(__VA_ARGS__); break;        \
+                    case 3 * 8 + 5: FN<R, RB, 3, S>(__VA_ARGS__); break;        \
+                    case 4 * 8 + 5: FN<R, RB, (RB > 5 ? 4 : 0), S>(__VA_ARGS__); break; \
+                    default: break;                                             \
+                    }                                                           \
+                }                                                               \
+                break;                                                          \
             }                                                                   \
         }                                                                       \
     }
@@ -139,8 +155,11 @@ __device__ __forceinline__ R dispatch_grad_xy(const V<R> *a, int j, int gen, uin
     case 0: return grad_xy_reg<R, RB, 0>(a, gen, mr);
     case 1: return grad_xy_reg<R, RB, 1>(a, gen, mr);
     case 2: return grad_xy_reg<R, RB, 2>(a, gen, mr);
+    case 3:
+        if constexpr (RB > 4) return grad_xy_reg<R, RB, (RB > 4 ? 3 : 0)>(a, gen, mr);
+        return 0;
     default:
-        if constexpr (RB > 4) return grad_xy_reg<R, RB, 3>(a, gen, mr);
+        if constexpr (RB > 5) return grad_xy_reg<R, RB, (RB > 5 ? 4 : 0)>(a, gen, mr);
         return 0;
     }
 }
@@ -206,27 +225,29 @@ __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, con
         s_qp[r] = expi<R>(-tau * q);
     }
     __syncthreads();
-    // the thread's 8 bits: lanes (local = global bits 0..4) and warp bits
-    int tg[8], tlc[8];
-    double tz[8];
+    // the thread's 5 + WB bits: lanes and warp bits
+    constexpr int WB = TileCfg<R>::WB;
+    constexpr int TB = kTileLaneBits + WB;
+    int tg[TB], tlc[TB];
+    double tz[TB];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        tg[i] = i;
-        tlc[i] = i;
+        tlc[i] = st.lloc[i];
+        tg[i] = p.gbit[st.lloc[i]];
         tz[i] = ((lane >> i) & 1) ? -1.0 : 1.0;
     }
 #pragma unroll
-    for (int w = 0; w < kTileWarpBits; ++w) {
+    for (int w = 0; w < WB; ++w) {
         tlc[5 + w] = st.wloc[w];
         tg[5 + w] = p.gbit[st.wloc[w]];
         tz[5 + w] = ((warp >> w) & 1) ? -1.0 : 1.0;
     }
     double C = *s_eo;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < TB; ++i) {
         C += s_g[tlc[i]] * tz[i];
 #pragma unroll
-        for (int j = i + 1; j < 8; ++j) C += J[tg[i] * nq + tg[j]] * tz[i] * tz[j];
+        for (int j = i + 1; j < TB; ++j) C += J[tg[i] * nq + tg[j]] * tz[i] * tz[j];
     }
     double wsum = 0.0;
     V<R> u[RB];
@@ -235,7 +256,7 @@ __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, con
         const int gj = p.gbit[st.rloc[j]];
         double wj = s_g[st.rloc[j]];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) wj += J[gj * nq + tg[i]] * tz[i];
+        for (int i = 0; i < TB; ++i) wj += J[gj * nq + tg[i]] * tz[i];
         wsum += wj;
         u[j] = expi<R>(2.0 * tau * wj);
     }
@@ -320,14 +341,14 @@ __device__ __forceinline__ V<R> outside_factor(const TileDFac<R> &d, uint64_t tb
 // A diagonal block (TOP_DBLOCK). The planner folded the factors on register
 // bits alone into constants C[0] (base) and C[1 + j] (ratio applied when
 // register bit j is 1) and a register flip mask; the factor table holds, in
-// order, `no` factors on outside bits alone (a per-tile product, computed by
-// warp 0), factors involving thread bits, and `np` factors on two or more
+// order, `no` factors on outside bits alone (a per-tile product, formed by
+// each warp), factors involving thread bits, and `np` factors on two or more
 // register bits. Per thread: base and ratios, then each register's phase as
 // base times the ratios of its set bits (prefix products shared by the
 // compiler), times sign flips, times the remaining pair factors.
 template <typename R, int RB>
 __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, const TileOp &op, uint64_t tbase,
-                                           uint32_t lt, V<R> *s_out, int parity) {
+                                           uint32_t lt) {
     constexpr int NR = 1 << RB;
     const V<R> *C = &p.mat[op.m];
     const int f0 = (int)op.mo, nf = op.b, np = op.a, no = op.gl;
@@ -335,23 +356,21 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
     V<R> u[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) u[j] = C[1 + j];
-    uint32_t flip = (uint32_t)op.tmask;
+    uint64_t flip = op.tmask;
     if (no > 0) {
+        // every warp forms the tile's product of outside factors itself (lanes
+        // over factors, then a shuffle product): no barrier
         const int lane = threadIdx.x & 31;
-        if ((threadIdx.x >> 5) == 0) {
-            V<R> v = mkc<R>(1, 0);
-            for (int f = f0 + lane; f < f0 + no; f += 32) v = cmul<R>(v, outside_factor<R>(p.dfac[f], tbase));
+        V<R> v = mkc<R>(1, 0);
+        for (int f = f0 + lane; f < f0 + no; f += 32) v = cmul<R>(v, outside_factor<R>(p.dfac[f], tbase));
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                V<R> w;
-                w.x = __shfl_down_sync(0xffffffffu, v.x, off);
-                w.y = __shfl_down_sync(0xffffffffu, v.y, off);
-                v = cmul<R>(v, w);
-            }
-            if (lane == 0) s_out[parity] = v;
+        for (int off = 16; off > 0; off >>= 1) {
+            V<R> w;
+            w.x = __shfl_xor_sync(0xffffffffu, v.x, off);
+            w.y = __shfl_xor_sync(0xffffffffu, v.y, off);
+            v = cmul<R>(v, w);
         }
-        __syncthreads();
-        base = cmul<R>(base, s_out[parity]);
+        base = cmul<R>(base, v);
     }
     // thread and mixed factors (two independent product chains)
     V<R> b2 = mkc<R>(1, 0);
@@ -366,7 +385,7 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
         }
         if ((tbase & d.mo) != d.mo || (lt & d.mt) != d.mt) continue;
         if (f >= f0 + nf - np) {                  // two or more register bits
-            if (d.a) flip ^= (uint32_t)d.tmask;
+            if (d.a) flip ^= d.tmask;
             else general = true;
         } else if (d.mr == 0) {
             if ((f - f0) & 1) b2 = cmul<R>(b2, d.v0);
@@ -391,7 +410,7 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 if ((lo >> j) & 1) ph = cmul<R>(ph, u[j]);
-            if ((flip >> r) & 1u) ph = mkc<R>(-ph.x, -ph.y);
+            if ((flip >> r) & 1ull) ph = mkc<R>(-ph.x, -ph.y);
             if (general)
                 for (int f = f0 + nf - np; f < f0 + nf; ++f) {
                     const TileDFac<R> &d = p.dfac[f];
@@ -403,6 +422,29 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
     }
 }
 
+// Shared-memory position of tile-local index j (see tiled.h): an XOR of j's
+// higher bits folded into its low bits; linear over XOR.
+template <typename R> __device__ __forceinline__ uint32_t swz(uint32_t j);
+template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t j) {
+    return j ^ (((j >> 4) ^ (j >> 8) ^ (j >> 12)) & 15u);
+}
+template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t j) {
+    return j ^ (((j >> 3) ^ (j >> 6) ^ (j >> 9) ^ (j >> 12)) & 7u);
+}
+
+// tile-local index of this thread's lane and warp bits under a stage mapping
+template <int WB>
+__device__ __forceinline__ uint32_t thread_local_index(const TileStage &st, int lane, int warp) {
+    uint32_t lt = 0;
+#pragma unroll
+    for (int i = 0; i < kTileLaneBits; ++i)
+        if ((lane >> i) & 1) lt |= 1u << st.lloc[i];
+#pragma unroll
+    for (int w = 0; w < WB; ++w)
+        if ((warp >> w) & 1) lt |= 1u << st.wloc[w];
+    return lt;
+}
+
 template <int RB>
 __device__ __forceinline__ uint64_t reg_offset(int r, const uint64_t *g) {
     uint64_t o = 0;
@@ -412,33 +454,34 @@ __device__ __forceinline__ uint64_t reg_offset(int r, const uint64_t *g) {
     return o;
 }
 
+// XOR of l[j] over the set bits j of r (swizzled positions are not disjoint)
 template <int RB>
 __device__ __forceinline__ uint32_t reg_local(int r, const uint32_t *l) {
     uint32_t o = 0;
 #pragma unroll
     for (int j = 0; j < RB; ++j)
-        if ((r >> j) & 1) o |= l[j];
+        if ((r >> j) & 1) o ^= l[j];
     return o;
 }
 
 // FULL = false compiles a lean kernel without the rarely used ops (4x4 gates,
 // swaps, Ising phases, gradients): less code, fewer instruction-fetch stalls.
 template <typename R, int RB, bool FULL>
-__global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
+__global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
     tiled_kernel(V<R> *__restrict__ psi, const __grid_constant__ TileParams<R> p) {
     constexpr int NR = 1 << RB;
+    constexpr int WB = TileCfg<R>::WB;
+    constexpr int NW = 1 << WB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V<R> *sm = reinterpret_cast<V<R> *>(smem_raw);
-    __shared__ R gsm[kTileMaxGrad][kTileThreads / 32];
+    __shared__ R gsm[kTileMaxGrad][NW];
     __shared__ double s_g[16];
     __shared__ double s_eo;
     __shared__ V<R> s_qp[NR];
-    __shared__ V<R> s_dout[2];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint64_t fmask = (1ull << p.n_free) - 1ull;
     V<R> a[NR];
-    int dblocks = 0;
 
     for (uint64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
         const uint64_t tbase = ((t >> p.n_free) << p.n) | expand_bits(t & fmask, p.tins);
@@ -447,7 +490,7 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
             const TileStage &s0 = p.st[0];
             uint64_t gt = tbase | (uint64_t)lane;
 #pragma unroll
-            for (int w = 0; w < kTileWarpBits; ++w)
+            for (int w = 0; w < WB; ++w)
                 if ((warp >> w) & 1) gt |= 1ull << p.gbit[s0.wloc[w]];
             uint64_t gr[RB];
 #pragma unroll
@@ -459,30 +502,23 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
         for (int s = 0; s < p.n_stages; ++s) {
             const TileStage &st = p.st[s];
             if (s > 0) {
+                // transpose: write under the previous mapping, read under this one
+                // (positions swizzled; swz is linear, so it applies per part)
                 const TileStage &pv = p.st[s - 1];
-                uint32_t lt = (uint32_t)lane, lr[RB];
+                uint32_t ps = swz<R>(thread_local_index<WB>(pv, lane, warp)), lr[RB];
 #pragma unroll
-                for (int w = 0; w < kTileWarpBits; ++w)
-                    if ((warp >> w) & 1) lt |= 1u << pv.wloc[w];
+                for (int j = 0; j < RB; ++j) lr[j] = swz<R>(1u << pv.rloc[j]);
 #pragma unroll
-                for (int j = 0; j < RB; ++j) lr[j] = 1u << pv.rloc[j];
-#pragma unroll
-                for (int r = 0; r < NR; ++r) sm[lt | reg_local<RB>(r, lr)] = a[r];
+                for (int r = 0; r < NR; ++r) sm[ps ^ reg_local<RB>(r, lr)] = a[r];
                 __syncthreads();
-                lt = (uint32_t)lane;
+                ps = swz<R>(thread_local_index<WB>(st, lane, warp));
 #pragma unroll
-                for (int w = 0; w < kTileWarpBits; ++w)
-                    if ((warp >> w) & 1) lt |= 1u << st.wloc[w];
+                for (int j = 0; j < RB; ++j) lr[j] = swz<R>(1u << st.rloc[j]);
 #pragma unroll
-                for (int j = 0; j < RB; ++j) lr[j] = 1u << st.rloc[j];
-#pragma unroll
-                for (int r = 0; r < NR; ++r) a[r] = sm[lt | reg_local<RB>(r, lr)];
+                for (int r = 0; r < NR; ++r) a[r] = sm[ps ^ reg_local<RB>(r, lr)];
                 __syncthreads();
             }
-            uint32_t lt = (uint32_t)lane;
-#pragma unroll
-            for (int w = 0; w < kTileWarpBits; ++w)
-                if ((warp >> w) & 1) lt |= 1u << st.wloc[w];
+            const uint32_t lt = thread_local_index<WB>(st, lane, warp);
             for (int o = st.op_begin; o < st.op_end; ++o) {
                 const TileOp &op = p.op[o];
                 const bool ok = ((tbase & op.mo) == op.mo) && ((lt & op.mt) == op.mt);
@@ -553,7 +589,8 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                             case 1: rot_reg<R, RB, 1>(a, cf.x, ROT_TAN); break;
                             case 2: rot_reg<R, RB, 2>(a, cf.x, ROT_TAN); break;
                             case 3: rot_reg<R, RB, 3>(a, cf.x, ROT_TAN); break;
-                            default: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, cf.x, ROT_TAN);
+                            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, cf.x, ROT_TAN); break;
+                            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, cf.x, ROT_TAN);
                             }
                         } else if (cf.y == (R)(ROT_COT + 1)) {
                             switch (j) {
@@ -561,7 +598,8 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                             case 1: rot_reg<R, RB, 1>(a, cf.x, ROT_COT); break;
                             case 2: rot_reg<R, RB, 2>(a, cf.x, ROT_COT); break;
                             case 3: rot_reg<R, RB, 3>(a, cf.x, ROT_COT); break;
-                            default: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, cf.x, ROT_COT);
+                            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, cf.x, ROT_COT); break;
+                            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, cf.x, ROT_COT);
                             }
                         }
                     }
@@ -585,10 +623,7 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
                     break;
                 }
                 case TOP_DBLOCK:
-                    // the tile product alternates between two slots, so a block's
-                    // writer never overtakes readers of the block before
-                    diag_block<R, RB>(a, p, op, tbase, lt, s_dout, dblocks & 1);
-                    ++dblocks;
+                    diag_block<R, RB>(a, p, op, tbase, lt);
                     break;
                 case TOP_GRAD: {
                     if constexpr (!FULL) break;
@@ -639,7 +674,7 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
             const TileStage &sl = p.st[p.n_stages - 1];
             uint64_t gt = tbase | (uint64_t)lane;
 #pragma unroll
-            for (int w = 0; w < kTileWarpBits; ++w)
+            for (int w = 0; w < WB; ++w)
                 if ((warp >> w) & 1) gt |= 1ull << p.gbit[sl.wloc[w]];
             uint64_t gr[RB];
 #pragma unroll
@@ -653,7 +688,7 @@ __global__ void __launch_bounds__(kTileThreads, TileCfg<R>::kMinBlocks)
             if ((int)threadIdx.x < p.n_grad) {
                 double sum = 0.0;
 #pragma unroll
-                for (int w = 0; w < kTileThreads / 32; ++w) sum += (double)gsm[threadIdx.x][w];
+                for (int w = 0; w < NW; ++w) sum += (double)gsm[threadIdx.x][w];
                 p.gpart[(uint64_t)p.gslot[threadIdx.x] * p.total_tiles + t] = sum;
             }
             __syncthreads();
@@ -674,8 +709,8 @@ static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) 
         QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
         int bps = 0;
-        QS_CUDA_TRY(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB, true>, kTileThreads, smem));
+        QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB, true>,
+                                                                  32 << TileCfg<R>::WB, smem));
         int sms = 0;
         QS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         blocks_per_sm[dev] = std::max(1, bps) * sms;
@@ -685,9 +720,9 @@ static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) 
     if (grid == 0) return QS_OK;
     ProfScope _ps(s->stream, KC_TILED);
     if (full)
-        tiled_kernel<R, RB, true><<<(unsigned)grid, kTileThreads, smem, s->stream>>>((V<R> *)s->data, p);
+        tiled_kernel<R, RB, true><<<(unsigned)grid, 32 << TileCfg<R>::WB, smem, s->stream>>>((V<R> *)s->data, p);
     else
-        tiled_kernel<R, RB, false><<<(unsigned)grid, kTileThreads, smem, s->stream>>>((V<R> *)s->data, p);
+        tiled_kernel<R, RB, false><<<(unsigned)grid, 32 << TileCfg<R>::WB, smem, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }

@@ -12,6 +12,8 @@
 // warps; the register set of a new stage is the needed bits plus the bits used
 // soonest afterwards (furthest-next-use eviction).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <memory>
@@ -262,7 +264,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                               int force_bit, double *gpart, bool *fits) {
     const int n = s->n;
     const int RB = TileCfg<R>::RB;
-    const int k = RB + kTileLaneBits + kTileWarpBits;
+    const int k = RB + kTileLaneBits + TileCfg<R>::WB;
     *fits = true;
     // local <-> global bit maps
     int gbit[16], loc_of[64];
@@ -273,31 +275,41 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         if ((pp.high >> b) & 1ull) gbit[nl++] = b;
     for (int i = 0; i < k; ++i) loc_of[gbit[i]] = i;
 
-    const std::vector<Entry> ent = build_entries(G, cls, slot, pp.gates, force_bit < 0);
+    // Free lanes (every pass but the adjoint sweep): dense targets, lane bits
+    // included, must be register bits; stages move lanes to any bits.
+    const bool free_lanes = force_bit < 0;
+    const std::vector<Entry> ent = build_entries(G, cls, slot, pp.gates, free_lanes);
     // per-entry needed local register bits
     const int ne = (int)ent.size();
     std::vector<uint32_t> needl(ne, 0);
     for (int i = 0; i < ne; ++i) {
         uint64_t nb = 0;
-        if (ent[i].kind == E_GATE) nb = need_bits(G[ent[i].gi], cls[ent[i].gi]);
-        if (ent[i].kind == E_ROT && ent[i].bit >= kTileLaneBits) nb = 1ull << ent[i].bit;
+        if (ent[i].kind == E_GATE) {
+            const LGate &g = G[ent[i].gi];
+            const GClass c = cls[ent[i].gi];
+            nb = need_bits(g, c);
+            if (free_lanes && (c == G_DENSE1 || (c == G_GRAD && (g.grad_gen == GEN_X || g.grad_gen == GEN_Y))))
+                nb = 1ull << g.tbit[0];
+        }
+        if (ent[i].kind == E_ROT && (free_lanes || ent[i].bit >= kTileLaneBits)) nb = 1ull << ent[i].bit;
         for (int b = 0; b < 64; ++b)
             if ((nb >> b) & 1ull) needl[i] |= 1u << loc_of[b];
     }
     const uint32_t force_loc = force_bit >= 0 ? (1u << loc_of[force_bit]) : 0u;
-    auto choose = [&](int from, uint32_t forced) {
+    const uint32_t low5 = (1u << kTileLaneBits) - 1u;
+    auto next_use = [&](int from, int lb) {
+        for (int i = from; i < ne; ++i)
+            if ((needl[i] >> lb) & 1u) return i;
+        return std::numeric_limits<int>::max();
+    };
+    // register set: forced bits plus the candidate bits used soonest from entry
+    // `from` on (furthest-next-use eviction)
+    auto choose = [&](int from, uint32_t forced, uint32_t candidates) {
         forced |= force_loc;
-        // forced bits plus the high local bits used soonest from entry `from` on
         std::vector<std::pair<int, int>> rank;  // (next use, local bit)
-        for (int lb = kTileLaneBits; lb < k; ++lb) {
-            if ((forced >> lb) & 1u) continue;
-            int nu = std::numeric_limits<int>::max();
-            for (int i = from; i < ne; ++i)
-                if ((needl[i] >> lb) & 1u) {
-                    nu = i;
-                    break;
-                }
-            rank.push_back({nu, lb});
+        for (int lb = 0; lb < k; ++lb) {
+            if (((forced >> lb) & 1u) || !((candidates >> lb) & 1u)) continue;
+            rank.push_back({next_use(from, lb), lb});
         }
         std::sort(rank.begin(), rank.end());
         uint32_t r = forced;
@@ -306,6 +318,30 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             r |= 1u << pr.second;
         }
         return r;
+    };
+    // lanes: the 5 remaining bits used soonest; ordered so that the lanes of a
+    // half-warp (complex64) / quarter-warp (complex128) have distinct residues
+    const int half = sizeof(R) == 4 ? 4 : 3;
+    auto lanes_for = [&](int from, uint32_t rset) {
+        std::vector<std::pair<int, int>> rank;
+        for (int lb = 0; lb < k; ++lb)
+            if (!((rset >> lb) & 1u)) rank.push_back({next_use(from, lb), lb});
+        std::sort(rank.begin(), rank.end());
+        std::vector<int> L;
+        for (int x = 0; x < kTileLaneBits; ++x) L.push_back(rank[x].second);
+        std::sort(L.begin(), L.end());
+        std::vector<int> best = L;
+        do {
+            bool okr = true;
+            for (int x = 0; x < half && okr; ++x)
+                for (int y = x + 1; y < half; ++y)
+                    if (L[x] % half == L[y] % half) okr = false;
+            if (okr) {
+                best = L;
+                break;
+            }
+        } while (std::next_permutation(L.begin(), L.end()));
+        return best;
     };
 
     TileParams<R> &P = *new TileParams<R>();
@@ -333,20 +369,33 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     int ngrad = 0, ndf = 0;
 
     int nops = 0, nmat = 0, nst = 0;
-    uint32_t cur = 0;
-    const uint32_t highmask = ((1u << k) - 1u) & ~((1u << kTileLaneBits) - 1u);
-    auto open_stage = [&](uint32_t rset) {
+    uint32_t cur = 0, curL = 0;
+    const uint32_t highmask = ((1u << k) - 1u) & ~low5;
+    auto open_stage = [&](uint32_t rset, const std::vector<int> &L) {
         TileStage &st = P.st[nst];
+        uint32_t lset = 0;
+        for (int x = 0; x < kTileLaneBits; ++x) {
+            st.lloc[x] = (uint8_t)L[x];
+            lset |= 1u << L[x];
+        }
         int j = 0, w = 0;
-        for (int lb = kTileLaneBits; lb < k; ++lb) {
+        for (int lb = 0; lb < k; ++lb) {
             if ((rset >> lb) & 1u)
                 st.rloc[j++] = (uint8_t)lb;
-            else
+            else if (!((lset >> lb) & 1u))
                 st.wloc[w++] = (uint8_t)lb;
         }
         st.op_begin = st.op_end = (uint16_t)nops;
         ++nst;
         cur = rset;
+        curL = lset;
+    };
+    const std::vector<int> natural = {0, 1, 2, 3, 4};
+    auto lane_index = [&](int lb) {
+        const TileStage &st = P.st[nst - 1];
+        for (int x = 0; x < kTileLaneBits; ++x)
+            if (st.lloc[x] == lb) return x;
+        return -1;
     };
     auto regidx = [&](int lb) {
         const TileStage &st = P.st[nst - 1];
@@ -364,7 +413,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             const int lb = b < n ? loc_of[b] : -1;
             if (lb < 0) {
                 *mo |= 1ull << b;
-            } else if (lb >= kTileLaneBits && ((cur >> lb) & 1u)) {
+            } else if ((cur >> lb) & 1u) {
                 *mr |= (uint8_t)(1u << regidx(lb));
             } else {
                 *mt |= 1u << lb;
@@ -379,7 +428,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         if (lb < 0) {
             *tkind = TB_OUTSIDE;
             *tmask = 1ull << b;
-        } else if (lb >= kTileLaneBits && ((cur >> lb) & 1u)) {
+        } else if ((cur >> lb) & 1u) {
             *tkind = TB_REG;
             *a = (uint8_t)regidx(lb);
         } else {
@@ -392,12 +441,18 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         return QS_OK;
     };
 
-    open_stage(choose(0, ne ? needl[0] : 0u) & highmask);
+    // the first stage reads the tile with lanes on the 5 lowest bits
+    open_stage(choose(0, (ne ? needl[0] : 0u) & highmask, highmask), natural);
     for (int i = 0; i < ne; ++i) {
         const Entry &e = ent[i];
         if ((needl[i] & ~cur) != 0) {
             if (nst >= kTileMaxStages) return overflow();
-            open_stage(choose(i, needl[i]));
+            if (free_lanes) {
+                const uint32_t rset = choose(i, needl[i], (1u << k) - 1u);
+                open_stage(rset, lanes_for(i, rset));
+            } else {
+                open_stage(choose(i, needl[i], highmask), natural);
+            }
         }
         if (nops + 1 > kTileMaxOps) return overflow();
         TileOp op;
@@ -406,8 +461,8 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             // rotations on distinct bits commute: consecutive ones of one stage
             // share an op (register bits or lane bits)
             const int lb = loc_of[e.bit];
-            const bool lane = lb < kTileLaneBits;
-            const int j = lane ? lb : regidx(lb);
+            const bool lane = !((cur >> lb) & 1u);
+            const int j = lane ? lane_index(lb) : regidx(lb);
             const uint8_t want = lane ? TOP_ROTS_L : TOP_ROTS_R;
             const int width = lane ? kTileLaneBits : RB;
             if (nops > P.st[nst - 1].op_begin && P.op[nops - 1].type == want &&
@@ -426,7 +481,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             // table: outside-only first, then thread/mixed, pairs last
             cd cbase = 1.0;
             std::vector<cd> cu(RB, cd(1.0));
-            uint32_t cflip = 0;
+            uint64_t cflip = 0;
             std::vector<TileDFac<R>> outside, single, pair;
             auto reg_pattern = [&](uint8_t mr) {
                 uint64_t pat = 0;
@@ -457,7 +512,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                         } else if (nr == 1) {
                             cu[__builtin_ctz(d.mr)] *= f.v0;
                         } else if (f.v0 == cd(-1.0, 0.0)) {
-                            cflip ^= (uint32_t)reg_pattern(d.mr);
+                            cflip ^= reg_pattern(d.mr);
                         } else {
                             d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
                             d.tmask = reg_pattern(d.mr);
@@ -528,9 +583,9 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             }
             case G_DENSE1: {
                 const int lb = loc_of[g.tbit[0]];
-                if (lb < kTileLaneBits) {
+                if (!((cur >> lb) & 1u)) {
                     op.type = TOP_DENSE1_L;
-                    op.a = (uint8_t)lb;
+                    op.a = (uint8_t)lane_index(lb);
                 } else {
                     op.type = TOP_DENSE1_R;
                     op.a = (uint8_t)regidx(lb);
@@ -585,9 +640,9 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 const int lb = loc_of[g.tbit[0]];
                 if (g.grad_gen == GEN_Z) {
                     locate(g.tbit[0], &op.tkind, &op.a, &op.tmask);
-                } else if (lb < kTileLaneBits) {
+                } else if (!((cur >> lb) & 1u)) {
                     op.tkind = TB_THREAD;  // lane bit: shuffles
-                    op.a = (uint8_t)lb;
+                    op.a = (uint8_t)lane_index(lb);
                 } else {
                     op.tkind = TB_REG;
                     op.a = (uint8_t)regidx(lb);
@@ -601,8 +656,34 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         P.op[nops++] = op;
         P.st[nst - 1].op_end = (uint16_t)nops;
     }
+    // the last stage stores the tile: lanes back on the 5 lowest bits
+    {
+        const TileStage &last = P.st[nst - 1];
+        bool natural_lanes = true;
+        for (int x = 0; x < kTileLaneBits; ++x) natural_lanes &= last.lloc[x] == x;
+        if (!natural_lanes) {
+            if (nst >= kTileMaxStages) return overflow();
+            open_stage(choose(ne, 0u, highmask), natural);
+        }
+    }
     P.n_stages = nst;
     P.n_grad = ngrad;
+    static const bool stats = std::getenv("QSIM_PLAN_STATS") != nullptr;
+    if (stats) {
+        int cnt[16] = {0};
+        for (int o = 0; o < nops; ++o) cnt[P.op[o].type & 15]++;
+        int rots = 0;
+        for (int o = 0; o < nops; ++o)
+            if (P.op[o].type == TOP_ROTS_R || P.op[o].type == TOP_ROTS_L)
+                for (int j = 0; j < 5; ++j) rots += P.mat[P.op[o].m + j].y != (R)0;
+        std::fprintf(stderr,
+                     "[qsim plan] gates %zu entries %d stages %d ops %d: rots_r %d rots_l %d (rotations %d) "
+                     "dblock %d (factors %d) dense1 %d phase %d diag1 %d other %d\n",
+                     pp.gates.size(), ne, nst, nops, cnt[TOP_ROTS_R], cnt[TOP_ROTS_L], rots, cnt[TOP_DBLOCK], ndf,
+                     cnt[TOP_DENSE1_R] + cnt[TOP_DENSE1_L], cnt[TOP_PHASE], cnt[TOP_DIAG1],
+                     nops - cnt[TOP_ROTS_R] - cnt[TOP_ROTS_L] - cnt[TOP_DBLOCK] - cnt[TOP_DENSE1_R] -
+                         cnt[TOP_DENSE1_L] - cnt[TOP_PHASE] - cnt[TOP_DIAG1]);
+    }
     if (prof_enabled()) {
         // algorithmic flops per amplitude: 16 for a 2x2 complex gate, 64 for 4x4,
         // 6 for a diagonal factor, 4 for a scaled rotation, 12 for a diagonal

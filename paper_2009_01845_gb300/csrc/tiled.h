@@ -7,14 +7,17 @@
 // tile while it is on chip, and writes it back once: one HBM round trip for
 // many gates (the grouping of local gates of Sec. 2.5, done per tile).
 //
-// Inside a CTA of 256 threads (8 warps) each thread holds 2^RB amplitudes in
-// registers. The tile's k = RB + 8 local bits are split, per stage, into
-//   L: local bits 0..4  -> lane index (fixed in every stage; coalesced),
+// Inside a CTA of 2^WB warps each thread holds 2^RB amplitudes in registers
+// (see TileCfg). The tile's k = RB + 5 + WB local bits are split, per stage, into
+//   L: 5 local bits     -> lane index (local bits 0..4 in the first and last
+//                          stage, so global loads and stores are coalesced),
 //   R: RB local bits    -> register index,
-//   W: 3 local bits     -> warp index.
+//   W: WB local bits    -> warp index.
 // Gates whose dense targets lie in R are applied in registers, targets in L
-// through warp shuffles; a new stage re-splits R/W through a shared-memory
-// transpose. Diagonal gates may act on any bits, inside or outside the tile.
+// through warp shuffles; a new stage re-splits the bits through a shared-memory
+// transpose, XOR-swizzled so that any stage's half-warp (quarter-warp for
+// complex128) hits distinct banks when its lane bits have distinct residues
+// mod 4 (mod 3). Diagonal gates may act on any bits, inside or outside the tile.
 #pragma once
 
 #include <cstdint>
@@ -23,22 +26,27 @@
 
 namespace qsim {
 
-constexpr int kTileThreads = 256;
 constexpr int kTileLaneBits = 5;
-constexpr int kTileWarpBits = 3;
+constexpr int kTileMaxWarpBits = 3;
 constexpr int kTileMaxStages = 48;
 constexpr int kTileMaxOps = 288;
 constexpr int kTileMaxMat = 640;   // complex entries in the matrix pool
 constexpr int kTileMaxGrad = 48;   // gradient ops per pass (adjoint sweep)
 constexpr int kTileMaxDFac = 96;   // diagonal-block factors per pass
 
-// register bits per thread for each precision (c64: 32 amplitudes, c128: 16)
+// Per precision: RB register bits per thread, WB warp bits (2^WB warps per
+// CTA), kMinBlocks resident CTAs per SM the register budget is sized for.
+// complex64: 32 amplitudes per thread, 8 warps, 2 CTAs per SM (k = 13);
+// complex128: 16 amplitudes per thread, 8 warps, 1 CTA per SM (k = 12).
+// (64 amplitudes per thread with 4 warps and 3 CTAs per SM measured slower:
+// fewer transposes, but register spills and fewer warps to hide latency.)
 template <typename R> struct TileCfg;
-// kMinBlocks: resident CTAs per SM the register budget is sized for
-template <> struct TileCfg<float> { static constexpr int RB = 5, kMinBlocks = 2; };
-template <> struct TileCfg<double> { static constexpr int RB = 4, kMinBlocks = 1; };
+template <> struct TileCfg<float> { static constexpr int RB = 5, WB = 3, kMinBlocks = 2; };
+template <> struct TileCfg<double> { static constexpr int RB = 4, WB = 3, kMinBlocks = 1; };
 inline int tile_reg_bits(qs_dtype dt) { return dt == QS_C64 ? 5 : 4; }
-inline int tile_bits(qs_dtype dt) { return tile_reg_bits(dt) + kTileLaneBits + kTileWarpBits; }
+inline int tile_warp_bits(qs_dtype dt) { return 3; }
+inline int tile_threads(qs_dtype dt) { return 32 << tile_warp_bits(dt); }
+inline int tile_bits(qs_dtype dt) { return tile_reg_bits(dt) + kTileLaneBits + tile_warp_bits(dt); }
 
 enum TileOpType : uint8_t {
     TOP_PHASE = 0,   // multiply by mat[m] where all required bits are 1
@@ -106,10 +114,11 @@ template <typename R> struct TileDFac {
 };
 
 struct TileStage {
-    uint8_t rloc[5];  // local bit of register bit j
+    uint8_t rloc[6];  // local bit of register bit j
     uint8_t wloc[3];  // local bit of warp bit w
+    uint8_t lloc[5];  // local bit of lane bit i (the first and last stage: 0..4)
+    uint8_t pad[2];
     uint16_t op_begin, op_end;
-    uint32_t pad;
 };
 
 template <typename R> struct TileParams {
