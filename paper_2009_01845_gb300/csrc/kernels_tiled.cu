@@ -340,12 +340,12 @@ __device__ __forceinline__ V<R> outside_factor(const TileDFac<R> &d, uint64_t tb
 
 // A diagonal block (TOP_DBLOCK). The planner folded the factors on register
 // bits alone into constants C[0] (base) and C[1 + j] (ratio applied when
-// register bit j is 1) and a register flip mask; the factor table holds, in
-// order, `no` factors on outside bits alone (a per-tile product, formed by
-// each warp), factors involving thread bits, and `np` factors on two or more
-// register bits. Per thread: base and ratios, then each register's phase as
-// base times the ratios of its set bits (prefix products shared by the
-// compiler), times sign flips, times the remaining pair factors.
+// register bit j is 1); sign flips on two register bits are TOP_FLIP ops. The
+// factor table holds, in order, `no` factors on outside bits alone (a per-tile
+// product, formed by each warp), factors involving thread bits or one register
+// bit, and `np` factors on two or more register bits. Per thread: base and
+// ratios, then each register's phase as base times the ratios of its set bits
+// (prefix products shared by the compiler), then the remaining pair factors.
 template <typename R, int RB>
 __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, const TileOp &op, uint64_t tbase,
                                            uint32_t lt) {
@@ -356,7 +356,6 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
     V<R> u[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) u[j] = C[1 + j];
-    uint64_t flip = op.tmask;
     if (no > 0) {
         // every warp forms the tile's product of outside factors itself (lanes
         // over factors, then a shuffle product): no barrier
@@ -374,8 +373,7 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
     }
     // thread and mixed factors (two independent product chains)
     V<R> b2 = mkc<R>(1, 0);
-    bool general = false;
-    for (int f = f0 + no; f < f0 + nf; ++f) {
+    for (int f = f0 + no; f < f0 + nf - np; ++f) {
         const TileDFac<R> &d = p.dfac[f];
         if (d.type == DF_BIT) {
             const V<R> v = (lt & (uint32_t)d.tmask) ? d.v1 : d.v0;
@@ -384,10 +382,7 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
             continue;
         }
         if ((tbase & d.mo) != d.mo || (lt & d.mt) != d.mt) continue;
-        if (f >= f0 + nf - np) {                  // two or more register bits
-            if (d.a) flip ^= d.tmask;
-            else general = true;
-        } else if (d.mr == 0) {
+        if (d.mr == 0) {
             if ((f - f0) & 1) b2 = cmul<R>(b2, d.v0);
             else base = cmul<R>(base, d.v0);
         } else {
@@ -405,31 +400,50 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
             if ((hb >> (j - 3)) & 1) q = cmul<R>(q, u[j]);
 #pragma unroll
         for (int lo = 0; lo < 8; ++lo) {
-            const int r = hb * 8 + lo;
             V<R> ph = q;
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 if ((lo >> j) & 1) ph = cmul<R>(ph, u[j]);
-            if ((flip >> r) & 1ull) ph = mkc<R>(-ph.x, -ph.y);
-            if (general)
-                for (int f = f0 + nf - np; f < f0 + nf; ++f) {
-                    const TileDFac<R> &d = p.dfac[f];
-                    if (!d.a && ((d.tmask >> r) & 1ull) && (tbase & d.mo) == d.mo && (lt & d.mt) == d.mt)
-                        ph = cmul<R>(ph, d.v0);
-                }
-            a[r] = cmul<R>(a[r], ph);
+            a[hb * 8 + lo] = cmul<R>(a[hb * 8 + lo], ph);
         }
+    }
+    // factors on two or more register bits (rare: controlled phases inside a block)
+    for (int f = f0 + nf - np; f < f0 + nf; ++f) {
+        const TileDFac<R> &d = p.dfac[f];
+        if ((tbase & d.mo) != d.mo || (lt & d.mt) != d.mt) continue;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if ((d.tmask >> r) & 1ull) a[r] = cmul<R>(a[r], d.v0);
     }
 }
 
-// Shared-memory position of tile-local index j (see tiled.h): an XOR of j's
-// higher bits folded into its low bits; linear over XOR.
-template <typename R> __device__ __forceinline__ uint32_t swz(uint32_t j);
-template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t j) {
-    return j ^ (((j >> 4) ^ (j >> 8) ^ (j >> 12)) & 15u);
+// negate the registers whose bits A and B (and the bits of mr) are 1
+template <typename R, int RB, int A, int B>
+__device__ __forceinline__ void flip_reg(V<R> *a, uint32_t mr) {
+    if (mr == 0) {
+#pragma unroll
+        for (int r = 0; r < (1 << RB); ++r)
+            if ((r & (1 << A)) && (r & (1 << B))) a[r] = mkc<R>(-a[r].x, -a[r].y);
+    } else {
+#pragma unroll
+        for (int r = 0; r < (1 << RB); ++r)
+            if ((r & (1 << A)) && (r & (1 << B)) && (r & mr) == mr) a[r] = mkc<R>(-a[r].x, -a[r].y);
+    }
 }
-template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t j) {
-    return j ^ (((j >> 3) ^ (j >> 6) ^ (j >> 9) ^ (j >> 12)) & 7u);
+
+template <typename R, int RB>
+__device__ __forceinline__ void dispatch_flip(V<R> *a, int A, int B, uint32_t mr) {
+    QS_PAIR_CASES(flip_reg, a, mr)
+}
+
+// Shared-memory position of tile-local index x under a transpose's swizzle
+// (see tiled.h): the images f[i] of its high bits h + i XORed into its low bits.
+template <typename R> __device__ __forceinline__ uint32_t swizzle_pos(uint32_t x, const uint8_t *f, int k) {
+    constexpr int h = swizzle_low_bits<R>();
+    uint32_t y = x;
+    for (int i = 0; i < k - h; ++i)
+        if ((x >> (h + i)) & 1u) y ^= f[i];
+    return y;
 }
 
 // tile-local index of this thread's lane and warp bits under a stage mapping
@@ -473,7 +487,9 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
     constexpr int WB = TileCfg<R>::WB;
     constexpr int NW = 1 << WB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V<R> *sm = reinterpret_cast<V<R> *>(smem_raw);
+    // dynamic shared memory: the tile (sizeof(V<R>) << k bytes), then this
+    // CTA's transpose offsets, one word per (stage, thread)
+    uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw + (sizeof(V<R>) << p.k));
     __shared__ R gsm[kTileMaxGrad][NW];
     __shared__ double s_g[16];
     __shared__ double s_eo;
@@ -482,6 +498,15 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
     const int warp = threadIdx.x >> 5;
     const uint64_t fmask = (1ull << p.n_free) - 1ull;
     V<R> a[NR];
+    // this thread's byte offsets for every transpose (written and read by this
+    // thread only): low half under the previous stage's mapping (write), high
+    // half under the new stage's (read), both in the transpose's swizzle
+    for (int s = 1; s < p.n_stages; ++s) {
+        const TileStage &pv = p.st[s - 1], &st = p.st[s];
+        const uint32_t w = swizzle_pos<R>(thread_local_index<WB>(pv, lane, warp), st.fcol, p.k) * sizeof(V<R>);
+        const uint32_t r = swizzle_pos<R>(thread_local_index<WB>(st, lane, warp), st.fcol, p.k) * sizeof(V<R>);
+        tab[s * (NW * 32) + threadIdx.x] = w | (r << 16);
+    }
 
     for (uint64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
         const uint64_t tbase = ((t >> p.n_free) << p.n) | expand_bits(t & fmask, p.tins);
@@ -503,22 +528,23 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
             const TileStage &st = p.st[s];
             if (s > 0) {
                 // transpose: write under the previous mapping, read under this one
-                // (positions swizzled; swz is linear, so it applies per part)
-                const TileStage &pv = p.st[s - 1];
-                uint32_t ps = swz<R>(thread_local_index<WB>(pv, lane, warp)), lr[RB];
+                // (positions are linear over XOR: thread offset ^ register offsets)
+                const uint32_t e = tab[s * (NW * 32) + threadIdx.x];
+                uint32_t ro[RB];
 #pragma unroll
-                for (int j = 0; j < RB; ++j) lr[j] = swz<R>(1u << pv.rloc[j]);
+                for (int j = 0; j < RB; ++j) ro[j] = st.rw[j];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) sm[ps ^ reg_local<RB>(r, lr)] = a[r];
+                for (int r = 0; r < NR; ++r)
+                    *reinterpret_cast<V<R> *>(smem_raw + ((e & 0xffffu) ^ reg_local<RB>(r, ro))) = a[r];
                 __syncthreads();
-                ps = swz<R>(thread_local_index<WB>(st, lane, warp));
 #pragma unroll
-                for (int j = 0; j < RB; ++j) lr[j] = swz<R>(1u << st.rloc[j]);
+                for (int j = 0; j < RB; ++j) ro[j] = st.rr[j];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) a[r] = sm[ps ^ reg_local<RB>(r, lr)];
+                for (int r = 0; r < NR; ++r)
+                    a[r] = *reinterpret_cast<const V<R> *>(smem_raw + ((e >> 16) ^ reg_local<RB>(r, ro)));
                 __syncthreads();
             }
-            const uint32_t lt = thread_local_index<WB>(st, lane, warp);
+            const uint32_t lt = st.need_lt ? thread_local_index<WB>(st, lane, warp) : 0u;
             for (int o = st.op_begin; o < st.op_end; ++o) {
                 const TileOp &op = p.op[o];
                 const bool ok = ((tbase & op.mo) == op.mo) && ((lt & op.mt) == op.mt);
@@ -625,6 +651,9 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                 case TOP_DBLOCK:
                     diag_block<R, RB>(a, p, op, tbase, lt);
                     break;
+                case TOP_FLIP:
+                    if (ok) dispatch_flip<R, RB>(a, op.a, op.b, mr);
+                    break;
                 case TOP_GRAD: {
                     if constexpr (!FULL) break;
                     constexpr int H = NR / 2;
@@ -699,18 +728,22 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
 template <typename R>
 static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) {
     constexpr int RB = TileCfg<R>::RB;
-    const size_t smem = sizeof(V<R>) << p.k;
+    constexpr int threads = 32 << TileCfg<R>::WB;
+    // the tile, then the transpose-offset table (one word per stage and thread)
+    const size_t smem = (sizeof(V<R>) << p.k) + (size_t)std::max(p.n_stages, 1) * threads * sizeof(uint32_t);
+    const size_t smem_max = (sizeof(V<R>) << tile_bits(sizeof(R) == 4 ? QS_C64 : QS_C128)) +
+                            (size_t)kTileMaxStages * threads * sizeof(uint32_t);
     static int configured[64] = {0};
     const int dev = (s->device >= 0 && s->device < 64) ? s->device : 0;
     static int blocks_per_sm[64] = {0};
     if (!configured[dev]) {
         QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+                                         (int)smem_max));
         QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+                                         (int)smem_max));
         int bps = 0;
-        QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB, true>,
-                                                                  32 << TileCfg<R>::WB, smem));
+        QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB, true>, threads,
+                                                                  smem_max));
         int sms = 0;
         QS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         blocks_per_sm[dev] = std::max(1, bps) * sms;
@@ -720,9 +753,9 @@ static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) 
     if (grid == 0) return QS_OK;
     ProfScope _ps(s->stream, KC_TILED);
     if (full)
-        tiled_kernel<R, RB, true><<<(unsigned)grid, 32 << TileCfg<R>::WB, smem, s->stream>>>((V<R> *)s->data, p);
+        tiled_kernel<R, RB, true><<<(unsigned)grid, threads, smem, s->stream>>>((V<R> *)s->data, p);
     else
-        tiled_kernel<R, RB, false><<<(unsigned)grid, 32 << TileCfg<R>::WB, smem, s->stream>>>((V<R> *)s->data, p);
+        tiled_kernel<R, RB, false><<<(unsigned)grid, threads, smem, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }

@@ -258,6 +258,71 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
 // slot[i]: per-member table slot of gate i (batched parameters) or -1.
 // Emits one tiled pass for the gates pp.gates; *fits = false (nothing launched)
 // when the pass exceeds the descriptor's capacity.
+// Swizzle of the transpose from stage a into stage b (see tiled.h): the
+// images of the high local bits are chosen so that, for both stages, the
+// lanes of one wavefront (lane bits 0 .. h-1) land on h independent low-bit
+// patterns, i.e. distinct banks. The fold of the high bits onto bit (p mod h)
+// is kept when it already works; otherwise images of the wavefront lanes'
+// high bits are drawn from a fixed-seed generator until both stages pass.
+// Then the byte offsets of both stages' register bits under that swizzle.
+template <typename R> static void set_transpose(const TileStage &a, TileStage &b, int k, uint64_t *rng) {
+    constexpr int h = swizzle_low_bits<R>();
+    constexpr int RB = TileCfg<R>::RB;
+    const int nh = k - h;
+    uint8_t f[9];
+    for (int i = 0; i < 9; ++i) f[i] = (uint8_t)(i < nh ? 1u << ((h + i) % h) : 0u);
+    auto img = [&](int p) -> uint32_t { return p < h ? (1u << p) : f[p - h]; };
+    auto full_rank = [&](const uint8_t *lanes) {
+        uint32_t v[8];
+        for (int x = 0; x < h; ++x) v[x] = img(lanes[x]);
+        int rank = 0;
+        for (int bit = h - 1; bit >= 0; --bit) {
+            int piv = -1;
+            for (int x = rank; x < h; ++x)
+                if ((v[x] >> bit) & 1u) {
+                    piv = x;
+                    break;
+                }
+            if (piv < 0) continue;
+            std::swap(v[rank], v[piv]);
+            for (int x = 0; x < h; ++x)
+                if (x != rank && ((v[x] >> bit) & 1u)) v[x] ^= v[rank];
+            ++rank;
+        }
+        return rank == h;
+    };
+    if (!(full_rank(a.lloc) && full_rank(b.lloc))) {
+        uint32_t free_hi = 0;
+        for (int x = 0; x < h; ++x) {
+            if (a.lloc[x] >= h) free_hi |= 1u << (a.lloc[x] - h);
+            if (b.lloc[x] >= h) free_hi |= 1u << (b.lloc[x] - h);
+        }
+        uint8_t fold[9];
+        std::memcpy(fold, f, sizeof(f));
+        bool found = false;
+        for (int tries = 0; tries < 4096 && !found; ++tries) {
+            for (int i = 0; i < nh; ++i)
+                if ((free_hi >> i) & 1u) {
+                    *rng = *rng * 6364136223846793005ull + 1442695040888963407ull;
+                    f[i] = (uint8_t)((*rng >> 33) & ((1u << h) - 1u));
+                }
+            found = full_rank(a.lloc) && full_rank(b.lloc);
+        }
+        if (!found) std::memcpy(f, fold, sizeof(f));
+    }
+    std::memcpy(b.fcol, f, sizeof(f));
+    auto pos = [&](uint32_t x) {
+        uint32_t y = x;
+        for (int i = 0; i < nh; ++i)
+            if ((x >> (h + i)) & 1u) y ^= f[i];
+        return y;
+    };
+    for (int j = 0; j < 6; ++j) {
+        b.rw[j] = j < RB ? (uint16_t)(pos(1u << a.rloc[j]) * sizeof(V<R>)) : 0;
+        b.rr[j] = j < RB ? (uint16_t)(pos(1u << b.rloc[j]) * sizeof(V<R>)) : 0;
+    }
+}
+
 template <typename R>
 static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const std::vector<GClass> &cls,
                               const std::vector<int> &slot, uint32_t pm_stride, const PassPlan &pp,
@@ -476,13 +541,14 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             for (int x = 0; x < width; ++x) put(cd(0.0, 0.0));
             P.mat[op.m + j] = mkc<R>((R)e.coef, (R)(e.form + 1));
         } else if (e.kind == E_BLOCK) {
-            // constants (base, per-register-bit ratios, register flip mask) for
-            // the factors on register bits alone; the others go to the factor
-            // table: outside-only first, then thread/mixed, pairs last
+            // constants (base, per-register-bit ratios) for the factors on
+            // register bits alone; sign flips on two or more register bits become
+            // TOP_FLIP ops; the others go to the factor table: outside-only
+            // first, then thread/mixed, pairs last
             cd cbase = 1.0;
             std::vector<cd> cu(RB, cd(1.0));
-            uint64_t cflip = 0;
             std::vector<TileDFac<R>> outside, single, pair;
+            std::vector<TileOp> flips;
             auto reg_pattern = [&](uint8_t mr) {
                 uint64_t pat = 0;
                 for (int r = 0; r < (1 << RB); ++r)
@@ -506,13 +572,24 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 } else {
                     split(f.mask, &d.mr, &d.mt, &d.mo);
                     const int nr = __builtin_popcount(d.mr);
+                    if (nr >= 2 && f.v0 == cd(-1.0, 0.0)) {  // a sign flip
+                        TileOp fo;
+                        std::memset(&fo, 0, sizeof(fo));
+                        fo.type = TOP_FLIP;
+                        fo.a = (uint8_t)__builtin_ctz(d.mr);
+                        const uint8_t rest = (uint8_t)(d.mr & (d.mr - 1));
+                        fo.b = (uint8_t)__builtin_ctz(rest);
+                        fo.mr = (uint8_t)(rest & (rest - 1));
+                        fo.mt = d.mt;
+                        fo.mo = d.mo;
+                        flips.push_back(fo);
+                        continue;
+                    }
                     if (d.mt == 0 && d.mo == 0) {        // register bits alone
                         if (nr == 0) {
                             cbase *= f.v0;
                         } else if (nr == 1) {
                             cu[__builtin_ctz(d.mr)] *= f.v0;
-                        } else if (f.v0 == cd(-1.0, 0.0)) {
-                            cflip ^= reg_pattern(d.mr);
                         } else {
                             d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
                             d.tmask = reg_pattern(d.mr);
@@ -526,18 +603,22 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                         continue;
                     }
                     d.tmask = reg_pattern(d.mr);
-                    d.a = f.v0 == cd(-1.0, 0.0) ? 1 : 0;  // a sign flip
                     (nr >= 2 ? pair : single).push_back(d);
                 }
             }
             const int nf = (int)(outside.size() + single.size() + pair.size());
             if (ndf + nf > kTileMaxDFac || nf > 255 || (int)outside.size() > 255) return overflow();
             if (nmat + 1 + RB > kTileMaxMat) return overflow();
+            if (nops + 1 + (int)flips.size() > kTileMaxOps) return overflow();
+            bool trivial = nf == 0 && cbase == cd(1.0);
+            for (int x = 0; x < RB; ++x) trivial = trivial && cu[x] == cd(1.0);
+            for (const TileOp &fo : flips) P.op[nops++] = fo;
+            P.st[nst - 1].op_end = (uint16_t)nops;
+            if (trivial) continue;                // flips only
             op.type = TOP_DBLOCK;
             op.m = nmat;                     // constants: base, ratios u[0..RB)
             put(cbase);
             for (int x = 0; x < RB; ++x) put(cu[x]);
-            op.tmask = cflip;
             op.mo = (uint64_t)ndf;           // first factor
             op.b = (uint8_t)nf;
             op.a = (uint8_t)pair.size();
@@ -668,6 +749,20 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     }
     P.n_stages = nst;
     P.n_grad = ngrad;
+    // per-transpose swizzles and register offsets; which stages test thread bits
+    uint64_t rng = 0x9e3779b97f4a7c15ull;
+    for (int t = 1; t < nst; ++t) set_transpose<R>(P.st[t - 1], P.st[t], k, &rng);
+    for (int t = 0; t < nst; ++t) {
+        TileStage &st = P.st[t];
+        st.need_lt = 0;
+        for (int o = st.op_begin; o < st.op_end; ++o) {
+            const TileOp &op = P.op[o];
+            bool uses = op.mt != 0;
+            if (op.type == TOP_DBLOCK) uses = uses || op.b > op.gl;  // thread, mixed or pair factors
+            else if (op.type != TOP_ROTS_R && op.type != TOP_ROTS_L && op.type != TOP_FLIP) uses = true;
+            st.need_lt |= uses ? 1 : 0;
+        }
+    }
     static const bool stats = std::getenv("QSIM_PLAN_STATS") != nullptr;
     if (stats) {
         int cnt[16] = {0};

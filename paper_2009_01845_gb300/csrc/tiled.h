@@ -15,9 +15,13 @@
 //   W: WB local bits    -> warp index.
 // Gates whose dense targets lie in R are applied in registers, targets in L
 // through warp shuffles; a new stage re-splits the bits through a shared-memory
-// transpose, XOR-swizzled so that any stage's half-warp (quarter-warp for
-// complex128) hits distinct banks when its lane bits have distinct residues
-// mod 4 (mod 3). Diagonal gates may act on any bits, inside or outside the tile.
+// transpose. Each transpose has its own XOR swizzle, chosen by the planner so
+// that both of its accesses (the write under the previous stage's lanes, the
+// read under the new stage's) are free of bank conflicts: the shared-memory
+// position of tile-local index j is j with the images fcol[] of its high bits
+// XORed into its low h bits (h = 4 for complex64, 3 for complex128, the lanes
+// of one 128-byte wavefront), linear over XOR, so register and thread offsets
+// combine by XOR. Diagonal gates may act on any bits, inside or outside the tile.
 #pragma once
 
 #include <cstdint>
@@ -28,7 +32,7 @@ namespace qsim {
 
 constexpr int kTileLaneBits = 5;
 constexpr int kTileMaxWarpBits = 3;
-constexpr int kTileMaxStages = 48;
+constexpr int kTileMaxStages = 32;  // also sizes the per-CTA offset table
 constexpr int kTileMaxOps = 288;
 constexpr int kTileMaxMat = 640;   // complex entries in the matrix pool
 constexpr int kTileMaxGrad = 48;   // gradient ops per pass (adjoint sweep)
@@ -60,6 +64,7 @@ enum TileOpType : uint8_t {
     TOP_ROTS_R,      // scaled real rotations on register bits: mat[m + j] = (coef, form + 1) or (0, 0)
     TOP_ROTS_L,      // the same on the 5 lane bits (warp shuffles)
     TOP_DBLOCK,      // product of diagonal factors (see diag_block)
+    TOP_FLIP,        // negate where register bits a and b (and the required bits) are 1
 };
 
 // Scaled real rotations: form 0: (a, b) <- (a - t b, b + t a) with |t| <= 1;
@@ -117,9 +122,16 @@ struct TileStage {
     uint8_t rloc[6];  // local bit of register bit j
     uint8_t wloc[3];  // local bit of warp bit w
     uint8_t lloc[5];  // local bit of lane bit i (the first and last stage: 0..4)
-    uint8_t pad[2];
+    uint8_t fcol[9];  // swizzle of the transpose into this stage: low-bit image of high local bit h + i
+    uint8_t need_lt;  // some op of the stage tests thread-local bits
+    uint16_t rw[6];   // transpose into this stage: byte offset of the previous stage's register bit j
+    uint16_t rr[6];   // ... and of this stage's register bit j
     uint16_t op_begin, op_end;
 };
+
+// Low bits of a shared-memory position that the swizzle folds into: the lanes
+// of one 128-byte wavefront (16 of complex64, 8 of complex128).
+template <typename R> constexpr int swizzle_low_bits() { return sizeof(R) == 4 ? 4 : 3; }
 
 template <typename R> struct TileParams {
     int n;            // member shift: member b starts at amplitude b << n
