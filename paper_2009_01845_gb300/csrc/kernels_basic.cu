@@ -418,10 +418,20 @@ __global__ void __launch_bounds__(kRedThreads) norm2_partial_kernel(const V<R> *
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     double acc = 0.0;
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    while (i < per) {
+    // full runs: all kChunk loads in flight before the arithmetic
+    while (i + (kChunk - 1) * stride < per) {
+        V<R> av[kChunk];
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) av[c] = p[i + c * stride];
         RunSum<R> run;
-#pragma unroll 4
-        for (int c = 0; c < kChunk && i < per; ++c, i += stride) {
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) run.add_sq(av[c].x, av[c].y);
+        acc += run.value();
+        i += kChunk * stride;
+    }
+    {
+        RunSum<R> run;
+        for (; i < per; i += stride) {
             const V<R> a = p[i];
             run.add_sq(a.x, a.y);
         }
@@ -483,7 +493,9 @@ template <typename R> struct ExpP {
     int8_t za[kMaxTermsPerLaunch];   // first Z bit, or -1
     int8_t zc[kMaxTermsPerLaunch];   // second Z bit, or -1
     int8_t zn[kMaxTermsPerLaunch];   // number of Z bits: 0, 1, 2 or 3 (= more)
+    int8_t ys[kMaxTermsPerLaunch];   // (-1)^{popcount(z_t & xb)}: the term's sign at x ^ xb relative to x
     int nt;
+    int nv;           // terms [0, nv) touch the chunk bits (see expect_partial_kernel)
     uint64_t xb;      // X mask in index bits (0 for the diagonal group)
     int n;
     int ms;           // member shift
@@ -503,51 +515,128 @@ __device__ __forceinline__ bool term_odd(const ExpP<R> &p, int t, uint64_t x) {
     }
 }
 
+// Free-index bits that vary inside one thread's chunk: 16 amplitudes at
+// j = chunk * 4096 + c * 256 + thread, c = 0..15 (bits 8..11 of j).
+constexpr int kExpChunkLo = 8, kExpChunkBits = 4;
+
+// Host: order the terms so that those whose Z bits meet the chunk bits come
+// first (p->nv of them); the others are constant over a chunk and are summed
+// once per chunk. Also the per-term sign between x and x ^ xb.
+template <typename R> static void exp_order_terms(ExpP<R> *p) {
+    uint64_t cx = 0;
+    for (int b = kExpChunkLo; b < kExpChunkLo + kExpChunkBits; ++b)
+        cx |= 1ull << ((p->xb && b >= p->hb) ? b + 1 : b);
+    ExpP<R> q = *p;
+    int k = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int t = 0; t < p->nt; ++t) {
+            const bool varying = (p->zb[t] & cx) != 0;
+            if (varying != (pass == 0)) continue;
+            q.cre[k] = p->cre[t];
+            q.cim[k] = p->cim[t];
+            q.zb[k] = p->zb[t];
+            q.za[k] = p->za[t];
+            q.zc[k] = p->zc[t];
+            q.zn[k] = p->zn[t];
+            q.ys[k] = (int8_t)(__builtin_popcountll(p->zb[t] & p->xb) & 1);
+            if (pass == 0) q.nv = k + 1;
+            ++k;
+        }
+    *p = q;
+}
+
+// f_m at x (fr, fi) and at x ^ xb (gr, gi), adding terms [t0, t1)
+template <typename R>
+__device__ __forceinline__ void exp_terms(const ExpP<R> &p, int t0, int t1, uint64_t x, R &fr, R &fi, R &gr,
+                                          R &gi) {
+    for (int t = t0; t < t1; ++t) {
+        const bool sx = term_odd(p, t, x);
+        const R cr = sx ? -p.cre[t] : p.cre[t], ci = sx ? -p.cim[t] : p.cim[t];
+        fr += cr;
+        fi += ci;
+        gr += p.ys[t] ? -cr : cr;
+        gi += p.ys[t] ? -ci : ci;
+    }
+}
+
+// Per member: sum_x |psi[x]|^2 f_0(x) (diagonal group), or sum over the pairs
+// (x, y = x ^ xb) with bit hb of x clear of conj(psi[y]) psi[x] f(x) +
+// conj(psi[x]) psi[y] f(y). For 2^12 or more free indices a thread takes
+// chunks of 16 amplitudes (consecutive threads on consecutive addresses for
+// each c); terms that do not touch the chunk bits are summed once per chunk,
+// the others per amplitude. Runs of 16 are summed in R, then in FP64.
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> *__restrict__ psi,
                                                                      const __grid_constant__ ExpP<R> p,
                                                                      double2 *__restrict__ part) {
     const V<R> *q = psi + ((uint64_t)blockIdx.y << p.ms);
     const uint64_t cnt = 1ull << p.n_free;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     double ar = 0.0, ai = 0.0;
-    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p.xb == 0) {
-        while (j < cnt) {
-            R run = 0;
-            for (int c = 0; c < kChunk && j < cnt; ++c, j += stride) {
-                R f = 0;
-                for (int t = 0; t < p.nt; ++t) f += term_odd(p, t, j) ? -p.cre[t] : p.cre[t];
-                const V<R> a = q[j];
-                run = fma(f, fma(a.x, a.x, a.y * a.y), run);
-            }
-            ar += (double)run;
-        }
-    } else {
-        const uint64_t lo = (1ull << p.hb) - 1ull;
-        while (j < cnt) {
+    const uint64_t lo = (1ull << p.hb) - 1ull;
+    auto insert0 = [&](uint64_t j) { return p.xb ? (((j >> p.hb) << (p.hb + 1)) | (j & lo)) : j; };
+    if (p.n_free >= kExpChunkLo + kExpChunkBits) {
+        const uint64_t nchunks = cnt >> (kExpChunkLo + kExpChunkBits);
+        for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+            const uint64_t j0 = (ch << (kExpChunkLo + kExpChunkBits)) | threadIdx.x;
+            R f0r = 0, f0i = 0, g0r = 0, g0i = 0;
+            exp_terms(p, p.nv, p.nt, insert0(j0), f0r, f0i, g0r, g0i);
             R rr = 0, ri = 0;
-            for (int c = 0; c < kChunk && j < cnt; ++c, j += stride) {
-                const uint64_t x = ((j >> p.hb) << (p.hb + 1)) | (j & lo);
-                const uint64_t y = x ^ p.xb;
-                R fxr = 0, fxi = 0, fyr = 0, fyi = 0;
-                for (int t = 0; t < p.nt; ++t) {
-                    const R cr = p.cre[t], ci = p.cim[t];
-                    const bool sx = term_odd(p, t, x), sy = term_odd(p, t, y);
-                    fxr += sx ? -cr : cr;
-                    fxi += sx ? -ci : ci;
-                    fyr += sy ? -cr : cr;
-                    fyi += sy ? -ci : ci;
+            if (p.xb == 0) {
+                // all 16 loads in flight before the arithmetic
+                V<R> av[1 << kExpChunkBits];
+#pragma unroll
+                for (int c = 0; c < (1 << kExpChunkBits); ++c) av[c] = q[j0 | ((uint64_t)c << kExpChunkLo)];
+#pragma unroll
+                for (int c = 0; c < (1 << kExpChunkBits); ++c) {
+                    const uint64_t x = j0 | ((uint64_t)c << kExpChunkLo);
+                    R fr = f0r, fi = 0, gr = 0, gi = 0;
+                    exp_terms(p, 0, p.nv, x, fr, fi, gr, gi);
+                    rr = fma(fr, fma(av[c].x, av[c].x, av[c].y * av[c].y), rr);
                 }
-                const V<R> a = q[x], b = q[y];
-                // conj(b) a f(x) + conj(a) b f(y), with conj(a) b = conj(conj(b) a)
-                const R abr = b.x * a.x + b.y * a.y;
-                const R abi = b.x * a.y - b.y * a.x;
-                rr += abr * (fxr + fyr) - abi * (fxi - fyi);
-                ri += abr * (fxi + fyi) + abi * (fxr - fyr);
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    constexpr int H = (1 << kExpChunkBits) / 2;
+                    V<R> av[H], bv[H];
+#pragma unroll
+                    for (int c = 0; c < H; ++c) {
+                        const uint64_t x = insert0(j0 | ((uint64_t)(h * H + c) << kExpChunkLo));
+                        av[c] = q[x];
+                        bv[c] = q[x ^ p.xb];
+                    }
+#pragma unroll
+                    for (int c = 0; c < H; ++c) {
+                        const uint64_t x = insert0(j0 | ((uint64_t)(h * H + c) << kExpChunkLo));
+                        R fxr = f0r, fxi = f0i, fyr = g0r, fyi = g0i;
+                        exp_terms(p, 0, p.nv, x, fxr, fxi, fyr, fyi);
+                        const V<R> a = av[c], b = bv[c];
+                        // conj(b) a f(x) + conj(a) b f(y), with conj(a) b = conj(conj(b) a)
+                        const R abr = b.x * a.x + b.y * a.y;
+                        const R abi = b.x * a.y - b.y * a.x;
+                        rr += abr * (fxr + fyr) - abi * (fxi - fyi);
+                        ri += abr * (fxi + fyi) + abi * (fxr - fyr);
+                    }
+                }
             }
             ar += (double)rr;
             ai += (double)ri;
+        }
+    } else {
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
+            const uint64_t x = insert0(j);
+            R fxr = 0, fxi = 0, fyr = 0, fyi = 0;
+            exp_terms(p, 0, p.nt, x, fxr, fxi, fyr, fyi);
+            if (p.xb == 0) {
+                const V<R> a = q[x];
+                ar += (double)(fxr * fma(a.x, a.x, a.y * a.y));
+            } else {
+                const V<R> a = q[x], b = q[x ^ p.xb];
+                const R abr = b.x * a.x + b.y * a.y;
+                const R abi = b.x * a.y - b.y * a.x;
+                ar += (double)(abr * (fxr + fyr) - abi * (fxi - fyi));
+                ai += (double)(abr * (fxi + fyi) + abi * (fxr - fyr));
+            }
         }
     }
     const double2 r = block_sum2(ar, ai);
@@ -618,6 +707,7 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
             p.n_free = p.xb ? n - 1 : n;
             p.accumulate = first ? 0 : 1;
             first = false;
+            exp_order_terms(&p);
             if (prof_enabled())
                 prof_add_work(KC_REDUCE, (double)((uint64_t)s->batch << n) * amp_bytes(s),
                               (double)((uint64_t)s->batch << n) * (2.0 * p.nt + 6.0));
@@ -627,6 +717,8 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
                 std::memcpy(&pf.za, &p.za, sizeof(p.za));
                 std::memcpy(&pf.zc, &p.zc, sizeof(p.zc));
                 std::memcpy(&pf.zn, &p.zn, sizeof(p.zn));
+                std::memcpy(&pf.ys, &p.ys, sizeof(p.ys));
+                pf.nv = p.nv;
                 for (int j = 0; j < kMaxTermsPerLaunch; ++j) {
                     pf.cre[j] = (float)p.cre[j];
                     pf.cim[j] = (float)p.cim[j];
@@ -1008,6 +1100,7 @@ static qs_status expectation_noalloc_t(const V<R> *psi, int n, int batch, const 
             p.n_free = xb ? n - 1 : n;
             p.accumulate = first ? 0 : 1;
             first = false;
+            exp_order_terms(&p);
             expect_partial_kernel<R><<<grid, kRedThreads, 0, stream>>>(psi, p, part);
             QS_CUDA_TRY(cudaGetLastError());
             if (cursor >= count) break;
