@@ -488,8 +488,10 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
     constexpr int NW = 1 << WB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // dynamic shared memory: the tile (sizeof(V<R>) << k bytes), then this
-    // CTA's transpose offsets, one word per (stage, thread)
+    // CTA's transpose offsets, one word per (stage, thread), then the threads'
+    // tile-local lane/warp bits per stage (16 bits per stage and thread)
     uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw + (sizeof(V<R>) << p.k));
+    uint16_t *ltab = reinterpret_cast<uint16_t *>(tab + p.n_stages * (NW * 32));
     __shared__ R gsm[kTileMaxGrad][NW];
     __shared__ double s_g[16];
     __shared__ double s_eo;
@@ -501,10 +503,13 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
     // this thread's byte offsets for every transpose (written and read by this
     // thread only): low half under the previous stage's mapping (write), high
     // half under the new stage's (read), both in the transpose's swizzle
-    for (int s = 1; s < p.n_stages; ++s) {
-        const TileStage &pv = p.st[s - 1], &st = p.st[s];
-        const uint32_t w = swizzle_pos<R>(thread_local_index<WB>(pv, lane, warp), st.fcol, p.k) * sizeof(V<R>);
-        const uint32_t r = swizzle_pos<R>(thread_local_index<WB>(st, lane, warp), st.fcol, p.k) * sizeof(V<R>);
+    for (int s = 0; s < p.n_stages; ++s) {
+        const TileStage &st = p.st[s];
+        const uint32_t lt = thread_local_index<WB>(st, lane, warp);
+        ltab[s * (NW * 32) + threadIdx.x] = (uint16_t)lt;
+        if (s == 0) continue;
+        const uint32_t w = swizzle_pos<R>(thread_local_index<WB>(p.st[s - 1], lane, warp), st.fcol, p.k) * sizeof(V<R>);
+        const uint32_t r = swizzle_pos<R>(lt, st.fcol, p.k) * sizeof(V<R>);
         tab[s * (NW * 32) + threadIdx.x] = w | (r << 16);
     }
 
@@ -544,7 +549,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     a[r] = *reinterpret_cast<const V<R> *>(smem_raw + ((e >> 16) ^ reg_local<RB>(r, ro)));
                 __syncthreads();
             }
-            const uint32_t lt = st.need_lt ? thread_local_index<WB>(st, lane, warp) : 0u;
+            const uint32_t lt = st.need_lt ? (uint32_t)ltab[s * (NW * 32) + threadIdx.x] : 0u;
             for (int o = st.op_begin; o < st.op_end; ++o) {
                 const TileOp &op = p.op[o];
                 const bool ok = ((tbase & op.mo) == op.mo) && ((lt & op.mt) == op.mt);
@@ -729,10 +734,12 @@ template <typename R>
 static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) {
     constexpr int RB = TileCfg<R>::RB;
     constexpr int threads = 32 << TileCfg<R>::WB;
-    // the tile, then the transpose-offset table (one word per stage and thread)
-    const size_t smem = (sizeof(V<R>) << p.k) + (size_t)std::max(p.n_stages, 1) * threads * sizeof(uint32_t);
+    // the tile, then the transpose-offset and local-index tables (6 bytes per
+    // stage and thread)
+    constexpr size_t per_stage = threads * (sizeof(uint32_t) + sizeof(uint16_t));
+    const size_t smem = (sizeof(V<R>) << p.k) + (size_t)std::max(p.n_stages, 1) * per_stage;
     const size_t smem_max = (sizeof(V<R>) << tile_bits(sizeof(R) == 4 ? QS_C64 : QS_C128)) +
-                            (size_t)kTileMaxStages * threads * sizeof(uint32_t);
+                            (size_t)kTileMaxStages * per_stage;
     static int configured[64] = {0};
     const int dev = (s->device >= 0 && s->device < 64) ? s->device : 0;
     static int blocks_per_sm[64] = {0};

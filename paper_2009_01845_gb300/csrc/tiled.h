@@ -32,7 +32,7 @@ namespace qsim {
 
 constexpr int kTileLaneBits = 5;
 constexpr int kTileMaxWarpBits = 3;
-constexpr int kTileMaxStages = 32;  // also sizes the per-CTA offset table
+constexpr int kTileMaxStages = 24;  // also sizes the per-CTA offset tables
 constexpr int kTileMaxOps = 288;
 constexpr int kTileMaxMat = 640;   // complex entries in the matrix pool
 constexpr int kTileMaxGrad = 48;   // gradient ops per pass (adjoint sweep)
