@@ -552,12 +552,17 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
             const uint32_t lt = st.need_lt ? (uint32_t)ltab[s * (NW * 32) + threadIdx.x] : 0u;
             for (int o = st.op_begin; o < st.op_end; ++o) {
                 const TileOp &op = p.op[o];
-                const bool ok = ((tbase & op.mo) == op.mo) && ((lt & op.mt) == op.mt);
-                const uint32_t mr = op.mr;
-                const V<R> *M = op.pm ? (p.pmat + (t >> p.n_free) * p.pm_stride + op.m) : &p.mat[op.m];
+                // decoded per case: the common ops read only the fields they use
+                auto req_ok = [&]() { return ((tbase & op.mo) == op.mo) && ((lt & op.mt) == op.mt); };
+                auto mat_of = [&]() {
+                    return op.pm ? (p.pmat + (t >> p.n_free) * p.pm_stride + op.m) : &p.mat[op.m];
+                };
                 switch (op.type) {
                 case TOP_DENSE1_L: {
                     // every lane takes part in the shuffles; only `ok` lanes update
+                    const bool ok = req_ok();
+                    const uint32_t mr = op.mr;
+                    const V<R> *M = mat_of();
                     const int bit = (lane >> op.a) & 1;
                     const V<R> cs = bit ? M[3] : M[0];
                     const V<R> co = bit ? M[2] : M[1];
@@ -569,19 +574,24 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     break;
                 }
                 case TOP_DENSE1_R:
-                    if (ok)
-                        dispatch_dense1<R, RB>(a, op.a, M[0], M[1], M[2], M[3], mr);
+                    if (req_ok()) {
+                        const V<R> *M = mat_of();
+                        dispatch_dense1<R, RB>(a, op.a, M[0], M[1], M[2], M[3], op.mr);
+                    }
                     break;
                 case TOP_PHASE:
-                    if (ok) {
-                        const V<R> ph = M[0];
+                    if (req_ok()) {
+                        const uint32_t mr = op.mr;
+                        const V<R> ph = mat_of()[0];
 #pragma unroll
                         for (int r = 0; r < NR; ++r)
                             if ((r & mr) == mr) a[r] = cmul<R>(a[r], ph);
                     }
                     break;
                 case TOP_DIAG1:
-                    if (ok) {
+                    if (req_ok()) {
+                        const uint32_t mr = op.mr;
+                        const V<R> *M = mat_of();
                         const V<R> d0 = M[0], d1 = M[1];
                         if (op.tkind == TB_REG) {
 #pragma unroll
@@ -599,38 +609,40 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     break;
                 case TOP_DENSE2_RR:
                     if constexpr (FULL)
-                        if (ok) dispatch_dense2<R, RB>(a, op.a, op.b, M, mr);
+                        if (req_ok()) dispatch_dense2<R, RB>(a, op.a, op.b, mat_of(), op.mr);
                     break;
                 case TOP_SWAP_RR:
                     if constexpr (FULL)
-                        if (ok) dispatch_swap<R, RB>(a, op.a, op.b, mr);
+                        if (req_ok()) dispatch_swap<R, RB>(a, op.a, op.b, op.mr);
                     break;
                 case TOP_ISING:
                     if constexpr (FULL)
                         ising_phase<R, RB>(a, p, op, st, tbase, t >> p.n_free, lane, warp, s_g, &s_eo, s_qp);
                     break;
                 case TOP_ROTS_R: {
-                    // rotations on distinct register bits (they commute)
+                    // rotations on distinct register bits (they commute); op.a / op.b
+                    // mark the bits in tan / cot form, mat[m + j].x holds t or u
+                    const V<R> *M = &p.mat[op.m];
+                    const uint32_t tm = op.a, cm = op.b;
 #pragma unroll
                     for (int j = 0; j < RB; ++j) {
-                        const V<R> cf = M[j];
-                        if (cf.y == (R)(ROT_TAN + 1)) {
+                        if ((tm >> j) & 1u) {
                             switch (j) {
-                            case 0: rot_reg<R, RB, 0>(a, cf.x, ROT_TAN); break;
-                            case 1: rot_reg<R, RB, 1>(a, cf.x, ROT_TAN); break;
-                            case 2: rot_reg<R, RB, 2>(a, cf.x, ROT_TAN); break;
-                            case 3: rot_reg<R, RB, 3>(a, cf.x, ROT_TAN); break;
-                            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, cf.x, ROT_TAN); break;
-                            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, cf.x, ROT_TAN);
+                            case 0: rot_reg<R, RB, 0>(a, M[0].x, ROT_TAN); break;
+                            case 1: rot_reg<R, RB, 1>(a, M[1].x, ROT_TAN); break;
+                            case 2: rot_reg<R, RB, 2>(a, M[2].x, ROT_TAN); break;
+                            case 3: rot_reg<R, RB, 3>(a, M[3].x, ROT_TAN); break;
+                            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, M[4].x, ROT_TAN); break;
+                            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, M[5].x, ROT_TAN);
                             }
-                        } else if (cf.y == (R)(ROT_COT + 1)) {
+                        } else if ((cm >> j) & 1u) {
                             switch (j) {
-                            case 0: rot_reg<R, RB, 0>(a, cf.x, ROT_COT); break;
-                            case 1: rot_reg<R, RB, 1>(a, cf.x, ROT_COT); break;
-                            case 2: rot_reg<R, RB, 2>(a, cf.x, ROT_COT); break;
-                            case 3: rot_reg<R, RB, 3>(a, cf.x, ROT_COT); break;
-                            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, cf.x, ROT_COT); break;
-                            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, cf.x, ROT_COT);
+                            case 0: rot_reg<R, RB, 0>(a, M[0].x, ROT_COT); break;
+                            case 1: rot_reg<R, RB, 1>(a, M[1].x, ROT_COT); break;
+                            case 2: rot_reg<R, RB, 2>(a, M[2].x, ROT_COT); break;
+                            case 3: rot_reg<R, RB, 3>(a, M[3].x, ROT_COT); break;
+                            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, M[4].x, ROT_COT); break;
+                            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, M[5].x, ROT_COT);
                             }
                         }
                     }
@@ -638,6 +650,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                 }
                 case TOP_ROTS_L: {
                     // own value in row `bit`, partner value v from lane ^ (1 << j)
+                    const V<R> *M = &p.mat[op.m];
 #pragma unroll
                     for (int j = 0; j < kTileLaneBits; ++j) {
                         const V<R> cf = M[j];
@@ -657,10 +670,12 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     diag_block<R, RB>(a, p, op, tbase, lt);
                     break;
                 case TOP_FLIP:
-                    if (ok) dispatch_flip<R, RB>(a, op.a, op.b, mr);
+                    if (req_ok()) dispatch_flip<R, RB>(a, op.a, op.b, op.mr);
                     break;
                 case TOP_GRAD: {
                     if constexpr (!FULL) break;
+                    const bool ok = req_ok();
+                    const uint32_t mr = op.mr;
                     constexpr int H = NR / 2;
                     R acc = 0;
                     if (op.b == GEN_X || op.b == GEN_Y) {

@@ -530,14 +530,20 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             const int j = lane ? lane_index(lb) : regidx(lb);
             const uint8_t want = lane ? TOP_ROTS_L : TOP_ROTS_R;
             const int width = lane ? kTileLaneBits : RB;
+            const uint8_t tan_bit = (!lane && e.form == ROT_TAN) ? (uint8_t)(1u << j) : 0;
+            const uint8_t cot_bit = (!lane && e.form == ROT_COT) ? (uint8_t)(1u << j) : 0;
             if (nops > P.st[nst - 1].op_begin && P.op[nops - 1].type == want &&
                 P.mat[P.op[nops - 1].m + j].y == (R)0) {
                 P.mat[P.op[nops - 1].m + j] = mkc<R>((R)e.coef, (R)(e.form + 1));
+                P.op[nops - 1].a |= tan_bit;  // register form: bit masks of the two forms
+                P.op[nops - 1].b |= cot_bit;
                 continue;
             }
             if (nmat + width > kTileMaxMat) return overflow();
             op.type = want;
             op.m = nmat;
+            op.a = tan_bit;
+            op.b = cot_bit;
             for (int x = 0; x < width; ++x) put(cd(0.0, 0.0));
             P.mat[op.m + j] = mkc<R>((R)e.coef, (R)(e.form + 1));
         } else if (e.kind == E_BLOCK) {

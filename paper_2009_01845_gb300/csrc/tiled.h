@@ -61,7 +61,8 @@ enum TileOpType : uint8_t {
     TOP_SWAP_RR,     // swap register bits a < b
     TOP_GRAD,        // adjoint sweep: accumulate Im<lambda|P|phi> for a generator P
     TOP_ISING,       // psi_x *= exp(-i tau E(x)), E an Ising energy (<= 2-body Z terms)
-    TOP_ROTS_R,      // scaled real rotations on register bits: mat[m + j] = (coef, form + 1) or (0, 0)
+    TOP_ROTS_R,      // scaled real rotations on register bits: mat[m + j] = (coef, form + 1) or (0, 0);
+                     // a / b: masks of the register bits in tan / cot form
     TOP_ROTS_L,      // the same on the 5 lane bits (warp shuffles)
     TOP_DBLOCK,      // product of diagonal factors (see diag_block)
     TOP_FLIP,        // negate where register bits a and b (and the required bits) are 1
