@@ -341,17 +341,19 @@ __device__ __forceinline__ V<R> outside_factor(const TileDFac<R> &d, uint64_t tb
 // A diagonal block (TOP_DBLOCK). The planner folded the factors on register
 // bits alone into constants C[0] (base) and C[1 + j] (ratio applied when
 // register bit j is 1); sign flips on two register bits are TOP_FLIP ops. The
-// factor table holds, in order, `no` factors on outside bits alone (a per-tile
-// product, formed by each warp), factors involving thread bits or one register
-// bit, and `np` factors on two or more register bits. Per thread: base and
-// ratios, then each register's phase as base times the ratios of its set bits
-// (prefix products shared by the compiler), then the remaining pair factors.
+// factor table holds, in order, `no` complex factors on outside bits alone (a
+// per-tile product, formed by each warp), `ns` sign factors (negate the base
+// or one ratio where their required bits are 1), complex factors involving
+// thread bits or one register bit, and `np` factors on two or more register
+// bits. Per thread: base and ratios, then each register's phase as base times
+// the ratios of its set bits (prefix products shared by the compiler), then
+// the remaining pair factors.
 template <typename R, int RB>
 __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, const TileOp &op, uint64_t tbase,
                                            uint32_t lt) {
     constexpr int NR = 1 << RB;
     const V<R> *C = &p.mat[op.m];
-    const int f0 = (int)op.mo, nf = op.b, np = op.a, no = op.gl;
+    const int f0 = (int)op.mo, nf = op.b, np = op.a, no = op.gl, ns = op.tkind;
     V<R> base = C[0];
     V<R> u[RB];
 #pragma unroll
@@ -371,9 +373,21 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
         }
         base = cmul<R>(base, v);
     }
+    if (ns > 0) {
+        // sign factors: XOR of negation bits (bit j: ratio j, bit 7: base)
+        uint32_t neg = 0;
+        for (int f = f0 + no; f < f0 + no + ns; ++f) {
+            const TileDFac<R> &d = p.dfac[f];
+            if ((tbase & d.mo) == d.mo && (lt & d.mt) == d.mt) neg ^= d.a;
+        }
+        if (neg & 0x80u) base = mkc<R>(-base.x, -base.y);
+#pragma unroll
+        for (int j = 0; j < RB; ++j)
+            if ((neg >> j) & 1u) u[j] = mkc<R>(-u[j].x, -u[j].y);
+    }
     // thread and mixed factors (two independent product chains)
     V<R> b2 = mkc<R>(1, 0);
-    for (int f = f0 + no; f < f0 + nf - np; ++f) {
+    for (int f = f0 + no + ns; f < f0 + nf - np; ++f) {
         const TileDFac<R> &d = p.dfac[f];
         if (d.type == DF_BIT) {
             const V<R> v = (lt & (uint32_t)d.tmask) ? d.v1 : d.v0;

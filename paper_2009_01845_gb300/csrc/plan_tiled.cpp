@@ -139,14 +139,24 @@ uint64_t factor_bits(const Factor &f) { return f.type == DF_BIT ? (1ull << f.bit
 
 }  // namespace
 
-// Build the entry list of a pass. With `algebra`, uncontrolled one-qubit gates
-// become D_R, a scaled rotation and D_L; those diagonals, uncontrolled one-bit
-// diagonal gates and phase gates become factors, each placed anywhere between
-// the last and the next entry that does not commute with it (a rotation or a
-// dense gate on one of its bits), at as few points as possible (greedy interval
-// stabbing: sort by right end, cut at the first right end, repeat).
+// Split the gates of a pass into entries. With `algebra`, uncontrolled
+// one-qubit gates become D_R, a scaled rotation and D_L; those diagonals,
+// uncontrolled one-bit diagonal gates and phase gates become factors. Returns
+// the other entries in queue order and, in *facs, every factor with the range
+// of positions it may be applied at: a cut at position p means "just before
+// entry p" (p = size: after the last), valid for left < p <= right, where left
+// and right are the last and next entries that do not commute with the factor
+// (a rotation or a dense gate on one of its bits). The caller places the cuts
+// (diagonal blocks) and assigns the factors to them.
+struct FactorSpan {
+    Factor f;
+    int left, right;
+};
+
 static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::vector<GClass> &cls,
-                                        const std::vector<int> &slot, const std::vector<int> &gates, bool algebra) {
+                                        const std::vector<int> &slot, const std::vector<int> &gates, bool algebra,
+                                        std::vector<FactorSpan> *facs) {
+    facs->clear();
     std::vector<Entry> base;                  // non-factor entries in order
     std::vector<uint64_t> blocks_bits;        // bits each base entry does not commute on
     struct PF { Factor f; int pos; };         // factor and the base position it precedes
@@ -194,65 +204,23 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
         if (c == G_GRAD || c == G_SINGLE) nb = ~0ull;  // barrier
         blocks_bits.push_back(nb);
     }
-    if (pf.empty()) return base;
-    // valid cut points for factor f: base positions p in (left, right], where a
-    // cut at p means "just before base[p]" (p = base.size(): after the last)
     const int nbase = (int)base.size();
-    std::vector<std::pair<int, int>> iv(pf.size());
-    for (size_t i = 0; i < pf.size(); ++i) {
-        const uint64_t fb = factor_bits(pf[i].f);
+    for (const PF &q : pf) {
+        const uint64_t fb = factor_bits(q.f);
         int left = -1, right = nbase;
-        for (int p = pf[i].pos - 1; p >= 0; --p)
+        for (int p = q.pos - 1; p >= 0; --p)
             if (blocks_bits[p] & fb) {
                 left = p;
                 break;
             }
-        for (int p = pf[i].pos; p < nbase; ++p)
+        for (int p = q.pos; p < nbase; ++p)
             if (blocks_bits[p] & fb) {
                 right = p;
                 break;
             }
-        iv[i] = {left, right};
+        facs->push_back(FactorSpan{q.f, left, right});
     }
-    std::vector<int> order(pf.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return iv[a].second < iv[b].second; });
-    std::vector<int> cut_of(pf.size(), -1);
-    std::vector<int> cuts;
-    for (int i : order) {
-        if (cut_of[i] >= 0) continue;
-        const int c = iv[i].second;
-        cuts.push_back(c);
-        for (size_t j = 0; j < pf.size(); ++j)
-            if (cut_of[j] < 0 && iv[j].first < c && c <= iv[j].second) cut_of[j] = c;
-    }
-    std::sort(cuts.begin(), cuts.end());
-    cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
-    std::vector<Entry> out;
-    size_t ci = 0;
-    for (int p = 0; p <= nbase; ++p) {
-        if (ci < cuts.size() && cuts[ci] == p) {
-            Entry b{E_BLOCK};
-            for (size_t j = 0; j < pf.size(); ++j) {  // factors in queue order
-                if (cut_of[j] != p) continue;
-                const Factor &f = pf[j].f;
-                bool merged = false;
-                if (f.type == DF_BIT)  // one-bit diagonals on the same bit multiply
-                    for (Factor &g : b.fac)
-                        if (g.type == DF_BIT && g.bit == f.bit) {
-                            g.v0 *= f.v0;
-                            g.v1 *= f.v1;
-                            merged = true;
-                            break;
-                        }
-                if (!merged) b.fac.push_back(f);
-            }
-            out.push_back(std::move(b));
-            ++ci;
-        }
-        if (p < nbase) out.push_back(std::move(base[p]));
-    }
-    return out;
+    return base;
 }
 
 // slot[i]: per-member table slot of gate i (batched parameters) or -1.
@@ -343,23 +311,31 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     // Free lanes (every pass but the adjoint sweep): dense targets, lane bits
     // included, must be register bits; stages move lanes to any bits.
     const bool free_lanes = force_bit < 0;
-    const std::vector<Entry> ent = build_entries(G, cls, slot, pp.gates, free_lanes);
-    // per-entry needed local register bits
-    const int ne = (int)ent.size();
-    std::vector<uint32_t> needl(ne, 0);
-    for (int i = 0; i < ne; ++i) {
+    std::vector<FactorSpan> facs;
+    const std::vector<Entry> base = build_entries(G, cls, slot, pp.gates, free_lanes, &facs);
+    // needed local register bits of an entry
+    auto need_of = [&](const Entry &e) {
         uint64_t nb = 0;
-        if (ent[i].kind == E_GATE) {
-            const LGate &g = G[ent[i].gi];
-            const GClass c = cls[ent[i].gi];
+        if (e.kind == E_GATE) {
+            const LGate &g = G[e.gi];
+            const GClass c = cls[e.gi];
             nb = need_bits(g, c);
             if (free_lanes && (c == G_DENSE1 || (c == G_GRAD && (g.grad_gen == GEN_X || g.grad_gen == GEN_Y))))
                 nb = 1ull << g.tbit[0];
         }
-        if (ent[i].kind == E_ROT && (free_lanes || ent[i].bit >= kTileLaneBits)) nb = 1ull << ent[i].bit;
+        if (e.kind == E_ROT && (free_lanes || e.bit >= kTileLaneBits)) nb = 1ull << e.bit;
+        uint32_t l = 0;
         for (int b = 0; b < 64; ++b)
-            if ((nb >> b) & 1ull) needl[i] |= 1u << loc_of[b];
-    }
+            if ((nb >> b) & 1ull) l |= 1u << loc_of[b];
+        return l;
+    };
+    // the stage choices below read needl/ne: first over the entries without
+    // diagonal blocks (blocks need no bits, so the stages are the same), then
+    // over the final list
+    std::vector<Entry> ent;
+    int ne = (int)base.size();
+    std::vector<uint32_t> needl(ne, 0);
+    for (int i = 0; i < ne; ++i) needl[i] = need_of(base[i]);
     const uint32_t force_loc = force_bit >= 0 ? (1u << loc_of[force_bit]) : 0u;
     const uint32_t low5 = (1u << kTileLaneBits) - 1u;
     auto next_use = [&](int from, int lb) {
@@ -407,6 +383,156 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             }
         } while (std::next_permutation(L.begin(), L.end()));
         return best;
+    };
+
+    const uint32_t low5_mask = (1u << kTileLaneBits) - 1u;
+    const uint32_t high_bits = ((1u << k) - 1u) & ~low5_mask;
+
+    // Diagonal blocks. The register set in effect at every entry (a stage
+    // opens at an entry whose needed bits are not all registers). Costs in
+    // instructions per thread: a block's phase walk (kWalk; paid by a cut
+    // holding any factor but register sign flips), and per factor: on register
+    // bits alone 0 (folds into the block's constants), a register sign flip 16
+    // (its own op), a sign under thread/outside bits 10, a complex product 25,
+    // a pair factor 60. Cuts start as the fewest points that meet every
+    // factor's range (greedy interval stabbing: sort by right end, cut at the
+    // first right end, repeat), each factor at its cheapest open cut; then,
+    // while it lowers the total, the stage opening (or pass end) whose opening
+    // saves most is added, factors moving to it where cheaper.
+    {
+        const int nbase = (int)base.size();
+        std::vector<uint32_t> reg_base(nbase + 1, 0u);
+        std::vector<char> cand(nbase + 1, 0), open(nbase + 1, 0);
+        uint32_t c = choose(0, (ne ? needl[0] : 0u) & high_bits, high_bits);
+        cand[0] = 1;
+        for (int i = 0; i < nbase; ++i) {
+            if ((needl[i] & ~c) != 0) {
+                c = free_lanes ? choose(i, needl[i], (1u << k) - 1u) : choose(i, needl[i], high_bits);
+                cand[i] = 1;
+            }
+            reg_base[i] = c;
+        }
+        reg_base[nbase] = c;
+        cand[nbase] = 1;
+        const int nf = (int)facs.size();
+        {
+            std::vector<int> order(nf);
+            for (int j = 0; j < nf; ++j) order[j] = j;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return facs[x].right < facs[y].right; });
+            for (int j : order) {
+                bool met = false;
+                for (int p = facs[j].left + 1; p <= facs[j].right && !met; ++p) met = open[p] != 0;
+                if (!met) open[facs[j].right] = 1;
+            }
+        }
+        constexpr int kWalk = 280;
+        // cost of factor f at a cut with register set regs; *walk: needs the phase walk
+        auto cost = [&](const Factor &f, uint32_t regs, bool *walk) {
+            int nr = 0, nt = 0, no = 0;
+            const uint64_t m = factor_bits(f);
+            for (int b = 0; b < 64; ++b) {
+                if (!((m >> b) & 1ull)) continue;
+                const int lb = b < n ? loc_of[b] : -1;
+                if (lb < 0) ++no;
+                else if ((regs >> lb) & 1u) ++nr;
+                else ++nt;
+            }
+            *walk = true;
+            if (f.type == DF_BIT) return nr ? 0 : 25;
+            const bool sign = f.v0 == cd(-1.0, 0.0);
+            if (sign && nr >= 2) {
+                *walk = false;
+                return 16;
+            }
+            if (nt == 0 && no == 0) return nr <= 1 ? 0 : 60;
+            if (sign) return 10;
+            return nr >= 2 ? 60 : 25;
+        };
+        std::vector<int> where(nf, -1), fc(nf, 0);
+        std::vector<char> fw(nf, 0);
+        for (int j = 0; j < nf; ++j) {
+            int bc = std::numeric_limits<int>::max();
+            for (int p = facs[j].left + 1; p <= facs[j].right; ++p) {
+                if (!open[p]) continue;
+                bool w;
+                const int cc = cost(facs[j].f, reg_base[p], &w);
+                if (cc < bc) {
+                    bc = cc;
+                    where[j] = p;
+                    fc[j] = cc;
+                    fw[j] = w;
+                }
+            }
+        }
+        for (;;) {
+            // walkers per open cut
+            std::vector<int> walkers(nbase + 1, 0);
+            for (int j = 0; j < nf; ++j) walkers[where[j]] += fw[j];
+            int best_q = -1, best_delta = 0;
+            for (int q = 0; q <= nbase; ++q) {
+                if (!cand[q] || open[q]) continue;
+                int delta = 0;
+                bool q_walks = false;
+                std::vector<int> left_walkers = walkers;
+                for (int j = 0; j < nf; ++j) {
+                    if (!(facs[j].left < q && q <= facs[j].right)) continue;
+                    bool w;
+                    const int cc = cost(facs[j].f, reg_base[q], &w);
+                    if (cc >= fc[j]) continue;
+                    delta += cc - fc[j];
+                    q_walks = q_walks || w;
+                    if (fw[j] && --left_walkers[where[j]] == 0) delta -= kWalk;  // a block emptied of walkers
+                }
+                if (q_walks) delta += kWalk;
+                if (delta < best_delta) {
+                    best_delta = delta;
+                    best_q = q;
+                }
+            }
+            if (best_q < 0) break;
+            open[best_q] = 1;
+            for (int j = 0; j < nf; ++j) {
+                if (!(facs[j].left < best_q && best_q <= facs[j].right)) continue;
+                bool w;
+                const int cc = cost(facs[j].f, reg_base[best_q], &w);
+                if (cc >= fc[j]) continue;
+                where[j] = best_q;
+                fc[j] = cc;
+                fw[j] = w;
+            }
+        }
+        std::vector<std::vector<Factor>> at(nbase + 1);
+        for (int j = 0; j < nf; ++j) {  // factors in queue order
+            const Factor &f = facs[j].f;
+            std::vector<Factor> &bf = at[where[j]];
+            bool merged = false;
+            if (f.type == DF_BIT)  // one-bit diagonals on the same bit multiply
+                for (Factor &g : bf)
+                    if (g.type == DF_BIT && g.bit == f.bit) {
+                        g.v0 *= f.v0;
+                        g.v1 *= f.v1;
+                        merged = true;
+                        break;
+                    }
+            if (!merged) bf.push_back(f);
+        }
+        for (int p = 0; p <= nbase; ++p) {
+            if (!at[p].empty()) {
+                Entry b{E_BLOCK};
+                b.fac = std::move(at[p]);
+                ent.push_back(std::move(b));
+            }
+            if (p < nbase) ent.push_back(base[p]);
+        }
+        ne = (int)ent.size();
+        needl.assign(ne, 0u);
+        for (int i = 0; i < ne; ++i) needl[i] = need_of(ent[i]);
+    }
+    // a diagonal block is placed in the stage of the next non-block entry
+    // (that stage opens before the block)
+    auto opener = [&](int i) {
+        while (i < ne && ent[i].kind == E_BLOCK) ++i;
+        return i;
     };
 
     TileParams<R> &P = *new TileParams<R>();
@@ -510,13 +636,14 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     open_stage(choose(0, (ne ? needl[0] : 0u) & highmask, highmask), natural);
     for (int i = 0; i < ne; ++i) {
         const Entry &e = ent[i];
-        if ((needl[i] & ~cur) != 0) {
+        const int oi = opener(i);
+        if (oi < ne && (needl[oi] & ~cur) != 0) {
             if (nst >= kTileMaxStages) return overflow();
             if (free_lanes) {
-                const uint32_t rset = choose(i, needl[i], (1u << k) - 1u);
-                open_stage(rset, lanes_for(i, rset));
+                const uint32_t rset = choose(oi, needl[oi], (1u << k) - 1u);
+                open_stage(rset, lanes_for(oi, rset));
             } else {
-                open_stage(choose(i, needl[i], highmask), natural);
+                open_stage(choose(oi, needl[oi], highmask), natural);
             }
         }
         if (nops + 1 > kTileMaxOps) return overflow();
@@ -550,10 +677,12 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             // constants (base, per-register-bit ratios) for the factors on
             // register bits alone; sign flips on two or more register bits become
             // TOP_FLIP ops; the others go to the factor table: outside-only
-            // first, then thread/mixed, pairs last
+            // complex factors first, then sign factors (a negation of the base or
+            // of one ratio under conditions), then thread/mixed complex factors,
+            // pairs last
             cd cbase = 1.0;
             std::vector<cd> cu(RB, cd(1.0));
-            std::vector<TileDFac<R>> outside, single, pair;
+            std::vector<TileDFac<R>> outside, signs, single, pair;
             std::vector<TileOp> flips;
             auto reg_pattern = [&](uint8_t mr) {
                 uint64_t pat = 0;
@@ -561,6 +690,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                     if ((r & mr) == mr) pat |= 1ull << r;
                 return pat;
             };
+            auto is_pm1 = [](const cd &v) { return v == cd(1.0, 0.0) || v == cd(-1.0, 0.0); };
             for (const Factor &f : e.fac) {
                 TileDFac<R> d;
                 std::memset(&d, 0, sizeof(d));
@@ -572,13 +702,27 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                         cu[d.a] *= f.v1 / f.v0;
                         continue;
                     }
+                    if (is_pm1(f.v0) && is_pm1(f.v1)) {  // +-1 values: a sign under the bit
+                        cbase *= f.v0;
+                        if (f.v1 != f.v0) {
+                            TileDFac<R> sg;
+                            std::memset(&sg, 0, sizeof(sg));
+                            sg.type = DF_SIGN;
+                            sg.a = 0x80;
+                            if (d.tkind == TB_THREAD) sg.mt = (uint32_t)d.tmask;
+                            else sg.mo = d.tmask;
+                            signs.push_back(sg);
+                        }
+                        continue;
+                    }
                     d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
                     d.v1 = mkc<R>((R)f.v1.real(), (R)f.v1.imag());
                     (d.tkind == TB_OUTSIDE ? outside : single).push_back(d);
                 } else {
                     split(f.mask, &d.mr, &d.mt, &d.mo);
                     const int nr = __builtin_popcount(d.mr);
-                    if (nr >= 2 && f.v0 == cd(-1.0, 0.0)) {  // a sign flip
+                    const bool sign = f.v0 == cd(-1.0, 0.0);
+                    if (nr >= 2 && sign) {  // a sign flip of registers
                         TileOp fo;
                         std::memset(&fo, 0, sizeof(fo));
                         fo.type = TOP_FLIP;
@@ -603,6 +747,13 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                         }
                         continue;
                     }
+                    if (sign && nr <= 1) {                // negate the base or one ratio
+                        d.type = DF_SIGN;
+                        d.a = nr ? d.mr : (uint8_t)0x80;
+                        d.mr = 0;
+                        signs.push_back(d);
+                        continue;
+                    }
                     d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
                     if (d.mr == 0 && d.mt == 0) {         // outside bits alone
                         outside.push_back(d);
@@ -612,8 +763,9 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                     (nr >= 2 ? pair : single).push_back(d);
                 }
             }
-            const int nf = (int)(outside.size() + single.size() + pair.size());
-            if (ndf + nf > kTileMaxDFac || nf > 255 || (int)outside.size() > 255) return overflow();
+            const int nf = (int)(outside.size() + signs.size() + single.size() + pair.size());
+            if (ndf + nf > kTileMaxDFac || nf > 255 || (int)outside.size() > 255 || (int)signs.size() > 255)
+                return overflow();
             if (nmat + 1 + RB > kTileMaxMat) return overflow();
             if (nops + 1 + (int)flips.size() > kTileMaxOps) return overflow();
             bool trivial = nf == 0 && cbase == cd(1.0);
@@ -629,7 +781,9 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             op.b = (uint8_t)nf;
             op.a = (uint8_t)pair.size();
             op.gl = (uint8_t)outside.size();
+            op.tkind = (uint8_t)signs.size();
             for (auto &d : outside) P.dfac[ndf++] = d;
+            for (auto &d : signs) P.dfac[ndf++] = d;
             for (auto &d : single) P.dfac[ndf++] = d;
             for (auto &d : pair) P.dfac[ndf++] = d;
         } else {
@@ -797,7 +951,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 continue;
             }
             if (ent[i].kind == E_BLOCK) {
-                fl += 12.0 * amps;
+                if (!ent[i].fac.empty()) fl += 12.0 * amps;
                 continue;
             }
             const LGate &g = G[ent[i].gi];

@@ -78,10 +78,13 @@ enum TileRotForm : uint8_t { ROT_TAN = 0, ROT_COT = 1 };
 //           or one outside bit (TB_OUTSIDE, global mask tmask);
 //   DF_PHASE: v0 where all required bits (mr register, mt thread, mo outside)
 //           are 1; for two or more register bits tmask holds the registers
-//           covered and a = 1 marks a sign flip (v0 = -1).
+//           covered;
+//   DF_SIGN: where the required bits mt, mo are 1, negate the block's ratio
+//           of register bit j (a = 1 << j) or its base (a = 0x80).
 // Factors on register bits alone are folded by the planner into the block's
-// constants (a base value, one ratio per register bit, a register flip mask).
-enum TileDFacType : uint8_t { DF_BIT = 0, DF_PHASE = 1 };
+// constants (a base value and one ratio per register bit); sign flips on two
+// or more register bits are TOP_FLIP ops.
+enum TileDFacType : uint8_t { DF_BIT = 0, DF_PHASE = 1, DF_SIGN = 2 };
 
 // Generators of TOP_GRAD (b field): Pauli X, Y, Z on one target, or the
 // projector on the all-ones block of the required bits (U1/CU1).
