@@ -344,6 +344,87 @@ def fused_tc(steps: int = 2) -> dict:
     return out
 
 
+def _peak_hbm() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def unfused_passes(n: int = 32, reps: int = 5) -> dict:
+    """One-gate passes (the plain unfused simulator) at n = 32: a dense 1-qubit
+    gate on the lowest and the highest index bit, a 2-qubit dense gate, CZ and
+    SWAP in complex64, and the dense 1-qubit gate in complex128; per pass the
+    CUDA-event time, the algorithmic bytes (2^n reads and writes of the
+    amplitudes the gate touches) and the fraction of the measured HBM peak."""
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    G = qi.Gate
+    u4 = qi.random_unitary(2, qi.rng(7))
+    cases = [("c64", "H on qubit n-1 (index bit 0)", G("H", (n - 1,))),
+             ("c64", "H on qubit 0 (index bit n-1)", G("H", (0,))),
+             ("c64", "U3 on qubit n/2", G("U3", (n // 2,), (), (0.3, 0.2, 0.1))),
+             ("c64", "dense 2-qubit on qubits (3, n-5)", G("UNITARY", (3, n - 5), (), (), u4)),
+             ("c64", "CZ(0, 1)", G("CZ", (0, 1))),
+             ("c64", "SWAP(2, n-3)", G("SWAP", (2, n - 3))),
+             ("c128", "H on qubit n-1 (index bit 0)", G("H", (n - 1,))),
+             ("c128", "U3 on qubit n/2", G("U3", (n // 2,), (), (0.3, 0.2, 0.1)))]
+    peak = _peak_hbm()
+    out = {"workload": f"one-gate passes, n={n}", "peak_hbm_GBps": peak, "passes": []}
+    st = None
+    cur = None
+    for dt, name, g in cases:
+        if dt != cur:
+            if st is not None:
+                st.close()
+                del st
+                torch.cuda.empty_cache()
+            st = qsim.State(n, dtype=dt).init_plus()
+            cur = dt
+        t = _time_cuda(lambda: st.apply([g], mode="unfused"), reps, warmup=2)
+        qsim.profile_collect()
+        qsim.profile_enable(True)
+        st.apply([g], mode="unfused")
+        torch.cuda.synchronize()
+        qsim.profile_enable(False)
+        prof = qsim.profile_collect()
+        nbytes = sum(v[2] for v in prof.values())
+        gbs = nbytes / (t / 1000.0) / 1e9
+        out["passes"].append({"dtype": dt, "gate": name, "ms": t, "GB": nbytes / 1e9, "GBps": gbs,
+                              "frac_of_measured_hbm": gbs / peak})
+    if st is not None:
+        st.close()
+        del st
+        torch.cuda.empty_cache()
+    return out
+
+
+def random_layer_c128(n: int = 33, layers: int = 2) -> dict:
+    """The random-layer circuit's first `layers` layers at n = 33 in complex128
+    (128 GiB state): tiled passes against the plain unfused simulator on the
+    same GPU, per-gate rates and the full 20-layer circuit time they project."""
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    gates = qi.random_layer_circuit(n, layers, seed=2)
+    full = len(qi.random_layer_circuit(n, 20, seed=2))
+    st = qsim.State(n, dtype="c128")
+    out = {"workload": f"random-layer circuit, first {layers} of 20 layers, n={n}, complex128",
+           "gates_timed": len(gates)}
+    for mode in ("tiled", "unfused"):
+        st.init_basis(0)
+        torch.cuda.synchronize()
+        t = _time_cuda(lambda: st.apply(gates, mode=mode), 1, warmup=0)
+        rate = len(gates) / (t / 1000.0)
+        out[mode] = {"ms": t, "gate_apps_per_s": rate, "projected_full_circuit_s": full / rate}
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(a):
     import torch
@@ -455,6 +536,8 @@ def run_ours(a):
         secondary["variational_adjoint"] = variational_adjoint()
         secondary["adiabatic_batch"] = adiabatic_batch()
         secondary["fused_tc"] = fused_tc()
+        secondary["unfused_passes"] = unfused_passes()
+        secondary["random_layer_c128_n33"] = random_layer_c128()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
