@@ -135,6 +135,32 @@ def alu_peak_tflops(dtype: str, sm_mhz: float) -> float:
     return FP64_TFLOPS
 
 
+TILED_SOURCES = ("kernels_tiled.cu", "tiled.h", "plan_tiled.cpp")
+LAUNCH_PROFILE = os.path.join(ROOT, "profiles", "launches_random_layer_n32_c64.md")
+
+
+def tiled_traffic(a):
+    """DRAM bytes per launch of the tiled kernel from the committed ncu launch
+    list, if it was taken on this workload from the current kernel sources
+    (same source hash), else None."""
+    import hashlib
+    import re
+    try:
+        h = hashlib.sha256()
+        for f in TILED_SOURCES:
+            with open(os.path.join(ROOT, "paper_2009_01845_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        with open(LAUNCH_PROFILE) as fh:
+            txt = fh.read()
+        m = re.search(r"kernel sources sha256\[:16\][^:]*: ([0-9a-f]{16})", txt)
+        b = re.search(r"tiled_kernel DRAM bytes per launch \(n = (\d+)\): (\d+)", txt)
+        if m and b and m.group(1) == h.hexdigest()[:16] and int(b.group(1)) == a.n and a.dtype == "c64":
+            return float(b.group(2))
+    except OSError:
+        pass
+    return None
+
+
 def roofline(name, rec, a, clk):
     """Roofline of one kernel class: whichever of HBM time (algorithmic bytes /
     measured copy bandwidth) and ALU time (algorithmic flops / peak of the
@@ -156,7 +182,9 @@ def roofline(name, rec, a, clk):
             "alu": {"achieved": tfl, "peak": alu, "unit": "TFLOP/s", "frac": f_alu,
                     "peak_source": ("FP32: 152 SMs x 128 lanes x 2 x median SM clock" if a.dtype == "c64"
                                     else "FP64 FMA microbenchmark on GB300")},
-            "traffic": None}
+            "traffic": tiled_traffic(a) if name == "tiled" else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                              "profiles/launches_random_layer_n32_c64.md (null if the kernel sources changed)"}
     if nbytes / (bw * 1e9) >= nflops / (alu * 1e12):
         base.update({"bound": "hbm", "achieved": gbs, "peak": bw, "unit": "GB/s", "frac": f_hbm})
     else:
