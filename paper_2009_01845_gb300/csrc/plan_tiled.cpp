@@ -159,6 +159,7 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
     facs->clear();
     std::vector<Entry> base;                  // non-factor entries in order
     std::vector<uint64_t> blocks_bits;        // bits each base entry does not commute on
+    std::vector<char> is_grad;                // base entry is a gradient op
     struct PF { Factor f; int pos; };         // factor and the base position it precedes
     std::vector<PF> pf;
     for (int gi : gates) {
@@ -181,6 +182,7 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
             e.coef = coef;
             base.push_back(e);
             blocks_bits.push_back(1ull << g.tbit[0]);
+            is_grad.push_back(0);
             pf.push_back({Factor{DF_BIT, g.tbit[0], 0, dl[0], dl[1]}, (int)base.size()});
             continue;
         }
@@ -201,20 +203,31 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
         uint64_t nb = 0;
         if (c == G_DENSE1 || c == G_DENSE2 || c == G_SWAP)
             for (int j = 0; j < g.k; ++j) nb |= 1ull << g.tbit[j];
-        if (c == G_GRAD || c == G_SINGLE) nb = ~0ull;  // barrier
+        is_grad.push_back(c == G_GRAD ? 1 : 0);
+        if (c == G_SINGLE) nb = ~0ull;  // barrier
+        // a gradient op <lambda|P|phi> is unchanged by a unitary diagonal
+        // applied to both phi and lambda when the diagonal commutes with P: Z
+        // and projector generators commute with every diagonal, X and Y with
+        // the diagonals that do not involve their target. (A scaled factor,
+        // the D_L of a factored gate, never crosses a gradient op: the
+        // readout is bilinear in the state.)
+        if (c == G_GRAD) nb = (g.grad_gen == GEN_X || g.grad_gen == GEN_Y) ? (1ull << g.tbit[0]) : 0ull;
         blocks_bits.push_back(nb);
     }
     const int nbase = (int)base.size();
     for (const PF &q : pf) {
         const uint64_t fb = factor_bits(q.f);
+        const bool unitary = std::abs(std::abs(q.f.v0) - 1.0) < 1e-12 &&
+                             (q.f.type != DF_BIT || std::abs(std::abs(q.f.v1) - 1.0) < 1e-12);
+        auto blocks = [&](int p) { return (blocks_bits[p] & fb) != 0 || (is_grad[p] && !unitary); };
         int left = -1, right = nbase;
         for (int p = q.pos - 1; p >= 0; --p)
-            if (blocks_bits[p] & fb) {
+            if (blocks(p)) {
                 left = p;
                 break;
             }
         for (int p = q.pos; p < nbase; ++p)
-            if (blocks_bits[p] & fb) {
+            if (blocks(p)) {
                 right = p;
                 break;
             }
@@ -308,9 +321,11 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         if ((pp.high >> b) & 1ull) gbit[nl++] = b;
     for (int i = 0; i < k; ++i) loc_of[gbit[i]] = i;
 
-    // Free lanes (every pass but the adjoint sweep): dense targets, lane bits
-    // included, must be register bits; stages move lanes to any bits.
-    const bool free_lanes = force_bit < 0;
+    // Free lanes: dense targets, lane bits included, must be register bits;
+    // stages move lanes to any bits. (In the adjoint sweep the forced bit that
+    // tells phi from lambda is the highest tile bit, so it is always the top
+    // register bit, as the gradient ops require.)
+    const bool free_lanes = true;
     std::vector<FactorSpan> facs;
     const std::vector<Entry> base = build_entries(G, cls, slot, pp.gates, free_lanes, &facs);
     // needed local register bits of an entry
