@@ -732,10 +732,14 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                 }
             }
         }
-        // ---------------- store (last stage mapping)
+        // ---------------- store (last stage mapping: its lanes hold index bits 0
+        // and 1, or bit 0 for complex128, so every warp store covers whole sectors)
         {
             const TileStage &sl = p.st[p.n_stages - 1];
-            uint64_t gt = tbase | (uint64_t)lane;
+            uint64_t gt = tbase;
+#pragma unroll
+            for (int i = 0; i < kTileLaneBits; ++i)
+                if ((lane >> i) & 1) gt |= 1ull << p.gbit[sl.lloc[i]];
 #pragma unroll
             for (int w = 0; w < WB; ++w)
                 if ((warp >> w) & 1) gt |= 1ull << p.gbit[sl.wloc[w]];

@@ -375,17 +375,16 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         }
         return r;
     };
-    // lanes: the 5 remaining bits used soonest; ordered so that the lanes of a
-    // half-warp (complex64) / quarter-warp (complex128) have distinct residues
+    // lanes: the 5 lowest bits that are not registers (ops never act on lane
+    // bits; keeping index bits 0 and 1 on lanes lets the last stage store whole
+    // 32-byte sectors from any lane map), ordered, where possible, so that the
+    // lanes of a half-warp (complex64) / quarter-warp (complex128) have
+    // distinct residues, which the default swizzle then serves
     const int half = sizeof(R) == 4 ? 4 : 3;
-    auto lanes_for = [&](int from, uint32_t rset) {
-        std::vector<std::pair<int, int>> rank;
-        for (int lb = 0; lb < k; ++lb)
-            if (!((rset >> lb) & 1u)) rank.push_back({next_use(from, lb), lb});
-        std::sort(rank.begin(), rank.end());
+    auto lanes_for = [&](int, uint32_t rset) {
         std::vector<int> L;
-        for (int x = 0; x < kTileLaneBits; ++x) L.push_back(rank[x].second);
-        std::sort(L.begin(), L.end());
+        for (int lb = 0; lb < k && (int)L.size() < kTileLaneBits; ++lb)
+            if (!((rset >> lb) & 1u)) L.push_back(lb);
         std::vector<int> best = L;
         do {
             bool okr = true;
@@ -912,12 +911,16 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         P.op[nops++] = op;
         P.st[nst - 1].op_end = (uint16_t)nops;
     }
-    // the last stage stores the tile: lanes back on the 5 lowest bits
+    // the last stage stores the tile through its own lane map when every warp
+    // store covers whole 32-byte sectors (index bits 0 and 1 on lanes for
+    // complex64, bit 0 for complex128); otherwise one more stage puts the lanes
+    // back on the 5 lowest bits
     {
         const TileStage &last = P.st[nst - 1];
-        bool natural_lanes = true;
-        for (int x = 0; x < kTileLaneBits; ++x) natural_lanes &= last.lloc[x] == x;
-        if (!natural_lanes) {
+        const uint32_t sector_bits = sizeof(R) == 4 ? 3u : 1u;
+        uint32_t lanes = 0;
+        for (int x = 0; x < kTileLaneBits; ++x) lanes |= 1u << last.lloc[x];
+        if ((lanes & sector_bits) != sector_bits) {
             if (nst >= kTileMaxStages) return overflow();
             open_stage(choose(ne, 0u, highmask), natural);
         }
