@@ -494,8 +494,12 @@ template <typename R> struct ExpP {
     int8_t zc[kMaxTermsPerLaunch];   // second Z bit, or -1
     int8_t zn[kMaxTermsPerLaunch];   // number of Z bits: 0, 1, 2 or 3 (= more)
     int8_t ys[kMaxTermsPerLaunch];   // (-1)^{popcount(z_t & xb)}: the term's sign at x ^ xb relative to x
+    // one- and two-bit terms: bits 0-7 first Z bit a, 8-15 second bit b (= a
+    // for one bit), bit 16: two bits; parity = ((x >> a) ^ ((x >> b) & two)) & 1
+    uint32_t zw[kMaxTermsPerLaunch];
     int nt;
     int nv;           // terms [0, nv) touch the chunk bits (see expect_partial_kernel)
+    int nvf, nff;     // [0, nvf) and [nv, nff): one- and two-bit terms; the rest general
     uint64_t xb;      // X mask in index bits (0 for the diagonal group)
     int n;
     int ms;           // member shift
@@ -521,17 +525,20 @@ constexpr int kExpChunkLo = 8, kExpChunkBits = 4;
 
 // Host: order the terms so that those whose Z bits meet the chunk bits come
 // first (p->nv of them); the others are constant over a chunk and are summed
-// once per chunk. Also the per-term sign between x and x ^ xb.
+// once per chunk. Within each part the one- and two-bit terms come first
+// (evaluated by shifts), then the others (popcount). Also the per-term sign
+// between x and x ^ xb.
 template <typename R> static void exp_order_terms(ExpP<R> *p) {
     uint64_t cx = 0;
     for (int b = kExpChunkLo; b < kExpChunkLo + kExpChunkBits; ++b)
         cx |= 1ull << ((p->xb && b >= p->hb) ? b + 1 : b);
     ExpP<R> q = *p;
     int k = 0;
-    for (int pass = 0; pass < 2; ++pass)
+    for (int pass = 0; pass < 4; ++pass) {
         for (int t = 0; t < p->nt; ++t) {
             const bool varying = (p->zb[t] & cx) != 0;
-            if (varying != (pass == 0)) continue;
+            const bool fast = p->zn[t] == 1 || p->zn[t] == 2;
+            if (varying != (pass < 2) || fast != (pass % 2 == 0)) continue;
             q.cre[k] = p->cre[t];
             q.cim[k] = p->cim[t];
             q.zb[k] = p->zb[t];
@@ -539,9 +546,15 @@ template <typename R> static void exp_order_terms(ExpP<R> *p) {
             q.zc[k] = p->zc[t];
             q.zn[k] = p->zn[t];
             q.ys[k] = (int8_t)(__builtin_popcountll(p->zb[t] & p->xb) & 1);
-            if (pass == 0) q.nv = k + 1;
+            q.zw[k] = fast ? ((uint32_t)p->za[t] | ((uint32_t)(p->zn[t] == 2 ? p->zc[t] : p->za[t]) << 8) |
+                              ((uint32_t)(p->zn[t] == 2) << 16))
+                           : 0u;
             ++k;
         }
+        if (pass == 0) q.nvf = k;
+        if (pass == 1) q.nv = k;
+        if (pass == 2) q.nff = k;
+    }
     *p = q;
 }
 
@@ -559,38 +572,64 @@ __device__ __forceinline__ void exp_terms(const ExpP<R> &p, int t0, int t1, uint
     }
 }
 
+// the same for one- and two-bit terms, by shifts on an index of type U
+template <typename R, typename U>
+__device__ __forceinline__ void exp_terms_fast(const ExpP<R> &p, int t0, int t1, U x, R &fr, R &fi, R &gr,
+                                               R &gi) {
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t w = p.zw[t];
+        const bool sx = ((x >> (w & 0xffu)) ^ ((x >> ((w >> 8) & 0xffu)) & (U)((w >> 16) & 1u))) & 1u;
+        const R cr = sx ? -p.cre[t] : p.cre[t], ci = sx ? -p.cim[t] : p.cim[t];
+        fr += cr;
+        fi += ci;
+        gr += p.ys[t] ? -cr : cr;
+        gi += p.ys[t] ? -ci : ci;
+    }
+}
+
+// all terms of [t0, t1) that the ordering put in a fast or general run
+template <typename R, typename U>
+__device__ __forceinline__ void exp_range(const ExpP<R> &p, bool varying, U x, R &fr, R &fi, R &gr, R &gi) {
+    if (varying) {
+        exp_terms_fast<R, U>(p, 0, p.nvf, x, fr, fi, gr, gi);
+        exp_terms(p, p.nvf, p.nv, (uint64_t)x, fr, fi, gr, gi);
+    } else {
+        exp_terms_fast<R, U>(p, p.nv, p.nff, x, fr, fi, gr, gi);
+        exp_terms(p, p.nff, p.nt, (uint64_t)x, fr, fi, gr, gi);
+    }
+}
+
 // Per member: sum_x |psi[x]|^2 f_0(x) (diagonal group), or sum over the pairs
 // (x, y = x ^ xb) with bit hb of x clear of conj(psi[y]) psi[x] f(x) +
 // conj(psi[x]) psi[y] f(y). For 2^12 or more free indices a thread takes
 // chunks of 16 amplitudes (consecutive threads on consecutive addresses for
 // each c); terms that do not touch the chunk bits are summed once per chunk,
-// the others per amplitude. Runs of 16 are summed in R, then in FP64.
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> *__restrict__ psi,
-                                                                     const __grid_constant__ ExpP<R> p,
-                                                                     double2 *__restrict__ part) {
-    const V<R> *q = psi + ((uint64_t)blockIdx.y << p.ms);
+// the others per amplitude. Runs of 16 are summed in R, then in FP64. U: the
+// index type (32-bit while the indices fit).
+template <typename R, typename U>
+__device__ __forceinline__ double2 expect_body(const V<R> *__restrict__ q, const ExpP<R> &p) {
     const uint64_t cnt = 1ull << p.n_free;
     double ar = 0.0, ai = 0.0;
-    const uint64_t lo = (1ull << p.hb) - 1ull;
-    auto insert0 = [&](uint64_t j) { return p.xb ? (((j >> p.hb) << (p.hb + 1)) | (j & lo)) : j; };
+    const U lo = (U)((1ull << p.hb) - 1ull);
+    const U xb = (U)p.xb;
+    auto insert0 = [&](U j) { return p.xb ? (U)(((j >> p.hb) << (p.hb + 1)) | (j & lo)) : j; };
     if (p.n_free >= kExpChunkLo + kExpChunkBits) {
         const uint64_t nchunks = cnt >> (kExpChunkLo + kExpChunkBits);
         for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-            const uint64_t j0 = (ch << (kExpChunkLo + kExpChunkBits)) | threadIdx.x;
+            const U j0 = (U)((ch << (kExpChunkLo + kExpChunkBits)) | threadIdx.x);
             R f0r = 0, f0i = 0, g0r = 0, g0i = 0;
-            exp_terms(p, p.nv, p.nt, insert0(j0), f0r, f0i, g0r, g0i);
+            exp_range<R, U>(p, false, insert0(j0), f0r, f0i, g0r, g0i);
             R rr = 0, ri = 0;
             if (p.xb == 0) {
                 // all 16 loads in flight before the arithmetic
                 V<R> av[1 << kExpChunkBits];
 #pragma unroll
-                for (int c = 0; c < (1 << kExpChunkBits); ++c) av[c] = q[j0 | ((uint64_t)c << kExpChunkLo)];
+                for (int c = 0; c < (1 << kExpChunkBits); ++c) av[c] = q[j0 | ((U)c << kExpChunkLo)];
 #pragma unroll
                 for (int c = 0; c < (1 << kExpChunkBits); ++c) {
-                    const uint64_t x = j0 | ((uint64_t)c << kExpChunkLo);
+                    const U x = j0 | ((U)c << kExpChunkLo);
                     R fr = f0r, fi = 0, gr = 0, gi = 0;
-                    exp_terms(p, 0, p.nv, x, fr, fi, gr, gi);
+                    exp_range<R, U>(p, true, x, fr, fi, gr, gi);
                     rr = fma(fr, fma(av[c].x, av[c].x, av[c].y * av[c].y), rr);
                 }
             } else {
@@ -600,15 +639,15 @@ __global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> 
                     V<R> av[H], bv[H];
 #pragma unroll
                     for (int c = 0; c < H; ++c) {
-                        const uint64_t x = insert0(j0 | ((uint64_t)(h * H + c) << kExpChunkLo));
+                        const U x = insert0(j0 | ((U)(h * H + c) << kExpChunkLo));
                         av[c] = q[x];
-                        bv[c] = q[x ^ p.xb];
+                        bv[c] = q[x ^ xb];
                     }
 #pragma unroll
                     for (int c = 0; c < H; ++c) {
-                        const uint64_t x = insert0(j0 | ((uint64_t)(h * H + c) << kExpChunkLo));
+                        const U x = insert0(j0 | ((U)(h * H + c) << kExpChunkLo));
                         R fxr = f0r, fxi = f0i, fyr = g0r, fyi = g0i;
-                        exp_terms(p, 0, p.nv, x, fxr, fxi, fyr, fyi);
+                        exp_range<R, U>(p, true, x, fxr, fxi, fyr, fyi);
                         const V<R> a = av[c], b = bv[c];
                         // conj(b) a f(x) + conj(a) b f(y), with conj(a) b = conj(conj(b) a)
                         const R abr = b.x * a.x + b.y * a.y;
@@ -623,15 +662,16 @@ __global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> 
         }
     } else {
         const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-        for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += stride) {
-            const uint64_t x = insert0(j);
+        for (uint64_t jj = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; jj < cnt; jj += stride) {
+            const U x = insert0((U)jj);
             R fxr = 0, fxi = 0, fyr = 0, fyi = 0;
-            exp_terms(p, 0, p.nt, x, fxr, fxi, fyr, fyi);
+            exp_range<R, U>(p, true, x, fxr, fxi, fyr, fyi);
+            exp_range<R, U>(p, false, x, fxr, fxi, fyr, fyi);
             if (p.xb == 0) {
                 const V<R> a = q[x];
                 ar += (double)(fxr * fma(a.x, a.x, a.y * a.y));
             } else {
-                const V<R> a = q[x], b = q[x ^ p.xb];
+                const V<R> a = q[x], b = q[x ^ xb];
                 const R abr = b.x * a.x + b.y * a.y;
                 const R abi = b.x * a.y - b.y * a.x;
                 ar += (double)(abr * (fxr + fyr) - abi * (fxi - fyi));
@@ -639,7 +679,17 @@ __global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> 
             }
         }
     }
-    const double2 r = block_sum2(ar, ai);
+    return make_double2(ar, ai);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> *__restrict__ psi,
+                                                                     const __grid_constant__ ExpP<R> p,
+                                                                     double2 *__restrict__ part) {
+    const V<R> *q = psi + ((uint64_t)blockIdx.y << p.ms);
+    // indices within a member fit 32 bits up to n = 32
+    const double2 acc = p.n <= 32 ? expect_body<R, uint32_t>(q, p) : expect_body<R, uint64_t>(q, p);
+    const double2 r = block_sum2(acc.x, acc.y);
     if (threadIdx.x == 0) {
         double2 *slot = &part[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x];
         if (p.accumulate) {
@@ -718,7 +768,10 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
                 std::memcpy(&pf.zc, &p.zc, sizeof(p.zc));
                 std::memcpy(&pf.zn, &p.zn, sizeof(p.zn));
                 std::memcpy(&pf.ys, &p.ys, sizeof(p.ys));
+                std::memcpy(&pf.zw, &p.zw, sizeof(p.zw));
                 pf.nv = p.nv;
+                pf.nvf = p.nvf;
+                pf.nff = p.nff;
                 for (int j = 0; j < kMaxTermsPerLaunch; ++j) {
                     pf.cre[j] = (float)p.cre[j];
                     pf.cim[j] = (float)p.cim[j];
