@@ -45,6 +45,8 @@ static qs_status with_view(qs_state *base, int n, int ms, size_t offset_amps, F 
     base->ptab_bytes = v.ptab_bytes;
     base->itab = v.itab;
     base->itab_bytes = v.itab_bytes;
+    base->ithr = v.ithr;
+    base->ithr_bytes = v.ithr_bytes;
     base->host_pinned = v.host_pinned;
     base->host_pinned_doubles = v.host_pinned_doubles;
     return st;

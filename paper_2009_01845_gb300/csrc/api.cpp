@@ -129,13 +129,15 @@ qs_status qs_state_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *s
 qs_status qs_state_destroy(qs_state *s) {
     QS_GUARD_BEGIN
     if (!s) return QS_OK;
-    if (s->owns || s->scratch || s->host_pinned || s->gtab || s->ptab || s->itab) cudaStreamSynchronize(s->stream);
+    if (s->owns || s->scratch || s->host_pinned || s->gtab || s->ptab || s->itab || s->ithr)
+        cudaStreamSynchronize(s->stream);
     if (s->owns && s->data) cudaFree(s->data);
     if (s->scratch) cudaFree(s->scratch);
     if (s->host_pinned) cudaFreeHost(s->host_pinned);
     if (s->gtab) cudaFree(s->gtab);
     if (s->ptab) cudaFree(s->ptab);
     if (s->itab) cudaFree(s->itab);
+    if (s->ithr) cudaFree(s->ithr);
     plan_cache_release(s);
     delete s;
     return QS_OK;

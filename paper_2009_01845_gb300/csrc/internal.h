@@ -36,6 +36,9 @@ struct qs_state {
     double *itab = nullptr;
     size_t itab_bytes = 0;
     uint32_t ising_stride = 0;
+    // per-pass tables of the Ising op's tile-independent parts (see tiled.h)
+    double *ithr = nullptr;
+    size_t ithr_bytes = 0;
 };
 
 namespace qsim {

@@ -167,7 +167,8 @@ __device__ __forceinline__ R dispatch_grad_xy(const V<R> *a, int j, int gen, uin
 // exp(i angle) with the angle reduced to [-pi, pi] in FP64 first
 template <typename R> __device__ __forceinline__ V<R> expi(double angle) {
     const double two_pi = 6.283185307179586476925286766559;
-    const double a = angle - two_pi * rint(angle / two_pi);
+    const double inv_two_pi = 0.15915494309189533576888376337251;  // multiply: no FP64 division
+    const double a = angle - two_pi * rint(angle * inv_two_pi);
     if constexpr (sizeof(R) == 4) {
         float sn, cs;
         sincosf((float)a, &sn, &cs);
@@ -183,10 +184,13 @@ template <typename R> __device__ __forceinline__ V<R> conjc(V<R> v) { return mkc
 
 // psi_x *= exp(-i tau E(x)) for an Ising energy E(x) = c + sum_i h_i z_i +
 // sum_{i<j} J_ij z_i z_j, z_i = 1 - 2 x_i. Split over the tile: the outside bits
-// and the thread's lane/warp bits give a per-thread constant C and per-register-
-// bit fields w_j (FP64), the register-register couplings a table Q[r]; then
-// E = C + sum_j w_j - 2 sum_{j: r_j = 1} w_j + Q[r] and the phase is a product
-// of per-thread factors, walked over the registers in Gray-code order.
+// give per-tile fields s_g on the tile bits and a per-tile constant; the
+// thread's lane/warp bits add their mutual coupling energy and their fields on
+// the register bits, which depend on the member only and come from the op's
+// table (filled once per pass by ising_table_kernel), like the register-pair
+// phases. Then E = C + sum_j w_j - 2 sum_{j: r_j = 1} w_j + Q[r] per register,
+// a product of per-thread factors walked over the registers in Gray-code
+// order; angles are evaluated in FP64.
 template <typename R, int RB>
 __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, const TileOp &op, const TileStage &st,
                                             uint64_t tbase, uint64_t member, int lane, int warp, double *s_g,
@@ -196,6 +200,7 @@ __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, con
     const int nq = p.nq;
     const double *J = p.ising + member * p.ising_stride;
     const double *hv = J + (size_t)nq * nq;
+    const double *tab = p.ising_thr + ((size_t)op.m * (p.total_tiles >> p.n_free) + member) * p.ising_thr_stride;
     const int tid = threadIdx.x;
     if (tid < p.k) {
         const int g = p.gbit[tid];
@@ -216,47 +221,22 @@ __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, con
         if (tid == 32) *s_eo = acc + hv[nq];
     } else if (tid >= 64 && tid < 64 + NR) {
         const int r = tid - 64;
-        double q = 0.0;
-        for (int i = 0; i < RB; ++i)
-            for (int j = i + 1; j < RB; ++j) {
-                const double c = J[p.gbit[st.rloc[i]] * nq + p.gbit[st.rloc[j]]];
-                q += (((r >> i) ^ (r >> j)) & 1) ? -c : c;
-            }
-        s_qp[r] = expi<R>(-tau * q);
+        const double *qp = tab + (size_t)(32 << TileCfg<R>::WB) * (1 + RB);
+        s_qp[r] = mkc<R>((R)qp[2 * r], (R)qp[2 * r + 1]);
     }
     __syncthreads();
-    // the thread's 5 + WB bits: lanes and warp bits
     constexpr int WB = TileCfg<R>::WB;
-    constexpr int TB = kTileLaneBits + WB;
-    int tg[TB], tlc[TB];
-    double tz[TB];
+    const double *row = tab + (size_t)tid * (1 + RB);
+    double C = *s_eo + row[0];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        tlc[i] = st.lloc[i];
-        tg[i] = p.gbit[st.lloc[i]];
-        tz[i] = ((lane >> i) & 1) ? -1.0 : 1.0;
-    }
+    for (int i = 0; i < 5; ++i) C += ((lane >> i) & 1) ? -s_g[st.lloc[i]] : s_g[st.lloc[i]];
 #pragma unroll
-    for (int w = 0; w < WB; ++w) {
-        tlc[5 + w] = st.wloc[w];
-        tg[5 + w] = p.gbit[st.wloc[w]];
-        tz[5 + w] = ((warp >> w) & 1) ? -1.0 : 1.0;
-    }
-    double C = *s_eo;
-#pragma unroll
-    for (int i = 0; i < TB; ++i) {
-        C += s_g[tlc[i]] * tz[i];
-#pragma unroll
-        for (int j = i + 1; j < TB; ++j) C += J[tg[i] * nq + tg[j]] * tz[i] * tz[j];
-    }
+    for (int w = 0; w < WB; ++w) C += ((warp >> w) & 1) ? -s_g[st.wloc[w]] : s_g[st.wloc[w]];
     double wsum = 0.0;
     V<R> u[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) {
-        const int gj = p.gbit[st.rloc[j]];
-        double wj = s_g[st.rloc[j]];
-#pragma unroll
-        for (int i = 0; i < TB; ++i) wj += J[gj * nq + tg[i]] * tz[i];
+        const double wj = s_g[st.rloc[j]] + row[1 + j];
         wsum += wj;
         u[j] = expi<R>(2.0 * tau * wj);
     }
@@ -280,6 +260,49 @@ __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, con
         }
     }
     __syncthreads();
+}
+
+// The Ising op's tile-independent parts, one CTA per member, one thread per
+// thread pattern (lane bits, then warp bits): the coupling energy among the
+// pattern's bits and their field on every register bit (FP64); threads below
+// 2^rb also the (cos, sin) of -tau times the register-pair energy.
+__global__ void __launch_bounds__(256) ising_table_kernel(const __grid_constant__ IsingTabP tp) {
+    const int member = blockIdx.x, tid = threadIdx.x;
+    const int nq = tp.nq;
+    const double *J = tp.ising + (size_t)member * tp.ising_stride;
+    double *base = tp.out + (size_t)member * tp.stride;
+    double z[kTileLaneBits + kTileMaxWarpBits];
+    for (int i = 0; i < tp.tb; ++i) z[i] = ((tid >> i) & 1) ? -1.0 : 1.0;
+    double e = 0.0;
+    for (int i = 0; i < tp.tb; ++i)
+        for (int j = i + 1; j < tp.tb; ++j) e += J[tp.tg[i] * nq + tp.tg[j]] * z[i] * z[j];
+    double *row = base + (size_t)tid * (1 + tp.rb);
+    row[0] = e;
+    for (int j = 0; j < tp.rb; ++j) {
+        double w = 0.0;
+        for (int i = 0; i < tp.tb; ++i) w += J[tp.rg[j] * nq + tp.tg[i]] * z[i];
+        row[1 + j] = w;
+    }
+    if (tid < (1 << tp.rb)) {
+        double q = 0.0;
+        for (int i = 0; i < tp.rb; ++i)
+            for (int j = i + 1; j < tp.rb; ++j) {
+                const double c = J[tp.rg[i] * nq + tp.rg[j]];
+                q += (((tid >> i) ^ (tid >> j)) & 1) ? -c : c;
+            }
+        const V<double> v = expi<double>(-tp.tau * q);
+        double *qp = base + (size_t)blockDim.x * (1 + tp.rb);
+        qp[2 * tid] = v.x;
+        qp[2 * tid + 1] = v.y;
+    }
+}
+
+qs_status k_ising_table(qs_state *s, const IsingTabP &tp) {
+    if (tp.members <= 0) return QS_OK;
+    ProfScope _ps(s->stream, KC_TROTTER_DIAG);
+    ising_table_kernel<<<tp.members, 256, 0, s->stream>>>(tp);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
 }
 
 // acc + c * v on both components: one packed FMA for float pairs

@@ -130,6 +130,8 @@ static qs_status autotune(qs_plan *p) {
     scratch.ptab_bytes = 0;
     scratch.itab = nullptr;
     scratch.itab_bytes = 0;
+    scratch.ithr = nullptr;
+    scratch.ithr_bytes = 0;
     scratch.ms = s->n;
     QS_CUDA_TRY(cudaMalloc(&scratch.data, bytes));
     qs_status st = QS_OK;
@@ -156,6 +158,7 @@ static qs_status autotune(qs_plan *p) {
     if (scratch.ptab) cudaFree(scratch.ptab);
     if (scratch.host_pinned) cudaFreeHost(scratch.host_pinned);
     if (scratch.itab) cudaFree(scratch.itab);
+    if (scratch.ithr) cudaFree(scratch.ithr);
     if (st != QS_OK) return st;
     p->mode = best_mode;
     p->opts.fuse_qubits = best_w;

@@ -25,6 +25,7 @@
 namespace qsim {
 
 qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p);
+qs_status k_ising_table(qs_state *s, const IsingTabP &tp);
 qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p);
 
 namespace {
@@ -571,7 +572,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     P.ising_stride = s->ising_stride;
     P.nq = n;
     for (int i = 0; i < k; ++i) P.tile_mask |= 1ull << gbit[i];
-    int ngrad = 0, ndf = 0;
+    int ngrad = 0, ndf = 0, nising = 0;
 
     int nops = 0, nmat = 0, nst = 0;
     uint32_t cur = 0, curL = 0;
@@ -878,6 +879,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 op.type = TOP_ISING;
                 const double tau = g.m[0].real();
                 std::memcpy(&op.tmask, &tau, sizeof(double));
+                op.m = (uint32_t)nising++;  // index of the op's table
                 break;
             }
             case G_GRAD: {
@@ -993,6 +995,44 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             fl += amps * per / (double)(1ull << req);
         }
         prof_add_work(KC_TILED, 2.0 * amps * sizeof(V<R>), fl);
+    }
+    if (nising > 0) {
+        // the Ising ops' tile-independent tables, once per pass
+        const int threads = tile_threads(s->dtype);
+        const uint32_t stride = ising_thr_stride(RB, threads);
+        const size_t doubles = (size_t)nising * s->batch * stride;
+        if (s->ithr_bytes < doubles * sizeof(double)) {
+            if (s->ithr) {
+                QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+                cudaFree(s->ithr);
+                s->ithr = nullptr;
+                s->ithr_bytes = 0;
+            }
+            QS_CUDA_TRY(cudaMalloc(&s->ithr, doubles * sizeof(double)));
+            s->ithr_bytes = doubles * sizeof(double);
+        }
+        P.ising_thr = s->ithr;
+        P.ising_thr_stride = stride;
+        for (int st = 0; st < nst; ++st)
+            for (int o = P.st[st].op_begin; o < P.st[st].op_end; ++o) {
+                const TileOp &op = P.op[o];
+                if (op.type != TOP_ISING) continue;
+                IsingTabP tp;
+                std::memset(&tp, 0, sizeof(tp));
+                tp.tb = kTileLaneBits + TileCfg<R>::WB;
+                tp.rb = RB;
+                for (int i = 0; i < kTileLaneBits; ++i) tp.tg[i] = (int8_t)P.gbit[P.st[st].lloc[i]];
+                for (int w = 0; w < TileCfg<R>::WB; ++w) tp.tg[kTileLaneBits + w] = (int8_t)P.gbit[P.st[st].wloc[w]];
+                for (int j = 0; j < RB; ++j) tp.rg[j] = (int8_t)P.gbit[P.st[st].rloc[j]];
+                std::memcpy(&tp.tau, &op.tmask, sizeof(double));
+                tp.ising = s->itab;
+                tp.ising_stride = s->ising_stride;
+                tp.nq = n;
+                tp.stride = stride;
+                tp.members = s->batch;
+                tp.out = s->ithr + (size_t)op.m * s->batch * stride;
+                QS_TRY(k_ising_table(s, tp));
+            }
     }
     if constexpr (sizeof(R) == 4)
         return k_tiled_pass_c64(s, P);

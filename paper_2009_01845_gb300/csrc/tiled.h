@@ -159,6 +159,13 @@ template <typename R> struct TileParams {
     const double *ising;
     uint32_t ising_stride;
     int nq;
+    // per Ising op (index in op.m) and member: the tile-independent parts,
+    // ising_thr_stride doubles per member: for each thread (256) the coupling
+    // energy among its lane/warp bits and, per register bit j, the field those
+    // bits put on j; then (cos, sin) of -tau times the register-pair energy of
+    // each register index
+    const double *ising_thr;
+    uint32_t ising_thr_stride;
     uint64_t tile_mask;   // global bits of the tile
     TileDFac<R> dfac[kTileMaxDFac];
     TileStage st[kTileMaxStages];
@@ -167,5 +174,23 @@ template <typename R> struct TileParams {
 };
 
 static_assert(sizeof(TileParams<double>) <= 32700, "kernel parameter block too large");
+
+// Inputs of the Ising-table kernel for one op: global bits of the stage's
+// thread bits (lanes 0..4, then warps) and register bits, tau, and where the
+// op's tables start.
+struct IsingTabP {
+    int8_t tg[kTileLaneBits + kTileMaxWarpBits];
+    int8_t rg[6];
+    int tb, rb;
+    double tau;
+    const double *ising;
+    uint32_t ising_stride;
+    int nq;
+    double *out;
+    uint32_t stride;   // doubles per member
+    int members;
+};
+
+inline uint32_t ising_thr_stride(int rb, int threads) { return (uint32_t)(threads * (1 + rb) + 2 * (1 << rb)); }
 
 }  // namespace qsim
