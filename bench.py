@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--n", "--qubits", dest="n", type=int, default=32)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--layers", type=int, default=20)
     ap.add_argument("--mode", default="auto", choices=["auto", "unfused", "tiled", "fused"])
@@ -453,6 +453,27 @@ def random_layer_c128(n: int = 33, layers: int = 2) -> dict:
     return out
 
 
+# ------------------------------------------------------------------ multi-rank helpers
+def max_over_ranks(x: float, world: int) -> float:
+    """The maximum of x over all ranks (the slowest replica sets the job's
+    time); x itself at world size 1. Uses the process group's backend (a CUDA
+    tensor for NCCL, a CPU tensor for gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, gates_per_step: int, ms_per_step: float) -> float:
+    """Gate applications per second of the whole job: every replica applies the
+    step's gates once per step (weak scaling), timed by the slowest replica."""
+    return world * gates_per_step / (ms_per_step / 1000.0)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(a):
     import torch
@@ -519,12 +540,8 @@ def run_ours(a):
     clk = clocks.stop()
     qsim.profile_enable(False)
     prof = qsim.profile_collect()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * len(gates) / (ms / 1000.0)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, world)
+    value = whole_job_value(world, len(gates), ms)
 
     # roofline of the dominant kernel class: algorithmic bytes and flops tallied
     # by the library per launch, over the CUDA-event time of those launches
