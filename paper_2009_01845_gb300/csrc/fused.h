@@ -11,12 +11,17 @@ namespace qsim {
 struct FusedP {
     float2 u[1024];          // the block's 32 x 32 complex matrix, row-major
     uint64_t chunk_mask;     // the 11 index bits a chunk spans (block bits + 6 column bits)
-    uint64_t hi_mask;        // the remaining index bits (chunk number)
+    InsertBits cins;         // sorted positions of the chunk bits (chunk number -> index)
     int chunk_shift;         // log2(chunks per member) = n - 11
     int ms;                  // member shift
     uint64_t total_chunks;
-    uint8_t lmap[2048];      // chunk-local thread index -> local row (0..31)
-    uint8_t cmap[2048];      // chunk-local thread index -> column (0..63)
+    // element i = t + 256 h of a chunk (t: thread, h = 0..7) sits at address
+    // offset dep(t) | dhi[h], row rlo(t) | rhi[h], column clo(t) | chi[h]: the
+    // chunk bits split between the block (row) and the columns
+    uint64_t dhi[8];
+    uint8_t rhi[8], chi[8];
+    uint8_t lmap[256];       // row of thread t's bits (h = 0)
+    uint8_t cmap[256];       // column of thread t's bits (h = 0)
 };
 
 // Apply a 32 x 32 complex matrix U (row-major, local index MSB = bits[0]) to the

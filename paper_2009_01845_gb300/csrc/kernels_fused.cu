@@ -10,11 +10,14 @@
 // b = b_hi + b_lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32:
 // about FP32 accuracy for complex64 states.
 //
-// A CTA (8 warps) loops over chunks of 64 columns: the chunk's 2048 amplitudes
-// are loaded with consecutive threads on consecutive addresses, split into hi
-// and lo TF32 planes in shared memory (column-major, padded against bank
-// conflicts), multiplied by warp-level m16n8k8 TF32 MMAs (warp w owns rows
-// 16 (w & 3) .. + 15 and columns 32 (w >> 2) .. + 31), and written back.
+// A CTA (8 warps) loops over chunks of 64 columns (2048 amplitudes). The next
+// chunk is fetched with cp.async into a raw staging buffer (consecutive
+// threads on consecutive addresses) while the current one is multiplied; each
+// chunk is split from the raw buffer into hi and lo TF32 planes (column-major,
+// padded, rows XOR-swizzled by column group so that both the staging stores
+// and the MMA operand loads hit distinct banks), multiplied by warp-level
+// m16n8k8 TF32 MMAs (warp w owns rows 16 (w & 3) .. + 15 and columns
+// 32 (w >> 2) .. + 31), staged back and written out.
 #include <algorithm>
 #include <cstring>
 
@@ -28,6 +31,8 @@ namespace qsim {
 constexpr int kFCols = 64;           // columns per chunk
 constexpr int kFLd = 68;             // padded column stride (floats) in shared memory
 constexpr int kFThreads = 256;
+constexpr int kFElems = 2048;        // amplitudes per chunk
+constexpr size_t kFSmem = kFElems * sizeof(float2) + 2 * kFCols * kFLd * sizeof(float);
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -43,23 +48,25 @@ __device__ __forceinline__ void mma_tf32(float *d, const uint32_t *a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// scatter the low bits of v over the positions of mask (ascending)
-__device__ __forceinline__ uint64_t deposit(uint64_t v, uint64_t mask) {
-    uint64_t out = 0;
-    while (mask) {
-        const uint64_t low = mask & (~mask + 1);
-        if (v & 1ull) out |= low;
-        v >>= 1;
-        mask &= mask - 1;
-    }
-    return out;
+// 8-byte asynchronous copy global -> shared, and its group fences
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// row swizzle of a column group (8 columns): XOR into the row's low 2 bits
+__device__ __forceinline__ int fswz(int col) { return (col >> 3) & 3; }
 
 __global__ void __launch_bounds__(kFThreads, 2)
     fused5_tc_kernel(float2 *__restrict__ psi, const __grid_constant__ FusedP p) {
-    __shared__ float sb_hi[kFCols * kFLd];
-    __shared__ float sb_lo[kFCols * kFLd];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    float2 *raw = reinterpret_cast<float2 *>(fsm);
+    float *sb_hi = reinterpret_cast<float *>(fsm + kFElems * sizeof(float2));
+    float *sb_lo = sb_hi + kFCols * kFLd;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int gid = lane >> 2, tig = lane & 3;
     const int mt = warp & 3;          // rows 16 mt .. 16 mt + 15
     const int nb = (warp >> 2) * 32;  // columns nb .. nb + 31
@@ -84,26 +91,50 @@ __global__ void __launch_bounds__(kFThreads, 2)
             alo[ks][e] = to_tf32(v[e] - __uint_as_float(ahi[ks][e]));
         }
     }
-
-    for (uint64_t chunk = blockIdx.x; chunk < p.total_chunks; chunk += gridDim.x) {
-        const uint64_t member = chunk >> p.chunk_shift;
-        const uint64_t cbase = (member << p.ms) | deposit(chunk & ((1ull << p.chunk_shift) - 1), p.hi_mask);
-        // ---- load: thread index bits follow the chunk's 11 address bits in
-        // ascending order (consecutive threads -> consecutive addresses)
+    // this thread's part of every element's address (the chunk's lowest 8 bits)
+    uint64_t dt = 0;
+    {
+        uint64_t m = p.chunk_mask;
+        for (int b = 0; b < 8; ++b) {
+            const uint64_t low = m & (~m + 1);
+            if ((tid >> b) & 1) dt |= low;
+            m &= m - 1;
+        }
+    }
+    const int rt = p.lmap[tid], ct = p.cmap[tid];
+    const uint64_t cmask = (1ull << p.chunk_shift) - 1ull;
+    auto chunk_base = [&](uint64_t chunk) {
+        return ((chunk >> p.chunk_shift) << p.ms) | expand_bits(chunk & cmask, p.cins);
+    };
+    auto fetch = [&](uint64_t chunk) {
+        const uint64_t cb = chunk_base(chunk) | dt;
 #pragma unroll
-        for (int it = 0; it < (kFCols * 32) / kFThreads; ++it) {
-            const uint32_t i = threadIdx.x + it * kFThreads;
-            const uint64_t addr = cbase | deposit(i, p.chunk_mask);
-            const int row = p.lmap[i];  // local row index
-            const int c = p.cmap[i];    // column in the chunk
-            const float2 x = psi[addr];
-            float hr = __uint_as_float(to_tf32(x.x)), hi = __uint_as_float(to_tf32(x.y));
-            sb_hi[c * kFLd + row] = hr;
-            sb_hi[c * kFLd + 32 + row] = hi;
-            sb_lo[c * kFLd + row] = __uint_as_float(to_tf32(x.x - hr));
-            sb_lo[c * kFLd + 32 + row] = __uint_as_float(to_tf32(x.y - hi));
+        for (int h = 0; h < 8; ++h) cp_async8(&raw[tid + kFThreads * h], &psi[cb | p.dhi[h]]);
+    };
+
+    uint64_t chunk = blockIdx.x;
+    if (chunk < p.total_chunks) fetch(chunk);
+    cp_async_commit();
+    for (; chunk < p.total_chunks; chunk += gridDim.x) {
+        const uint64_t cb = chunk_base(chunk) | dt;
+        cp_async_wait_all();
+        __syncthreads();
+        // ---- split the raw chunk into TF32 hi and lo planes
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const float2 x = raw[tid + kFThreads * h];
+            const int row = rt | p.rhi[h], c = ct | p.chi[h];
+            const int o = c * kFLd + (row ^ fswz(c));
+            const float hr = __uint_as_float(to_tf32(x.x)), hi = __uint_as_float(to_tf32(x.y));
+            sb_hi[o] = hr;
+            sb_hi[o + 32] = hi;
+            sb_lo[o] = __uint_as_float(to_tf32(x.x - hr));
+            sb_lo[o + 32] = __uint_as_float(to_tf32(x.y - hi));
         }
         __syncthreads();
+        // ---- the next chunk streams in while this one is multiplied
+        if (chunk + gridDim.x < p.total_chunks) fetch(chunk + gridDim.x);
+        cp_async_commit();
         // ---- 3xTF32 MMAs: D[16 x 32] per warp
         float acc[4][4];
 #pragma unroll
@@ -115,38 +146,38 @@ __global__ void __launch_bounds__(kFThreads, 2)
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
                 const int col = nb + 8 * nt + gid;
+                const int sw = fswz(col);
                 const int k0 = 8 * ks + tig;
-                const uint32_t bh0 = __float_as_uint(sb_hi[col * kFLd + k0]);
-                const uint32_t bh1 = __float_as_uint(sb_hi[col * kFLd + k0 + 4]);
-                const uint32_t bl0 = __float_as_uint(sb_lo[col * kFLd + k0]);
-                const uint32_t bl1 = __float_as_uint(sb_lo[col * kFLd + k0 + 4]);
+                const uint32_t bh0 = __float_as_uint(sb_hi[col * kFLd + (k0 ^ sw)]);
+                const uint32_t bh1 = __float_as_uint(sb_hi[col * kFLd + ((k0 + 4) ^ sw)]);
+                const uint32_t bl0 = __float_as_uint(sb_lo[col * kFLd + (k0 ^ sw)]);
+                const uint32_t bl1 = __float_as_uint(sb_lo[col * kFLd + ((k0 + 4) ^ sw)]);
                 mma_tf32(acc[nt], alo[ks], bh0, bh1);
                 mma_tf32(acc[nt], ahi[ks], bl0, bl1);
                 mma_tf32(acc[nt], ahi[ks], bh0, bh1);
             }
         }
         __syncthreads();
-        // ---- stage D in the hi plane (row-major by column), then store
+        // ---- stage D in the hi plane (same swizzle), then store
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
             const int col = nb + 8 * nt + 2 * tig;
             const int row = 16 * mt + gid;
-            sb_hi[col * kFLd + row] = acc[nt][0];
-            sb_hi[(col + 1) * kFLd + row] = acc[nt][1];
-            sb_hi[col * kFLd + row + 8] = acc[nt][2];
-            sb_hi[(col + 1) * kFLd + row + 8] = acc[nt][3];
+            const int sw = fswz(col);
+            sb_hi[col * kFLd + (row ^ sw)] = acc[nt][0];
+            sb_hi[(col + 1) * kFLd + (row ^ sw)] = acc[nt][1];
+            sb_hi[col * kFLd + ((row + 8) ^ sw)] = acc[nt][2];
+            sb_hi[(col + 1) * kFLd + ((row + 8) ^ sw)] = acc[nt][3];
         }
         __syncthreads();
 #pragma unroll
-        for (int it = 0; it < (kFCols * 32) / kFThreads; ++it) {
-            const uint32_t i = threadIdx.x + it * kFThreads;
-            const uint64_t addr = cbase | deposit(i, p.chunk_mask);
-            const int row = p.lmap[i];
-            const int c = p.cmap[i];
-            psi[addr] = make_float2(sb_hi[c * kFLd + row], sb_hi[c * kFLd + 32 + row]);
+        for (int h = 0; h < 8; ++h) {
+            const int row = rt | p.rhi[h], c = ct | p.chi[h];
+            const int o = c * kFLd + (row ^ fswz(c));
+            psi[cb | p.dhi[h]] = make_float2(sb_hi[o], sb_hi[o + 32]);
         }
-        __syncthreads();
     }
+    cp_async_wait_all();
 }
 
 qs_status k_fused5(qs_state *s, const std::vector<cd> &U, const int *bits) {
@@ -173,37 +204,62 @@ qs_status k_fused5(qs_state *s, const std::vector<cd> &U, const int *bits) {
             ++got;
         }
     p.chunk_mask = qmask | colmask;
-    uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
-    p.hi_mask = all & ~p.chunk_mask;
     p.chunk_shift = n - 11;
     p.ms = s->ms;
     p.total_chunks = (uint64_t)s->batch << p.chunk_shift;
-    // thread index i (11 bits, over the chunk bits in ascending order) -> (row, column)
+    // chunk bits in ascending order; element index i (11 bits) -> address
+    // offset, row and column
     int cb[11], nc = 0;
     for (int b = 0; b < 64 && nc < 11; ++b)
         if ((p.chunk_mask >> b) & 1ull) cb[nc++] = b;
-    for (int i = 0; i < 2048; ++i) {
-        int row = 0, col = 0, ci = 0;
+    p.cins.count = 11;
+    for (int t = 0; t < 11; ++t) p.cins.pos[t] = (int8_t)cb[t];
+    auto row_col = [&](int i, int *row, int *col) {
+        *row = 0;
+        *col = 0;
+        int ci = 0;
         for (int t = 0; t < 11; ++t) {
             const int bit = (i >> t) & 1;
-            const int g = cb[t];
             int jq = -1;
             for (int j = 0; j < 5; ++j)
-                if (bits[j] == g) jq = j;
+                if (bits[j] == cb[t]) jq = j;
             if (jq >= 0)
-                row |= bit << (4 - jq);
+                *row |= bit << (4 - jq);
             else
-                col |= bit << ci++;
+                *col |= bit << ci++;
         }
-        p.lmap[i] = (uint8_t)row;
-        p.cmap[i] = (uint8_t)col;
+    };
+    for (int t = 0; t < 256; ++t) {
+        int r, c;
+        row_col(t, &r, &c);
+        p.lmap[t] = (uint8_t)r;
+        p.cmap[t] = (uint8_t)c;
     }
-    int dev = s->device, sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t grid = std::min<uint64_t>(p.total_chunks, (uint64_t)sms * 4);
+    for (int h = 0; h < 8; ++h) {
+        int r, c;
+        row_col(h << 8, &r, &c);
+        p.rhi[h] = (uint8_t)r;
+        p.chi[h] = (uint8_t)c;
+        uint64_t d = 0;
+        for (int t = 8; t < 11; ++t)
+            if (((h << 8) >> t) & 1) d |= 1ull << cb[t];
+        p.dhi[h] = d;
+    }
+    static int configured[64] = {0};
+    static int blocks_per_sm[64] = {0};
+    const int dev = (s->device >= 0 && s->device < 64) ? s->device : 0;
+    if (!configured[dev]) {
+        QS_CUDA_TRY(cudaFuncSetAttribute(fused5_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem));
+        int bps = 0, sms = 0;
+        QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fused5_tc_kernel, kFThreads, kFSmem));
+        QS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        blocks_per_sm[dev] = std::max(1, bps) * sms;
+        configured[dev] = 1;
+    }
+    const uint64_t grid = std::min<uint64_t>(p.total_chunks, (uint64_t)blocks_per_sm[dev]);
     const double amps = (double)((uint64_t)s->batch << n);
     ProfScope _ps(s->stream, KC_FUSED_TC, 2.0 * amps * 8.0, amps * 256.0 * 3.0);
-    fused5_tc_kernel<<<(unsigned)grid, kFThreads, 0, s->stream>>>((float2 *)s->data, p);
+    fused5_tc_kernel<<<(unsigned)grid, kFThreads, kFSmem, s->stream>>>((float2 *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }
