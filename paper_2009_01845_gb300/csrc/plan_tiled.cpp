@@ -308,7 +308,7 @@ template <typename R> static void set_transpose(const TileStage &a, TileStage &b
 template <typename R>
 static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const std::vector<GClass> &cls,
                               const std::vector<int> &slot, uint32_t pm_stride, const PassPlan &pp,
-                              int force_bit, double *gpart, bool *fits) {
+                              int force_bit, double *gpart, bool *fits, int *dry_stages = nullptr) {
     const int n = s->n;
     const int RB = TileCfg<R>::RB;
     const int k = RB + kTileLaneBits + TileCfg<R>::WB;
@@ -929,6 +929,10 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     }
     P.n_stages = nst;
     P.n_grad = ngrad;
+    if (dry_stages) {  // planning only: report the stage count
+        *dry_stages = nst;
+        return QS_OK;
+    }
     // per-transpose swizzles and register offsets; which stages test thread bits
     uint64_t rng = 0x9e3779b97f4a7c15ull;
     for (int t = 1; t < nst; ++t) set_transpose<R>(P.st[t - 1], P.st[t], k, &rng);
@@ -1040,6 +1044,49 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         return k_tiled_pass_c128(s, P);
 }
 
+// Orders of a pass's gates that keep every dependency: the queue order, then
+// the gates split into maximal runs of mutually commuting gates (disjoint
+// qubits, or both diagonal; gradient ops end a run) with alternate runs
+// reversed, once with the last run reversed and once with the second. Which
+// bits a pass's first and last stages hold, and how consecutive runs share
+// register bits, depends on these orders.
+static std::vector<std::vector<int>> run_orders(const std::vector<LGate> &G, const std::vector<GClass> &cls,
+                                                const std::vector<int> &gates) {
+    auto diag = [&](int i) { return cls[i] == G_PHASE || cls[i] == G_DIAG1 || cls[i] == G_ISING; };
+    // the Ising phase acts on every bit (its gate lists none)
+    auto bits = [&](int i) { return cls[i] == G_ISING ? ~0ull : qubit_bits(G[i]); };
+    std::vector<std::vector<int>> runs;
+    for (int gi : gates) {
+        bool joins = !runs.empty() && cls[gi] != G_GRAD;
+        if (joins)
+            for (int h : runs.back()) {
+                const bool commute = cls[h] != G_GRAD && ((bits(gi) & bits(h)) == 0 || (diag(gi) && diag(h)));
+                if (!commute) {
+                    joins = false;
+                    break;
+                }
+            }
+        if (joins)
+            runs.back().push_back(gi);
+        else
+            runs.push_back({gi});
+    }
+    std::vector<std::vector<int>> out = {gates};
+    const int nr = (int)runs.size();
+    for (int variant = 0; variant < 2; ++variant) {
+        std::vector<int> o;
+        for (int r = 0; r < nr; ++r) {
+            const bool rev = variant == 0 ? ((nr - 1 - r) % 2 == 0) : (r % 2 == 1);
+            if (rev)
+                o.insert(o.end(), runs[r].rbegin(), runs[r].rend());
+            else
+                o.insert(o.end(), runs[r].begin(), runs[r].end());
+        }
+        if (o != gates) out.push_back(o);
+    }
+    return out;
+}
+
 qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *params, int n_params, int force_bit,
                     double *gpart, double param_sign) {
     const int n = s->n;
@@ -1115,6 +1162,27 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
         }
         // complete the tile with unused high bits
         for (int b = kTileLaneBits; b < n && __builtin_popcountll(pp.high) < nh; ++b) pp.high |= 1ull << b;
+        // order: the fewest stages among the queue order and two orders that
+        // reverse alternate runs of mutually commuting gates
+        if (pp.gates.size() > 1) {
+            std::vector<std::vector<int>> cand = run_orders(G, cls, pp.gates);
+            int best = -1, best_stages = std::numeric_limits<int>::max();
+            for (size_t c = 0; c < cand.size(); ++c) {
+                PassPlan q = pp;
+                q.gates = cand[c];
+                bool fits = true;
+                int stages = 0;
+                if (s->dtype == QS_C64)
+                    QS_TRY(emit_and_run<float>(s, G, cls, slot, pm_stride, q, force_bit, gpart, &fits, &stages));
+                else
+                    QS_TRY(emit_and_run<double>(s, G, cls, slot, pm_stride, q, force_bit, gpart, &fits, &stages));
+                if (fits && stages < best_stages) {
+                    best_stages = stages;
+                    best = (int)c;
+                }
+            }
+            if (best > 0) pp.gates = cand[best];
+        }
         // emit; a pass over the descriptor's capacity is retried with a prefix of
         // its gates (a prefix keeps every dependency)
         while (true) {

@@ -36,13 +36,15 @@ def emu(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("emu") / "libtile_emu.so")
     cmd = [cxx, "-std=c++17", "-O2", "-fPIC", "-shared", "-I", inc, "-I", os.path.join(ROOT, "include"),
            "-I", CSRC, os.path.join(CSRC, "plan_tiled.cpp"), os.path.join(CSRC, "gates_host.cpp"),
-           os.path.join(ROOT, "tests", "tile_emulator.cpp"), "-o", out]
+           os.path.join(ROOT, "tests", "tile_emulator.cpp"), "-Wl,-Bsymbolic", "-o", out]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
     lib = ctypes.CDLL(out)
     lib.emu_apply.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     lib.emu_sweep.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                               ctypes.c_void_p]
+    lib.emu_trotter.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
     lib.emu_last_error.restype = ctypes.c_char_p
     return lib
 
@@ -140,3 +142,32 @@ def test_adjoint_sweep_gradients(emu, dtype, n):
     want = oracle.gradient_exact(n, gates, terms)
     scale = sum(abs(t[0]) for t in terms)
     assert np.max(np.abs(got - want)) < (1e-9 if dtype == 1 else 1e-4) * scale
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_tiled_trotter_steps(emu, dtype):
+    """The tiled Trotter queue (Ising phases merged across steps, RX layers)
+    against the oracle's step-by-step second-order splitting (Sec. 2.6)."""
+    n, T, dt, steps = 13, 1.0, 0.05, 6
+    h0 = qi.transverse_field_terms(n)
+    h1 = qi.random_ising_terms(n, qi.rng(11))
+    a0 = np.zeros(n)
+    for c, xm, zm in h0:
+        a0[xm.bit_length() - 1] += c
+    a1 = np.zeros(n)
+    table = np.zeros(n * n + n + 1)
+    for c, xm, zm in h1:
+        bits = [n - 1 - q for q in range(n) if (zm >> q) & 1]
+        if len(bits) == 1:
+            table[n * n + bits[0]] += c
+        elif len(bits) == 2:
+            table[bits[0] * n + bits[1]] += c
+            table[bits[1] * n + bits[0]] += c
+        else:
+            table[n * n + n] += c
+    psi = oracle.plus_state(n)
+    want = oracle.adiabatic_evolve(psi.copy(), n, h0, h1, T, dt, steps)
+    got = psi.copy()
+    st = emu.emu_trotter(n, dtype, a0.ctypes.data, a1.ctypes.data, table.ctypes.data, T, dt, steps, got.ctypes.data)
+    assert st == 0, emu.emu_last_error().decode()
+    assert np.max(np.abs(got - want)) < TOL[dtype]

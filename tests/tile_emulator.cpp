@@ -292,6 +292,25 @@ template <typename R> static qs_status emulate_pass(qs_state *s, const TileParam
                         (*g_gpart)[(size_t)p.gslot[op.gl] * p.total_tiles + t] += acc;
                         break;
                     }
+                    case TOP_ISING: {
+                        // psi_x *= exp(-i tau E(x)), E from the member's table (host memory here)
+                        double tau;
+                        std::memcpy(&tau, &op.tmask, sizeof(double));
+                        const int nq = p.nq;
+                        const double *J = p.ising + (t >> p.n_free) * p.ising_stride;
+                        const double *hv = J + (size_t)nq * nq;
+                        for (int r = 0; r < NR; ++r) {
+                            const uint64_t x = gidx(local_of(th, r));
+                            double e = hv[nq];
+                            for (int b = 0; b < nq; ++b) {
+                                const double zb = ((x >> b) & 1ull) ? -1.0 : 1.0;
+                                e += hv[b] * zb;
+                                for (int c = b + 1; c < nq; ++c) e += J[b * nq + c] * zb * (((x >> c) & 1ull) ? -1.0 : 1.0);
+                            }
+                            *a[r] *= std::polar(1.0, -tau * e);
+                        }
+                        break;
+                    }
                     default:
                         set_error("op type %d is not emulated", (int)op.type);
                         return QS_ERR_UNSUPPORTED;
@@ -388,6 +407,57 @@ int emu_sweep(int n, int dtype, const qs_gate *gates, int count, double *buf, do
         grad[slot_gate[sl]] += coef[sl] * sum;
     }
     return 0;
+}
+
+// Adiabatic evolution as the library's tiled Trotter path plans it: per step
+// k (s_k = (k + 1/2) dt / T) an Ising phase with the merged half steps, then
+// RX(2 dt a_q(s_k)) on every qubit, a_q(s) = (1 - s) a0[q] + s a1[q]; the
+// Ising table (index bits: J[a n + b], h[n], constant) is shared by the state.
+int emu_trotter(int n, int dtype, const double *a0, const double *a1, const double *table, double T, double dt,
+                int steps, double *psi) {
+    std::vector<double> svals, taus;
+    for (int k = 0; k < steps; ++k) svals.push_back((k + 0.5) * dt / T);
+    taus.push_back(0.5 * dt * svals[0]);
+    for (int k = 0; k + 1 < steps; ++k) taus.push_back(0.5 * dt * (svals[k] + svals[k + 1]));
+    taus.push_back(0.5 * dt * svals[steps - 1]);
+    std::vector<LGate> G;
+    auto ising = [&](double tau) {
+        LGate g;
+        g.kind = kKindIsing;
+        g.k = 0;
+        g.diagonal = true;
+        g.m.assign(1, cdd(tau, 0.0));
+        G.push_back(g);
+    };
+    for (int k = 0; k < steps; ++k) {
+        ising(taus[k]);
+        for (int q = 0; q < n; ++q) {
+            const double a = (1.0 - svals[k]) * a0[q] + svals[k] * a1[q];
+            if (a == 0.0) continue;
+            qs_gate g;
+            std::memset(&g, 0, sizeof(g));
+            g.kind = QS_GATE_RX;
+            g.n_targets = 1;
+            g.targets[0] = q;
+            g.param_index = -1;
+            g.params[0] = 2.0 * dt * a;
+            LGate lg;
+            if (lower_gate(n, g, &lg) != QS_OK) return -1;
+            G.push_back(lg);
+        }
+    }
+    ising(taus[steps]);
+    qs_state s;
+    s.n = n;
+    s.ms = n;
+    s.batch = 1;
+    s.dtype = (qs_dtype)dtype;
+    s.data = psi;
+    s.itab = const_cast<double *>(table);
+    s.ising_stride = 0;
+    const qs_status st = run_tiled(&s, G, nullptr, 0);
+    s.itab = nullptr;
+    return (int)st;
 }
 
 const char *emu_last_error(void) { return last_error(); }
