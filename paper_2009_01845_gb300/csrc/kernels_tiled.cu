@@ -454,6 +454,38 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
     }
 }
 
+// per-member rotation on register bit J: RY [[c, -s], [s, c]] (real, packed
+// FMAs) or RX [[c, -i s], [-i s, c]], for the registers whose bits of mr are 1
+template <typename R, int RB, int J>
+__device__ __forceinline__ void prot_reg(V<R> *a, R c, R s, bool rx, uint32_t mr) {
+#pragma unroll
+    for (int r = 0; r < (1 << RB); ++r) {
+        if (r & (1 << J)) continue;
+        if ((r & mr) != mr) continue;
+        const V<R> x = a[r], y = a[r | (1 << J)];
+        if (!rx) {
+            a[r] = fma_c2(c, x, fma_c2(-s, y, mkc<R>(0, 0)));
+            a[r | (1 << J)] = fma_c2(c, y, fma_c2(s, x, mkc<R>(0, 0)));
+        } else {
+            a[r] = mkc<R>(c * x.x + s * y.y, c * x.y - s * y.x);
+            a[r | (1 << J)] = mkc<R>(c * y.x + s * x.y, c * y.y - s * x.x);
+        }
+    }
+}
+
+template <typename R, int RB>
+__device__ __forceinline__ void dispatch_prot(V<R> *a, int j, R c, R s, bool rx, uint32_t mr) {
+    switch (j) {
+    case 0: prot_reg<R, RB, 0>(a, c, s, rx, mr); break;
+    case 1: prot_reg<R, RB, 1>(a, c, s, rx, mr); break;
+    case 2: prot_reg<R, RB, 2>(a, c, s, rx, mr); break;
+    case 3: prot_reg<R, RB, 3>(a, c, s, rx, mr); break;
+    default:
+        if constexpr (RB > 4) prot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, c, s, rx, mr);
+        break;
+    }
+}
+
 // negate the registers whose bits A and B (and the bits of mr) are 1
 template <typename R, int RB, int A, int B>
 __device__ __forceinline__ void flip_reg(V<R> *a, uint32_t mr) {
@@ -708,6 +740,14 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     break;
                 case TOP_FLIP:
                     if (req_ok()) dispatch_flip<R, RB>(a, op.a, op.b, op.mr);
+                    break;
+                case TOP_PROT:
+                    if (req_ok()) {
+                        const V<R> *M = mat_of();
+                        // table: RY m[2] = (s, 0); RX m[2] = (0, -s)
+                        const R c = M[0].x, sn = op.b ? -M[2].y : M[2].x;
+                        dispatch_prot<R, RB>(a, op.a, c, sn, op.b != 0, op.mr);
+                    }
                     break;
                 case TOP_GRAD: {
                     if constexpr (!FULL) break;

@@ -839,6 +839,16 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             }
             case G_DENSE1: {
                 const int lb = loc_of[g.tbit[0]];
+                if (sl >= 0 && ((cur >> lb) & 1u) && (g.kind == QS_GATE_RY || g.kind == QS_GATE_RX)) {
+                    // per-member rotation: cos and sin from the member's table
+                    op.type = TOP_PROT;
+                    op.a = (uint8_t)regidx(lb);
+                    op.b = g.kind == QS_GATE_RX ? 1 : 0;
+                    split(g.cmask, &op.mr, &op.mt, &op.mo);
+                    op.pm = 1;
+                    op.m = 4 * sl;
+                    break;
+                }
                 if (!((cur >> lb) & 1u)) {
                     op.type = TOP_DENSE1_L;
                     op.a = (uint8_t)lane_index(lb);

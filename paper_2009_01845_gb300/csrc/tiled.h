@@ -66,6 +66,7 @@ enum TileOpType : uint8_t {
     TOP_ROTS_L,      // the same on the 5 lane bits (warp shuffles)
     TOP_DBLOCK,      // product of diagonal factors (see diag_block)
     TOP_FLIP,        // negate where register bits a and b (and the required bits) are 1
+    TOP_PROT,        // per-member RY (b = 0) or RX (b = 1) on register bit a: (cos, sin) from the member's table
 };
 
 // Scaled real rotations: form 0: (a, b) <- (a - t b, b + t a) with |t| <= 1;
