@@ -56,7 +56,7 @@ typedef int32_t qs_status;
 #define QS_ERR_ARG 1          /* invalid argument: qubit range, arity, null pointer, size */
 #define QS_ERR_OOM 2          /* device allocation failed */
 #define QS_ERR_CUDA 3         /* a CUDA runtime call or kernel launch failed */
-#define QS_ERR_UNSUPPORTED 4  /* valid request outside what this build implements */
+#define QS_ERR_UNSUPPORTED 4  /* valid request outside what the library implements */
 #define QS_ERR_TIMEOUT 5      /* a bounded device-side wait ran out */
 
 typedef int32_t qs_dtype;
