@@ -429,6 +429,41 @@ def unfused_passes(n: int = 32, reps: int = 5) -> dict:
     return out
 
 
+def qft_n18(reps: int = 20) -> dict:
+    """QFT on n = 18 qubits in complex128 (4 MiB: the state stays in L2), input
+    a seeded basis state: per-call time of the 180-gate circuit one gate per
+    pass (the plain method), in tiled passes, and replayed from a CUDA-graph
+    plan of the unfused passes (no host launch overhead); max error against the
+    closed form 2^{-n/2} exp(2 pi i x k / 2^n)."""
+    import numpy as np
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    n = 18
+    x = qi.qft_input(n, seed=1)
+    gates = qi.qft_circuit(n)
+    st = qsim.State(n, dtype="c128")
+    out = {"workload": f"QFT n={n} complex128, |x> with x = {x} (seed 1), {len(gates)} gates"}
+    for mode in ("unfused", "tiled"):
+        t = _time_cuda(lambda: st.init_basis(x).apply(gates, mode=mode), reps, warmup=2)
+        out[mode] = {"ms_per_circuit": t, "gate_apps_per_s": len(gates) / (t / 1000.0)}
+    k = np.arange(1 << n)
+    want = np.exp(2j * np.pi * x * k / (1 << n)) / np.sqrt(1 << n)
+    for mode in ("unfused", "tiled"):
+        plan = qsim.Plan(st, gates, mode=mode, autotune=False)
+        t = _time_cuda(lambda: (st.init_basis(x), plan.execute()), reps, warmup=2)
+        st.init_basis(x)
+        plan.execute()
+        out[mode + "_graph"] = {"ms_per_circuit": t, "gate_apps_per_s": len(gates) / (t / 1000.0),
+                                "graph_nodes": plan.info()["graph_nodes"],
+                                "max_abs_error_vs_closed_form": float(np.max(np.abs(st.get() - want)))}
+        plan.close()
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
 def random_layer_c128(n: int = 33, layers: int = 2) -> dict:
     """The random-layer circuit's first `layers` layers at n = 33 in complex128
     (128 GiB state): tiled passes against the plain unfused simulator on the
@@ -582,6 +617,7 @@ def run_ours(a):
         secondary["adiabatic_batch"] = adiabatic_batch()
         secondary["fused_tc"] = fused_tc()
         secondary["unfused_passes"] = unfused_passes()
+        secondary["qft_n18_c128"] = qft_n18()
         secondary["random_layer_c128_n33"] = random_layer_c128()
 
     if rank == 0:
