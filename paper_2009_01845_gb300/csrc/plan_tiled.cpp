@@ -1133,30 +1133,49 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
     while (true) {
         while (first < G.size() && done[first]) ++first;
         if (first >= G.size()) break;
-        PassPlan pp;
-        pp.high = force;
-        uint64_t blocked = 0;
+        // gates from `first` on that can join a pass: a gate joins if it commutes
+        // past the gates skipped so far and its dense targets fit the tile's high
+        // bits, which are either taken greedily as gates need them or fixed
         const uint64_t all_bits = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
-        for (size_t i = first; i < G.size(); ++i) {
-            if (done[i]) continue;
-            if (blocked == all_bits) break;  // nothing later can join this pass
-            const uint64_t qb = cls[i] == G_ISING ? all_bits : qubit_bits(G[i]);
-            if (qb & blocked) {
-                blocked |= qb;
-                continue;
+        auto select = [&](bool fixed, uint64_t fixed_high, PassPlan *out) {
+            out->high = force | fixed_high;
+            out->gates.clear();
+            uint64_t blocked = 0;
+            for (size_t i = first; i < G.size(); ++i) {
+                if (done[i]) continue;
+                if (blocked == all_bits) break;  // nothing later can join this pass
+                const uint64_t qb = cls[i] == G_ISING ? all_bits : qubit_bits(G[i]);
+                if (qb & blocked) {
+                    blocked |= qb;
+                    continue;
+                }
+                if (cls[i] == G_SINGLE) {
+                    blocked |= qb;
+                    continue;
+                }
+                const uint64_t nb = need_bits(G[i], cls[i]);
+                if (fixed ? (nb & ~out->high) != 0 : __builtin_popcountll(out->high | nb) > nh) {
+                    blocked |= qb;
+                    continue;
+                }
+                out->high |= nb;
+                out->gates.push_back((int)i);
+                if ((int)out->gates.size() >= kTileMaxOps) break;
             }
-            if (cls[i] == G_SINGLE) {
-                blocked |= qb;
-                continue;
+        };
+        PassPlan pp;
+        select(false, 0, &pp);
+        // high bits fixed to a window of consecutive index bits: circuits with
+        // nearest-neighbour structure keep a whole light cone inside one window;
+        // the window (or the greedy choice) that takes the most gates wins
+        {
+            const int w = nh - __builtin_popcountll(force);
+            const int top = force_bit >= 0 ? force_bit : n;
+            for (int b = kTileLaneBits; w > 0 && b + w <= top; ++b) {
+                PassPlan q;
+                select(true, ((1ull << w) - 1ull) << b, &q);
+                if (q.gates.size() > pp.gates.size()) pp = std::move(q);
             }
-            const uint64_t nb = need_bits(G[i], cls[i]);
-            if (__builtin_popcountll(pp.high | nb) > nh) {
-                blocked |= qb;
-                continue;
-            }
-            pp.high |= nb;
-            pp.gates.push_back((int)i);
-            if ((int)pp.gates.size() >= kTileMaxOps) break;
         }
         if (pp.gates.empty()) {
             // the front gate cannot run in a tile
