@@ -319,38 +319,17 @@ __device__ __forceinline__ double2 fma_c2(double c, double2 v, double2 acc) {
     return make_double2(fma(c, v.x, acc.x), fma(c, v.y, acc.y));
 }
 
-// scaled real rotation on register bit J (see TileRotForm)
+// real rotation on register bit J as in-place shears (TOP_ROTS_R): x += s1 y,
+// then y += s2 x over the register pairs (x, y) that differ in bit J. Each
+// update reads the pair and overwrites one of its members, so no register is
+// copied.
 template <typename R, int RB, int J>
-__device__ __forceinline__ void rot_reg(V<R> *a, R c, int form) {
-    if (form == ROT_TAN) {
+__device__ __forceinline__ void rot_reg(V<R> *a, R s1, R s2) {
 #pragma unroll
-        for (int r = 0; r < (1 << RB); ++r) {
-            if (r & (1 << J)) continue;
-            const V<R> x = a[r], y = a[r | (1 << J)];
-            a[r] = fma_c2(-c, y, x);
-            a[r | (1 << J)] = fma_c2(c, x, y);
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < (1 << RB); ++r) {
-            if (r & (1 << J)) continue;
-            const V<R> x = a[r], y = a[r | (1 << J)];
-            a[r] = fma_c2(-c, x, y);
-            a[r | (1 << J)] = fma_c2(c, y, x);
-        }
-    }
-}
-
-template <typename R, int RB>
-__device__ __forceinline__ void dispatch_rot(V<R> *a, int j, R c, int form) {
-    switch (j) {
-    case 0: rot_reg<R, RB, 0>(a, c, form); break;
-    case 1: rot_reg<R, RB, 1>(a, c, form); break;
-    case 2: rot_reg<R, RB, 2>(a, c, form); break;
-    case 3: rot_reg<R, RB, 3>(a, c, form); break;
-    default:
-        if constexpr (RB > 4) rot_reg<R, RB, 4>(a, c, form);
-        break;
+    for (int r = 0; r < (1 << RB); ++r) {
+        if (r & (1 << J)) continue;
+        a[r] = fma_c2(s1, a[r | (1 << J)], a[r]);
+        a[r | (1 << J)] = fma_c2(s2, a[r], a[r | (1 << J)]);
     }
 }
 
@@ -486,23 +465,38 @@ __device__ __forceinline__ void dispatch_prot(V<R> *a, int j, R c, R s, bool rx,
     }
 }
 
-// negate the registers whose bits A and B (and the bits of mr) are 1
+// negate the registers whose bit A is 1 - PA and bit B is 1 - PB (PA, PB: the
+// register frame on A and B)
+template <typename R, int RB, int A, int B, int PA, int PB>
+__device__ __forceinline__ void flip_pat(V<R> *a) {
+#pragma unroll
+    for (int r = 0; r < (1 << RB); ++r)
+        if (((r >> A) & 1) != PA && ((r >> B) & 1) != PB) a[r] = mkc<R>(-a[r].x, -a[r].y);
+}
+
 template <typename R, int RB, int A, int B>
-__device__ __forceinline__ void flip_reg(V<R> *a, uint32_t mr) {
-    if (mr == 0) {
-#pragma unroll
-        for (int r = 0; r < (1 << RB); ++r)
-            if ((r & (1 << A)) && (r & (1 << B))) a[r] = mkc<R>(-a[r].x, -a[r].y);
-    } else {
-#pragma unroll
-        for (int r = 0; r < (1 << RB); ++r)
-            if ((r & (1 << A)) && (r & (1 << B)) && (r & mr) == mr) a[r] = mkc<R>(-a[r].x, -a[r].y);
+__device__ __forceinline__ void flip_reg(V<R> *a, uint32_t pat) {
+    switch (pat) {
+    case 0: flip_pat<R, RB, A, B, 0, 0>(a); break;
+    case 1: flip_pat<R, RB, A, B, 1, 0>(a); break;
+    case 2: flip_pat<R, RB, A, B, 0, 1>(a); break;
+    default: flip_pat<R, RB, A, B, 1, 1>(a); break;
     }
 }
 
+// TOP_FLIP: with further required register bits mr (a sign on three or more
+// register bits, rare) every register is tested
 template <typename R, int RB>
-__device__ __forceinline__ void dispatch_flip(V<R> *a, int A, int B, uint32_t mr) {
-    QS_PAIR_CASES(flip_reg, a, mr)
+__device__ __forceinline__ void dispatch_flip(V<R> *a, int A, int B, uint32_t mr, uint32_t pat, uint32_t fx) {
+    if (mr == 0) {
+        QS_PAIR_CASES(flip_reg, a, pat)
+        return;
+    }
+    const uint32_t m = mr | (1u << A) | (1u << B);
+    const uint32_t x = fx | ((pat & 1u) << A) | (((pat >> 1) & 1u) << B);
+#pragma unroll
+    for (int r = 0; r < (1 << RB); ++r)
+        if ((((uint32_t)r ^ x) & m) == m) a[r] = mkc<R>(-a[r].x, -a[r].y);
 }
 
 // Shared-memory position of tile-local index x under a transpose's swizzle
@@ -577,7 +571,10 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
         const uint32_t lt = thread_local_index<WB>(st, lane, warp);
         ltab[s * (NW * 32) + threadIdx.x] = (uint16_t)lt;
         if (s == 0) continue;
-        const uint32_t w = swizzle_pos<R>(thread_local_index<WB>(p.st[s - 1], lane, warp), st.fcol, p.k) * sizeof(V<R>);
+        uint32_t w = swizzle_pos<R>(thread_local_index<WB>(p.st[s - 1], lane, warp), st.fcol, p.k) * sizeof(V<R>);
+        // the previous stage's register frame: register r is written where r ^ rflip belongs
+        for (int j = 0; j < RB; ++j)
+            if ((p.st[s - 1].rflip >> j) & 1u) w ^= st.rw[j];
         const uint32_t r = swizzle_pos<R>(lt, st.fcol, p.k) * sizeof(V<R>);
         tab[s * (NW * 32) + threadIdx.x] = w | (r << 16);
     }
@@ -689,30 +686,20 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                         ising_phase<R, RB>(a, p, op, st, tbase, t >> p.n_free, lane, warp, s_g, &s_eo, s_qp);
                     break;
                 case TOP_ROTS_R: {
-                    // rotations on distinct register bits (they commute); op.a / op.b
-                    // mark the bits in tan / cot form, mat[m + j].x holds t or u
+                    // rotations on distinct register bits (they commute): bit j of
+                    // op.a marks an active one
                     const V<R> *M = &p.mat[op.m];
-                    const uint32_t tm = op.a, cm = op.b;
+                    const uint32_t am = op.a;
 #pragma unroll
                     for (int j = 0; j < RB; ++j) {
-                        if ((tm >> j) & 1u) {
-                            switch (j) {
-                            case 0: rot_reg<R, RB, 0>(a, M[0].x, ROT_TAN); break;
-                            case 1: rot_reg<R, RB, 1>(a, M[1].x, ROT_TAN); break;
-                            case 2: rot_reg<R, RB, 2>(a, M[2].x, ROT_TAN); break;
-                            case 3: rot_reg<R, RB, 3>(a, M[3].x, ROT_TAN); break;
-                            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, M[4].x, ROT_TAN); break;
-                            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, M[5].x, ROT_TAN);
-                            }
-                        } else if ((cm >> j) & 1u) {
-                            switch (j) {
-                            case 0: rot_reg<R, RB, 0>(a, M[0].x, ROT_COT); break;
-                            case 1: rot_reg<R, RB, 1>(a, M[1].x, ROT_COT); break;
-                            case 2: rot_reg<R, RB, 2>(a, M[2].x, ROT_COT); break;
-                            case 3: rot_reg<R, RB, 3>(a, M[3].x, ROT_COT); break;
-                            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, M[4].x, ROT_COT); break;
-                            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, M[5].x, ROT_COT);
-                            }
+                        if (!((am >> j) & 1u)) continue;
+                        switch (j) {
+                        case 0: rot_reg<R, RB, 0>(a, M[0].x, M[0].y); break;
+                        case 1: rot_reg<R, RB, 1>(a, M[1].x, M[1].y); break;
+                        case 2: rot_reg<R, RB, 2>(a, M[2].x, M[2].y); break;
+                        case 3: rot_reg<R, RB, 3>(a, M[3].x, M[3].y); break;
+                        case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, M[4].x, M[4].y); break;
+                        default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, M[5].x, M[5].y);
                         }
                     }
                     break;
@@ -739,7 +726,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     diag_block<R, RB>(a, p, op, tbase, lt);
                     break;
                 case TOP_FLIP:
-                    if (req_ok()) dispatch_flip<R, RB>(a, op.a, op.b, op.mr);
+                    if (req_ok()) dispatch_flip<R, RB>(a, op.a, op.b, op.mr, op.tkind, op.fx);
                     break;
                 case TOP_PROT:
                     if (req_ok()) {
@@ -808,9 +795,12 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                 if ((warp >> w) & 1) gt |= 1ull << p.gbit[sl.wloc[w]];
             uint64_t gr[RB];
 #pragma unroll
-            for (int j = 0; j < RB; ++j) gr[j] = 1ull << p.gbit[sl.rloc[j]];
+            for (int j = 0; j < RB; ++j) {
+                gr[j] = 1ull << p.gbit[sl.rloc[j]];
+                if ((sl.rflip >> j) & 1u) gt |= gr[j];  // register frame: r holds r ^ rflip
+            }
 #pragma unroll
-            for (int r = 0; r < NR; ++r) psi[gt | reg_offset<RB>(r, gr)] = a[r];
+            for (int r = 0; r < NR; ++r) psi[gt ^ reg_offset<RB>(r, gr)] = a[r];
         }
         // ---------------- gradient partials of this tile (fixed summation order)
         if (FULL && p.n_grad > 0) {

@@ -17,6 +17,8 @@
 #include <cstring>
 #include <limits>
 #include <memory>
+#include <unordered_map>
+#include <utility>
 
 #include "plan.h"
 #include "prof.h"
@@ -97,43 +99,80 @@ struct Factor {
     int bit;         // DF_BIT: index bit
     uint64_t mask;   // DF_PHASE: required index bits
     cd v0, v1;       // DF_BIT: diag(v0, v1); DF_PHASE: v0
+    int rot = -1;    // the D_L of rotation gate `rot`: also times that rotation's diagonal
 };
 
 struct Entry {
     EKind kind;
-    int gi = -1;              // E_GATE: gate index
+    int gi = -1;              // E_GATE / E_ROT: gate index
     int bit = -1;             // E_ROT: index bit
-    int form = 0;             // E_ROT: ROT_TAN / ROT_COT
-    double coef = 0.0;        // E_ROT: t or u
+    double cg = 0.0, sg = 0.0;  // E_ROT: cos h, sin h of R = [[cos h, -sin h], [sin h, cos h]]
     std::vector<Factor> fac;  // E_BLOCK
 };
 
 // U = D_L R D_R with R = [[cos h, -sin h], [sin h, cos h]], 0 <= h <= pi/2,
-// D_R = diag(1, e^{i b1}), D_L = diag(e^{i a0}, e^{i a1}). Then
-//   h <= pi/4: R = cos h * K_tan(t = tan h),  K_tan (a, b) = (a - t b, b + t a);
-//   h >  pi/4: R = sin h * diag(-1, 1) * K_cot(u = cot h), K_cot (a, b) = (b - u a, a + u b);
-// and the scalars and signs join D_L. Returns false if U is diagonal.
-bool split_1q(const std::vector<cd> &m, cd *dr, cd *dl, int *form, double *coef) {
-    const double cg = std::abs(m[0]), sg = std::abs(m[2]);
-    if (sg == 0.0) return false;
-    const double a0 = cg > 0.0 ? std::arg(m[0]) : 0.0;
+// D_R = diag(1, e^{i b1}), D_L = diag(e^{i a0}, e^{i a1}). How R is applied
+// (see rot_plan) adds a real diagonal to D_L when the stage is emitted.
+// Returns false if U is diagonal.
+bool split_1q(const std::vector<cd> &m, cd *dr, cd *dl, double *cg, double *sg) {
+    *cg = std::abs(m[0]);
+    *sg = std::abs(m[2]);
+    if (*sg == 0.0) return false;
+    const double a0 = *cg > 0.0 ? std::arg(m[0]) : 0.0;
     const double a1 = std::arg(m[2]);
     const double b1 = std::arg(-m[1]) - a0;
     dr[0] = 1.0;
     dr[1] = std::polar(1.0, b1);
-    const cd l0 = std::polar(1.0, a0), l1 = std::polar(1.0, a1);
-    if (cg >= sg) {
-        *form = ROT_TAN;
-        *coef = sg / cg;
-        dl[0] = cg * l0;
-        dl[1] = cg * l1;
-    } else {
-        *form = ROT_COT;
-        *coef = cg / sg;
-        dl[0] = -sg * l0;
-        dl[1] = sg * l1;
-    }
+    dl[0] = std::polar(1.0, a0);
+    dl[1] = std::polar(1.0, a1);
     return true;
+}
+
+// How the rotation R (cos h = cg, sin h = sg) runs on a register bit whose
+// halves are (frame = 0) or are not (frame = 1) in natural order: physical
+// shears x += s1 y, y += s2 x (and x += s1 y again if `three`), with x the
+// register half where the bit is 0, then R = dd * [swap] * (those shears) in
+// the bit's own terms, the swap (`swap`: the frame flips) left to the frame.
+//   h <= pi/4, t = tan h:  R = diag(cos h, sec h) Sy(sin h cos h) Sx(-t)
+//                            = diag(sec h, cos h) Sx(-sin h cos h) Sy(t);
+//   h >  pi/4, psi = pi/2 - h, u = tan psi, with the frame:
+//                          R = diag(-sec psi, cos psi) X Sy(-sin psi cos psi) Sx(u)
+//                            = diag(-cos psi, sec psi) X Sx(sin psi cos psi) Sy(-u);
+//   h >  pi/4 without it:  R = Sx(-tan h/2) Sy(sin h) Sx(-tan h/2)
+//                            = Sy(tan h/2) Sx(-sin h) Sy(tan h/2),
+// where Sx(c): x += c y, Sy(c): y += c x, X swaps x and y; the first form of
+// each pair starts with x (frame 0), the second with y (frame 1, where the
+// physical x holds the bit's 1 half). Every coefficient and diagonal entry is
+// at most sqrt(2) in magnitude.
+struct RotPlan {
+    double s1, s2;
+    bool three, swap;
+    cd dd0, dd1;
+};
+RotPlan rot_plan(double cg, double sg, int frame, bool allow_swap) {
+    RotPlan q{};
+    const double sc = sg * cg;
+    if (cg >= sg) {
+        const double t = sg / cg;
+        q.s1 = frame ? t : -t;
+        q.s2 = frame ? -sc : sc;
+        q.dd0 = frame ? 1.0 / cg : cg;
+        q.dd1 = frame ? cg : 1.0 / cg;
+    } else if (allow_swap) {
+        const double u = cg / sg;
+        q.swap = true;
+        q.s1 = frame ? -u : u;
+        q.s2 = frame ? sc : -sc;
+        q.dd0 = frame ? -sg : -1.0 / sg;
+        q.dd1 = frame ? 1.0 / sg : sg;
+    } else {
+        const double th = sg / (1.0 + cg);  // tan(h/2)
+        q.three = true;
+        q.s1 = frame ? th : -th;
+        q.s2 = frame ? -sg : sg;
+        q.dd0 = q.dd1 = 1.0;
+    }
+    return q;
 }
 
 uint64_t factor_bits(const Factor &f) { return f.type == DF_BIT ? (1ull << f.bit) : f.mask; }
@@ -169,9 +208,8 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
         const bool plain = algebra && slot[gi] < 0 && g.cmask == 0;
         if (plain && c == G_DENSE1) {
             cd dr[2], dl[2];
-            int form = 0;
-            double coef = 0.0;
-            if (!split_1q(g.m, dr, dl, &form, &coef)) {
+            double cg = 0.0, sg = 0.0;
+            if (!split_1q(g.m, dr, dl, &cg, &sg)) {
                 pf.push_back({Factor{DF_BIT, g.tbit[0], 0, g.m[0], g.m[3]}, (int)base.size()});
                 continue;
             }
@@ -179,12 +217,14 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
             Entry e{E_ROT};
             e.gi = gi;
             e.bit = g.tbit[0];
-            e.form = form;
-            e.coef = coef;
+            e.cg = cg;
+            e.sg = sg;
             base.push_back(e);
             blocks_bits.push_back(1ull << g.tbit[0]);
             is_grad.push_back(0);
-            pf.push_back({Factor{DF_BIT, g.tbit[0], 0, dl[0], dl[1]}, (int)base.size()});
+            Factor fl{DF_BIT, g.tbit[0], 0, dl[0], dl[1]};
+            fl.rot = gi;
+            pf.push_back({fl, (int)base.size()});
             continue;
         }
         if (plain && c == G_DIAG1) {
@@ -218,7 +258,7 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
     const int nbase = (int)base.size();
     for (const PF &q : pf) {
         const uint64_t fb = factor_bits(q.f);
-        const bool unitary = std::abs(std::abs(q.f.v0) - 1.0) < 1e-12 &&
+        const bool unitary = q.f.rot < 0 && std::abs(std::abs(q.f.v0) - 1.0) < 1e-12 &&
                              (q.f.type != DF_BIT || std::abs(std::abs(q.f.v1) - 1.0) < 1e-12);
         auto blocks = [&](int p) { return (blocks_bits[p] & fb) != 0 || (is_grad[p] && !unitary); };
         int left = -1, right = nbase;
@@ -517,20 +557,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             }
         }
         std::vector<std::vector<Factor>> at(nbase + 1);
-        for (int j = 0; j < nf; ++j) {  // factors in queue order
-            const Factor &f = facs[j].f;
-            std::vector<Factor> &bf = at[where[j]];
-            bool merged = false;
-            if (f.type == DF_BIT)  // one-bit diagonals on the same bit multiply
-                for (Factor &g : bf)
-                    if (g.type == DF_BIT && g.bit == f.bit) {
-                        g.v0 *= f.v0;
-                        g.v1 *= f.v1;
-                        merged = true;
-                        break;
-                    }
-            if (!merged) bf.push_back(f);
-        }
+        for (int j = 0; j < nf; ++j) at[where[j]].push_back(facs[j].f);  // in queue order
         for (int p = 0; p <= nbase; ++p) {
             if (!at[p].empty()) {
                 Entry b{E_BLOCK};
@@ -576,8 +603,12 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
 
     int nops = 0, nmat = 0, nst = 0;
     uint32_t cur = 0, curL = 0;
+    uint32_t curF = 0;  // register frame of the open stage (see tiled.h)
+    std::unordered_map<int, std::pair<cd, cd>> rot_dd;  // rotation gate -> diagonal joining its D_L
     const uint32_t highmask = ((1u << k) - 1u) & ~low5;
     auto open_stage = [&](uint32_t rset, const std::vector<int> &L) {
+        if (nst > 0) P.st[nst - 1].rflip = (uint8_t)curF;  // the transpose undoes the frame
+        curF = 0;
         TileStage &st = P.st[nst];
         uint32_t lset = 0;
         for (int x = 0; x < kTileLaneBits; ++x) {
@@ -672,22 +703,56 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             const int j = lane ? lane_index(lb) : regidx(lb);
             const uint8_t want = lane ? TOP_ROTS_L : TOP_ROTS_R;
             const int width = lane ? kTileLaneBits : RB;
-            const uint8_t tan_bit = (!lane && e.form == ROT_TAN) ? (uint8_t)(1u << j) : 0;
-            const uint8_t cot_bit = (!lane && e.form == ROT_COT) ? (uint8_t)(1u << j) : 0;
-            if (nops > P.st[nst - 1].op_begin && P.op[nops - 1].type == want &&
-                P.mat[P.op[nops - 1].m + j].y == (R)0) {
-                P.mat[P.op[nops - 1].m + j] = mkc<R>((R)e.coef, (R)(e.form + 1));
-                P.op[nops - 1].a |= tan_bit;  // register form: bit masks of the two forms
-                P.op[nops - 1].b |= cot_bit;
+            // place rotation coefficients in slot j: into the stage's last op when
+            // it is a rotation op of this kind with slot j free, else a new op
+            auto push_rot = [&](const V<R> &cf) {
+                if (nops > P.st[nst - 1].op_begin && P.op[nops - 1].type == want) {
+                    TileOp &prev = P.op[nops - 1];
+                    const bool free_slot = lane ? P.mat[prev.m + j].y == (R)0 : !((prev.a >> j) & 1u);
+                    if (free_slot) {
+                        P.mat[prev.m + j] = cf;
+                        if (!lane) prev.a |= (uint8_t)(1u << j);
+                        return true;
+                    }
+                }
+                if (nops + 1 > kTileMaxOps || nmat + width > kTileMaxMat) return false;
+                TileOp ro;
+                std::memset(&ro, 0, sizeof(ro));
+                ro.type = want;
+                ro.m = nmat;
+                ro.a = lane ? (uint8_t)0 : (uint8_t)(1u << j);
+                for (int x = 0; x < width; ++x) put(cd(0.0, 0.0));
+                P.mat[ro.m + j] = cf;
+                P.op[nops++] = ro;
+                P.st[nst - 1].op_end = (uint16_t)nops;
+                return true;
+            };
+            if (lane) {  // scaled forms (see TileRotForm); the scalar and sign join D_L
+                const bool tanf = e.cg >= e.sg;
+                rot_dd[e.gi] = tanf ? std::make_pair(cd(e.cg), cd(e.cg)) : std::make_pair(cd(-e.sg), cd(e.sg));
+                if (!push_rot(mkc<R>((R)(tanf ? e.sg / e.cg : e.cg / e.sg), (R)((tanf ? ROT_TAN : ROT_COT) + 1))))
+                    return overflow();
                 continue;
             }
-            if (nmat + width > kTileMaxMat) return overflow();
-            op.type = want;
-            op.m = nmat;
-            op.a = tan_bit;
-            op.b = cot_bit;
-            for (int x = 0; x < width; ++x) put(cd(0.0, 0.0));
-            P.mat[op.m + j] = mkc<R>((R)e.coef, (R)(e.form + 1));
+            // the swap of a near-swap rotation may stay in the frame when no later
+            // op of this stage, other than rotations and diagonal blocks (which the
+            // frame rewrites), touches the bit
+            bool allow = true;
+            for (int i2 = i + 1; i2 < ne && allow; ++i2) {
+                const int o2 = opener(i2);
+                if (o2 < ne && (needl[o2] & ~cur) != 0) break;  // the next stage opens
+                const Entry &e2 = ent[i2];
+                if (e2.kind != E_GATE) continue;
+                allow = cls[e2.gi] != G_ISING && !((qubit_bits(G[e2.gi]) >> e.bit) & 1ull);
+            }
+            const RotPlan q = rot_plan(e.cg, e.sg, (int)((curF >> j) & 1u), allow);
+            if (q.swap) curF ^= 1u << j;
+            rot_dd[e.gi] = std::make_pair(q.dd0, q.dd1);
+            // (a swap alone, cos h = 0, is all frame: no op)
+            if ((q.s1 != 0.0 || q.s2 != 0.0) && !push_rot(mkc<R>((R)q.s1, (R)q.s2))) return overflow();
+            // the third shear of the three-shear form: one more x += s1 y
+            if (q.three && !push_rot(mkc<R>((R)q.s1, (R)0))) return overflow();
+            continue;
         } else if (e.kind == E_BLOCK) {
             // constants (base, per-register-bit ratios) for the factors on
             // register bits alone; sign flips on two or more register bits become
@@ -695,6 +760,9 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             // complex factors first, then sign factors (a negation of the base or
             // of one ratio under conditions), then thread/mixed complex factors,
             // pairs last
+            // Everything on register bits is written for the stage's register
+            // frame F (register r holds register index r ^ F): a condition "bit
+            // j is 1" on a register bit of F reads "bit j is 0".
             cd cbase = 1.0;
             std::vector<cd> cu(RB, cd(1.0));
             std::vector<TileDFac<R>> outside, signs, single, pair;
@@ -702,19 +770,42 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             auto reg_pattern = [&](uint8_t mr) {
                 uint64_t pat = 0;
                 for (int r = 0; r < (1 << RB); ++r)
-                    if ((r & mr) == mr) pat |= 1ull << r;
+                    if (((r ^ curF) & mr) == mr) pat |= 1ull << r;
                 return pat;
             };
             auto is_pm1 = [](const cd &v) { return v == cd(1.0, 0.0) || v == cd(-1.0, 0.0); };
-            for (const Factor &f : e.fac) {
+            // the rotations' diagonals join their D_L factors; one-bit diagonals
+            // on the same bit multiply
+            std::vector<Factor> facl;
+            for (Factor f : e.fac) {
+                if (f.rot >= 0) {
+                    const auto it = rot_dd.find(f.rot);
+                    if (it != rot_dd.end()) {
+                        f.v0 *= it->second.first;
+                        f.v1 *= it->second.second;
+                    }
+                }
+                bool merged = false;
+                if (f.type == DF_BIT)
+                    for (Factor &g : facl)
+                        if (g.type == DF_BIT && g.bit == f.bit) {
+                            g.v0 *= f.v0;
+                            g.v1 *= f.v1;
+                            merged = true;
+                            break;
+                        }
+                if (!merged) facl.push_back(f);
+            }
+            for (const Factor &f : facl) {
                 TileDFac<R> d;
                 std::memset(&d, 0, sizeof(d));
                 d.type = (uint8_t)f.type;
                 if (f.type == DF_BIT) {
                     locate(f.bit, &d.tkind, &d.a, &d.tmask);
                     if (d.tkind == TB_REG) {
-                        cbase *= f.v0;
-                        cu[d.a] *= f.v1 / f.v0;
+                        const bool fl = (curF >> d.a) & 1u;
+                        cbase *= fl ? f.v1 : f.v0;
+                        cu[d.a] *= fl ? f.v0 / f.v1 : f.v1 / f.v0;
                         continue;
                     }
                     if (is_pm1(f.v0) && is_pm1(f.v1)) {  // +-1 values: a sign under the bit
@@ -745,16 +836,24 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                         const uint8_t rest = (uint8_t)(d.mr & (d.mr - 1));
                         fo.b = (uint8_t)__builtin_ctz(rest);
                         fo.mr = (uint8_t)(rest & (rest - 1));
+                        fo.tkind = (uint8_t)(((curF >> fo.a) & 1u) | (((curF >> fo.b) & 1u) << 1));
+                        fo.fx = (uint8_t)(curF & fo.mr);
                         fo.mt = d.mt;
                         fo.mo = d.mo;
                         flips.push_back(fo);
                         continue;
                     }
+                    const bool fl1 = nr == 1 && (curF & d.mr) != 0;  // one register bit, in the frame
                     if (d.mt == 0 && d.mo == 0) {        // register bits alone
                         if (nr == 0) {
                             cbase *= f.v0;
                         } else if (nr == 1) {
-                            cu[__builtin_ctz(d.mr)] *= f.v0;
+                            if (fl1) {
+                                cbase *= f.v0;
+                                cu[__builtin_ctz(d.mr)] /= f.v0;
+                            } else {
+                                cu[__builtin_ctz(d.mr)] *= f.v0;
+                            }
                         } else {
                             d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
                             d.tmask = reg_pattern(d.mr);
@@ -764,7 +863,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                     }
                     if (sign && nr <= 1) {                // negate the base or one ratio
                         d.type = DF_SIGN;
-                        d.a = nr ? d.mr : (uint8_t)0x80;
+                        d.a = nr ? (uint8_t)(d.mr | (fl1 ? 0x80 : 0)) : (uint8_t)0x80;
                         d.mr = 0;
                         signs.push_back(d);
                         continue;
@@ -772,6 +871,17 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                     d.v0 = mkc<R>((R)f.v0.real(), (R)f.v0.imag());
                     if (d.mr == 0 && d.mt == 0) {         // outside bits alone
                         outside.push_back(d);
+                        continue;
+                    }
+                    if (fl1) {  // v0 where the register bit is 0: v0 on all, 1 / v0 where it is 1
+                        TileDFac<R> d0 = d;
+                        d0.mr = 0;
+                        d0.tmask = reg_pattern(0);
+                        single.push_back(d0);
+                        const cd iv = 1.0 / f.v0;
+                        d.v0 = mkc<R>((R)iv.real(), (R)iv.imag());
+                        d.tmask = 0;
+                        single.push_back(d);
                         continue;
                     }
                     d.tmask = reg_pattern(d.mr);
@@ -937,6 +1047,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
             open_stage(choose(ne, 0u, highmask), natural);
         }
     }
+    P.st[nst - 1].rflip = (uint8_t)curF;  // the store undoes the last stage's frame
     P.n_stages = nst;
     P.n_grad = ngrad;
     if (dry_stages) {  // planning only: report the stage count
@@ -961,14 +1072,23 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     if (stats) {
         int cnt[16] = {0};
         for (int o = 0; o < nops; ++o) cnt[P.op[o].type & 15]++;
-        int rots = 0;
-        for (int o = 0; o < nops; ++o)
-            if (P.op[o].type == TOP_ROTS_R || P.op[o].type == TOP_ROTS_L)
+        int rots = 0, threes = 0, frames = 0;
+        for (int o = 0; o < nops; ++o) {
+            if (P.op[o].type == TOP_ROTS_R)
+                for (int j = 0; j < RB; ++j) {
+                    if (!((P.op[o].a >> j) & 1u)) continue;
+                    ++rots;
+                    threes += P.mat[P.op[o].m + j].y == (R)0;  // third shears
+                }
+            if (P.op[o].type == TOP_ROTS_L)
                 for (int j = 0; j < 5; ++j) rots += P.mat[P.op[o].m + j].y != (R)0;
+        }
+        for (int t = 0; t < nst; ++t) frames += __builtin_popcount(P.st[t].rflip);
         std::fprintf(stderr,
                      "[qsim plan] gates %zu entries %d stages %d ops %d: rots_r %d rots_l %d (rotations %d) "
-                     "dblock %d (factors %d) dense1 %d phase %d diag1 %d other %d\n",
-                     pp.gates.size(), ne, nst, nops, cnt[TOP_ROTS_R], cnt[TOP_ROTS_L], rots, cnt[TOP_DBLOCK], ndf,
+                     "third shears %d, frame bits at stage ends %d dblock %d (factors %d) dense1 %d phase %d diag1 %d other %d\n",
+                     pp.gates.size(), ne, nst, nops, cnt[TOP_ROTS_R], cnt[TOP_ROTS_L], rots, threes, frames,
+                     cnt[TOP_DBLOCK], ndf,
                      cnt[TOP_DENSE1_R] + cnt[TOP_DENSE1_L], cnt[TOP_PHASE], cnt[TOP_DIAG1],
                      nops - cnt[TOP_ROTS_R] - cnt[TOP_ROTS_L] - cnt[TOP_DBLOCK] - cnt[TOP_DENSE1_R] -
                          cnt[TOP_DENSE1_L] - cnt[TOP_PHASE] - cnt[TOP_DIAG1]);

@@ -61,18 +61,31 @@ enum TileOpType : uint8_t {
     TOP_SWAP_RR,     // swap register bits a < b
     TOP_GRAD,        // adjoint sweep: accumulate Im<lambda|P|phi> for a generator P
     TOP_ISING,       // psi_x *= exp(-i tau E(x)), E an Ising energy (<= 2-body Z terms)
-    TOP_ROTS_R,      // scaled real rotations on register bits: mat[m + j] = (coef, form + 1) or (0, 0);
-                     // a / b: masks of the register bits in tan / cot form
-    TOP_ROTS_L,      // the same on the 5 lane bits (warp shuffles)
+    TOP_ROTS_R,      // real rotations on register bits as in-place shears: for each bit j of a,
+                     // x += s1 y, then y += s2 x, with (s1, s2) = mat[m + j] and (x, y) the
+                     // register pairs that differ in bit j (x: bit j is 0)
+    TOP_ROTS_L,      // scaled real rotations on the 5 lane bits (warp shuffles):
+                     // mat[m + j] = (coef, form + 1) or (0, 0)
     TOP_DBLOCK,      // product of diagonal factors (see diag_block)
-    TOP_FLIP,        // negate where register bits a and b (and the required bits) are 1
+    TOP_FLIP,        // negate the registers whose bit a is 1 - (tkind & 1), bit b is
+                     // 1 - (tkind >> 1 & 1), and whose bits of mr, XORed with fx, are 1
     TOP_PROT,        // per-member RY (b = 0) or RX (b = 1) on register bit a: (cos, sin) from the member's table
 };
 
-// Scaled real rotations: form 0: (a, b) <- (a - t b, b + t a) with |t| <= 1;
-// form 1: (a, b) <- (b - u a, a + u b) with |u| <= 1. The planner moves the
-// scalar and sign that make these equal to the rotation into diagonal factors.
+// Scaled real rotations on lane bits: form 0: (a, b) <- (a - t b, b + t a)
+// with |t| <= 1; form 1: (a, b) <- (b - u a, a + u b) with |u| <= 1. The
+// planner moves the scalar and sign that make these equal to the rotation
+// into diagonal factors.
 enum TileRotForm : uint8_t { ROT_TAN = 0, ROT_COT = 1 };
+
+// Register frame. A rotation closer to a swap than to the identity is applied
+// as the shears of the remaining small rotation, and the swap of the two
+// register halves is not carried out: from there to the end of the stage
+// register r holds the amplitude of register index r ^ rflip (rflip = the
+// register bits swapped so far). The planner writes every later op of the
+// stage in those terms; the transpose that ends the stage writes register r
+// where r ^ rflip belongs (an XOR of the stage's write offsets), and so does
+// the last stage's store, so the next stage starts with no frame.
 
 // One factor of a diagonal block, located in the block's stage:
 //   DF_BIT: diag(v0, v1) on one thread bit (kind TB_THREAD, local mask tmask)
@@ -105,7 +118,7 @@ struct TileOp {
     uint8_t mr;
     uint8_t pm;       // 1: matrix entries come from the per-member table (pmat)
     uint8_t gl;       // TOP_GRAD: row of this op in the pass's gradient table
-    uint8_t pad0;
+    uint8_t fx;       // TOP_FLIP: register frame bits among mr
     uint32_t mt;
     uint32_t m;       // first matrix-pool entry
     uint64_t mo;
@@ -129,6 +142,7 @@ struct TileStage {
     uint8_t lloc[5];  // local bit of lane bit i (the first and last stage: 0..4)
     uint8_t fcol[9];  // swizzle of the transpose into this stage: low-bit image of high local bit h + i
     uint8_t need_lt;  // some op of the stage tests thread-local bits
+    uint8_t rflip;    // register frame at the end of the stage (register bits)
     uint16_t rw[6];   // transpose into this stage: byte offset of the previous stage's register bit j
     uint16_t rr[6];   // ... and of this stage's register bit j
     uint16_t op_begin, op_end;

@@ -7,9 +7,12 @@
 // tile's local indices; gates the planner sends to unfused passes are applied
 // as dense matrices. The test-suite compares the results with the oracle, so
 // planner logic (pass selection, stages, factor placement, commutation rules,
-// the adjoint sweep's gradient ops) is checked without a GPU. Nothing here is
-// part of the library; shared memory, swizzles and the thread decomposition of
-// the kernel are not emulated (the local index is used directly).
+// the adjoint sweep's gradient ops, the register frame) is checked without a
+// GPU. Nothing here is part of the library. Each stage's registers are held per
+// thread as the kernel holds them: filled from the tile's local indices when
+// the stage opens, changed by the ops in place, and written back (through the
+// stage's register frame) when it ends; shared-memory positions and swizzles
+// are not emulated.
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
@@ -131,6 +134,9 @@ template <typename R> static qs_status emulate_pass(qs_state *s, const TileParam
                 return li;
             };
             const uint32_t nthreads = 32u << WB;
+            std::vector<cdd> REG((size_t)nthreads * NR);
+            for (uint32_t th = 0; th < nthreads; ++th)
+                for (int r = 0; r < NR; ++r) REG[(size_t)th * NR + r] = A[local_of(th, r)];
             for (int o = st.op_begin; o < st.op_end; ++o) {
                 const TileOp &op = p.op[o];
                 const V<R> *M = &p.mat[op.m];
@@ -138,7 +144,7 @@ template <typename R> static qs_status emulate_pass(qs_state *s, const TileParam
                     const uint32_t lt = local_of(th, 0);
                     const bool ok = ((tbase & op.mo) == op.mo) && ((lt & op.mt) == op.mt);
                     cdd *a[NR];
-                    for (int r = 0; r < NR; ++r) a[r] = &A[local_of(th, r)];
+                    for (int r = 0; r < NR; ++r) a[r] = &REG[(size_t)th * NR + r];
                     const uint32_t mr = op.mr;
                     switch (op.type) {
                     case TOP_DENSE1_R:
@@ -188,28 +194,27 @@ template <typename R> static qs_status emulate_pass(qs_state *s, const TileParam
                         }
                         break;
                     case TOP_ROTS_R:
+                        // in-place shears x += s1 y, y += s2 x
                         for (int j = 0; j < RB; ++j) {
-                            const bool tanf = (op.a >> j) & 1, cotf = (op.b >> j) & 1;
-                            if (!tanf && !cotf) continue;
-                            const double c = (double)M[j].x;
+                            if (!((op.a >> j) & 1)) continue;
+                            const double s1 = (double)M[j].x, s2 = (double)M[j].y;
                             for (int r = 0; r < NR; ++r) {
                                 if ((r >> j) & 1) continue;
-                                const cdd x = *a[r], y = *a[r | (1 << j)];
-                                if (tanf) {
-                                    *a[r] = x - c * y;
-                                    *a[r | (1 << j)] = y + c * x;
-                                } else {
-                                    *a[r] = y - c * x;
-                                    *a[r | (1 << j)] = x + c * y;
-                                }
+                                cdd &x = *a[r], &y = *a[r | (1 << j)];
+                                x += s1 * y;
+                                y += s2 * x;
                             }
                         }
                         break;
-                    case TOP_FLIP:
+                    case TOP_FLIP: {
+                        // bits a and b equal to 1 in the frame's terms (tkind: frame on a, b)
                         if (!ok) break;
+                        const int va = 1 - (op.tkind & 1), vb = 1 - ((op.tkind >> 1) & 1);
                         for (int r = 0; r < NR; ++r)
-                            if (((r >> op.a) & 1) && ((r >> op.b) & 1) && (r & mr) == mr) *a[r] = -*a[r];
+                            if (((r >> op.a) & 1) == va && ((r >> op.b) & 1) == vb && ((r ^ op.fx) & mr) == mr)
+                                *a[r] = -*a[r];
                         break;
+                    }
                     case TOP_DBLOCK: {
                         const int f0 = (int)op.mo, nf = op.b, np = op.a, no = op.gl, ns = op.tkind;
                         cdd base = C<R>(M[0]);
@@ -273,7 +278,7 @@ template <typename R> static qs_status emulate_pass(qs_state *s, const TileParam
                                 } else {
                                     // target on lane bit op.a: the partner is the lane's neighbour
                                     const uint32_t partner = th ^ (1u << op.a);
-                                    ph = A[local_of(partner, r)];
+                                    ph = REG[(size_t)partner * NR + r];
                                     const cdd v = std::conj(la) * ph;
                                     const int bit = (th >> op.a) & 1;
                                     acc += op.b == GEN_X ? v.imag() : (bit ? v.real() : -v.real());
@@ -317,6 +322,9 @@ template <typename R> static qs_status emulate_pass(qs_state *s, const TileParam
                     }
                 }
             }
+            // the transpose (or the store) writes register r where r ^ rflip belongs
+            for (uint32_t th = 0; th < nthreads; ++th)
+                for (int r = 0; r < NR; ++r) A[local_of(th, r ^ st.rflip)] = REG[(size_t)th * NR + r];
         }
         for (uint32_t li = 0; li < (1u << k); ++li) psi[gidx(li)] = A[li];
     }
