@@ -541,11 +541,14 @@ __device__ __forceinline__ uint32_t reg_local(int r, const uint32_t *l) {
     return o;
 }
 
-// FULL = false compiles a lean kernel without the rarely used ops (4x4 gates,
-// swaps, Ising phases, gradients): less code, fewer instruction-fetch stalls.
-template <typename R, int RB, bool FULL>
+// MODE selects the ops compiled in (less code, fewer instruction-fetch
+// stalls): 0: rotations on register bits, diagonal blocks, sign flips, phase
+// and one-bit diagonal gates; 1: also dense one-qubit gates, lane rotations and
+// per-member rotations; 2: also 4x4 gates, swaps, Ising phases and gradients.
+template <typename R, int RB, int MODE>
 __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
     tiled_kernel(V<R> *__restrict__ psi, const __grid_constant__ TileParams<R> p) {
+    constexpr bool FULL = MODE == 2;
     constexpr int NR = 1 << RB;
     constexpr int WB = TileCfg<R>::WB;
     constexpr int NW = 1 << WB;
@@ -625,6 +628,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                 };
                 switch (op.type) {
                 case TOP_DENSE1_L: {
+                    if constexpr (MODE < 1) break;
                     // every lane takes part in the shuffles; only `ok` lanes update
                     const bool ok = req_ok();
                     const uint32_t mr = op.mr;
@@ -640,6 +644,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     break;
                 }
                 case TOP_DENSE1_R:
+                    if constexpr (MODE < 1) break;
                     if (req_ok()) {
                         const V<R> *M = mat_of();
                         dispatch_dense1<R, RB>(a, op.a, M[0], M[1], M[2], M[3], op.mr);
@@ -705,6 +710,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     break;
                 }
                 case TOP_ROTS_L: {
+                    if constexpr (MODE < 1) break;
                     // own value in row `bit`, partner value v from lane ^ (1 << j)
                     const V<R> *M = &p.mat[op.m];
 #pragma unroll
@@ -729,6 +735,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                     if (req_ok()) dispatch_flip<R, RB>(a, op.a, op.b, op.mr, op.tkind, op.fx);
                     break;
                 case TOP_PROT:
+                    if constexpr (MODE < 1) break;
                     if (req_ok()) {
                         const V<R> *M = mat_of();
                         // table: RY m[2] = (s, 0); RX m[2] = (0, -s)
@@ -817,7 +824,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
 }
 
 template <typename R>
-static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) {
+static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, int mode) {
     constexpr int RB = TileCfg<R>::RB;
     constexpr int threads = 32 << TileCfg<R>::WB;
     // the tile, then the transpose-offset and local-index tables (6 bytes per
@@ -830,12 +837,14 @@ static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) 
     const int dev = (s->device >= 0 && s->device < 64) ? s->device : 0;
     static int blocks_per_sm[64] = {0};
     if (!configured[dev]) {
-        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_max));
-        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_max));
+        QS_CUDA_TRY(cudaFuncSetAttribute(tiled_kernel<R, RB, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_max));
         int bps = 0;
-        QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB, true>, threads,
+        QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tiled_kernel<R, RB, 2>, threads,
                                                                   smem_max));
         int sms = 0;
         QS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -845,10 +854,12 @@ static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, bool full) 
     const uint64_t grid = std::min<uint64_t>(p.total_tiles, (uint64_t)blocks_per_sm[dev]);
     if (grid == 0) return QS_OK;
     ProfScope _ps(s->stream, KC_TILED);
-    if (full)
-        tiled_kernel<R, RB, true><<<(unsigned)grid, threads, smem, s->stream>>>((V<R> *)s->data, p);
+    if (mode == 2)
+        tiled_kernel<R, RB, 2><<<(unsigned)grid, threads, smem, s->stream>>>((V<R> *)s->data, p);
+    else if (mode == 1)
+        tiled_kernel<R, RB, 1><<<(unsigned)grid, threads, smem, s->stream>>>((V<R> *)s->data, p);
     else
-        tiled_kernel<R, RB, false><<<(unsigned)grid, threads, smem, s->stream>>>((V<R> *)s->data, p);
+        tiled_kernel<R, RB, 0><<<(unsigned)grid, threads, smem, s->stream>>>((V<R> *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }
@@ -862,25 +873,27 @@ qs_status tiled_configure(qs_state *s) {
     pf.k = tile_bits(QS_C64);
     pd.k = tile_bits(QS_C128);
     // total_tiles = 0: the launches configure the attributes and do no work
-    QS_TRY(launch_tiled_t<float>(s, pf, true));
-    return launch_tiled_t<double>(s, pd, true);
+    QS_TRY(launch_tiled_t<float>(s, pf, 2));
+    return launch_tiled_t<double>(s, pd, 2);
 }
 
-// a pass needs the full kernel if it holds a 4x4 gate, a swap, an Ising phase or a gradient op
-template <typename R> static bool needs_full(const TileParams<R> &p) {
+// the smallest kernel MODE that holds every op of the pass
+template <typename R> static int kernel_mode(const TileParams<R> &p) {
+    int mode = p.n_grad > 0 ? 2 : 0;
     for (int st = 0; st < p.n_stages; ++st)
         for (int o = p.st[st].op_begin; o < p.st[st].op_end; ++o) {
             const int t = p.op[o].type;
-            if (t == TOP_DENSE2_RR || t == TOP_SWAP_RR || t == TOP_ISING || t == TOP_GRAD) return true;
+            if (t == TOP_DENSE2_RR || t == TOP_SWAP_RR || t == TOP_ISING || t == TOP_GRAD) return 2;
+            if (t == TOP_DENSE1_R || t == TOP_DENSE1_L || t == TOP_ROTS_L || t == TOP_PROT) mode = 1;
         }
-    return p.n_grad > 0;
+    return mode;
 }
 
 qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) {
-    return launch_tiled_t<float>(s, p, needs_full(p));
+    return launch_tiled_t<float>(s, p, kernel_mode(p));
 }
 qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) {
-    return launch_tiled_t<double>(s, p, needs_full(p));
+    return launch_tiled_t<double>(s, p, kernel_mode(p));
 }
 
 }  // namespace qsim
