@@ -10,6 +10,7 @@ import math
 import numpy as np
 import pytest
 
+import circuit_utils
 import oracle
 from paper_2009_01845_gb300 import inputs as qi
 
@@ -240,6 +241,19 @@ def test_tiled_mixed_gates_with_controls_matches_oracle(qs, dtype, n):
     gates on bits inside and outside the tile, 2-qubit dense gates and SWAPs."""
     gates = qi.random_mixed_circuit(n, 150, seed=500 + n, max_controls=3, max_unitary_k=2)
     psi0 = qi.random_state(n, 40 + n)
+    want = oracle.apply_circuit(psi0.copy(), n, gates)
+    st = qs.State(n, dtype=dtype).set(psi0).apply(gates, mode="tiled")
+    close(st.get(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [13, 16])
+def test_tiled_near_swap_rotations_matches_oracle(qs, dtype, n):
+    """Rotations closer to a swap than to the identity, whose swap the tiled
+    pass keeps in a register frame, followed in the same stages by sign flips
+    on two and three register bits, controlled phases and further rotations."""
+    gates = circuit_utils.near_swap_circuit(n, 6, seed=n)
+    psi0 = qi.random_state(n, 90 + n)
     want = oracle.apply_circuit(psi0.copy(), n, gates)
     st = qs.State(n, dtype=dtype).set(psi0).apply(gates, mode="tiled")
     close(st.get(), want, dtype)

@@ -12,6 +12,7 @@ import subprocess
 import numpy as np
 import pytest
 
+import circuit_utils
 import oracle
 from paper_2009_01845_gb300 import inputs as qi
 from paper_2009_01845_gb300 import qsim
@@ -173,31 +174,10 @@ def test_tiled_trotter_steps(emu, dtype):
     assert np.max(np.abs(got - want)) < TOL[dtype]
 
 
-def near_swap_circuit(n, layers, seed):
-    """U3 gates whose rotation is closer to a swap than to the identity
-    (theta in (pi/2, pi): their swap stays in the register frame), with CZ and
-    controlled-CZ sign flips and controlled phases on the same qubits in the
-    same stages, so that the frame rewrites flips, pair factors and
-    register-bit phases."""
-    r = qi.rng(seed)
-    gates = []
-    for l in range(layers):
-        for q in range(n):
-            th = float(r.uniform(2.0, 3.1))
-            gates.append(qi.Gate("U3", (q,), (), (th, float(r.uniform(0, 6.28)), float(r.uniform(0, 6.28)))))
-        for q in range(l % 3, n - 2, 3):
-            gates.append(qi.Gate("CZ", (q, q + 1), (q + 2,)))
-            gates.append(qi.Gate("CZ", (q + 1, q + 2)))
-            gates.append(qi.Gate("CU1", (q, q + 2), (), (float(r.uniform(0, 6.28)),)))
-        gates.append(qi.Gate("X", (l % n,)))
-        gates.append(qi.Gate("RZ", ((l + 4) % n,), ((l + 1) % n,), (float(r.uniform(0, 6.28)),)))
-    return gates
-
-
 @pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("n,seed", [(13, 5), (14, 6)])
 def test_register_frame(emu, dtype, n, seed):
-    gates = near_swap_circuit(n, 6, seed)
+    gates = circuit_utils.near_swap_circuit(n, 6, seed)
     psi0 = qi.random_state(n, seed)
     got = run_emulated(emu, n, gates, dtype, psi0)
     want = oracle.run_circuit(n, gates, psi0)
