@@ -15,6 +15,11 @@ the single-state path does not shard without an exchange step), weak scaling.
 
 ``--impl reference`` times the CPU oracle (the plain complex128 unfused
 simulator) on the host cores on a bounded sample of the same workload.
+
+``--only NAME`` runs one secondary workload alone (variational_adjoint,
+adiabatic_batch, fused_tc, unfused_passes, qft_n18_c128,
+random_layer_c128_n33) and prints its result as one JSON line: for
+profiling those kernels; it is not the benchmark line.
 """
 from __future__ import annotations
 
@@ -50,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the secondary workloads (variational adjoint)")
+    ap.add_argument("--only", default=None, choices=sorted(SECONDARY),
+                    help="run one secondary workload alone and print its result")
     return ap.parse_args()
 
 
@@ -306,6 +313,13 @@ def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
                                                          steps=steps)
 
     t_b = _time_cuda(batched, 1, warmup=1)
+    # device time by kernel class of one batched run (the rest of t_b is host work)
+    qsim.profile_collect()
+    qsim.profile_enable(True)
+    batched()
+    torch.cuda.synchronize()
+    qsim.profile_enable(False)
+    prof_b = {k: {"ms": v[0], "launches": v[1]} for k, v in qsim.profile_collect().items() if v[1]}
     solo = {w: qsim.State(w, dtype=dtype) for w in widths}
 
     def sequential():
@@ -337,6 +351,8 @@ def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
             "instance_steps_per_s_batched": isteps / (t_b / 1000.0),
             "instance_steps_per_s_sequential": isteps / (t_s / 1000.0),
             "projected_full_run_s_batched": t_b / 1000.0 * 1000 / steps,
+            "kernels_batched_run": prof_b,
+            "widths": {int(w): len(ix) for w, ix in groups.items()},
             "smallest_instance": {"n": m0, "final_energy": e_final, "ground_energy": float(gmin),
                                   "ground_state_overlap": float(p[ground].sum())}}
 
@@ -628,12 +644,8 @@ def run_ours(a):
         st.close()
         del st
         torch.cuda.empty_cache()
-        secondary["variational_adjoint"] = variational_adjoint()
-        secondary["adiabatic_batch"] = adiabatic_batch()
-        secondary["fused_tc"] = fused_tc()
-        secondary["unfused_passes"] = unfused_passes()
-        secondary["qft_n18_c128"] = qft_n18()
-        secondary["random_layer_c128_n33"] = random_layer_c128()
+        for name, fn in SECONDARY.items():
+            secondary[name] = fn()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -655,8 +667,21 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+SECONDARY = {
+    "variational_adjoint": lambda: variational_adjoint(),
+    "adiabatic_batch": lambda: adiabatic_batch(),
+    "fused_tc": lambda: fused_tc(),
+    "unfused_passes": lambda: unfused_passes(),
+    "qft_n18_c128": lambda: qft_n18(),
+    "random_layer_c128_n33": lambda: random_layer_c128(),
+}
+
+
 def main():
     a = parse()
+    if a.only:
+        print(json.dumps({a.only: SECONDARY[a.only]()}), flush=True)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

@@ -77,6 +77,10 @@ struct LGate {
     bool is_swap = false;      // the SWAP permutation
     int param_index = -1;      // batched parameter column, or -1
     int kind = -1;             // QS_GATE_* of the source gate, or kKindGrad
+    // tiled pass: if the gate is a real rotation (no diagonal factors), apply
+    // it as three in-place shears, which need no diagonal block after it (set
+    // where no other diagonal sits between a qubit's rotations: Trotter layers)
+    bool paeth = false;
     // adjoint sweep only (kind == kKindGrad): generator (GEN_X/Y/Z/PROJ) and
     // the gradient slot the op accumulates into
     int grad_gen = -1;

@@ -138,36 +138,8 @@ qs_status ensure_itab(qs_state *s, size_t doubles) {
 // layers. `taus[k]` precedes layer k; layer k rotates qubit q by 2 dt a_q(s_k).
 static qs_status trotter_tiled(qs_state *s, const TrotterTerms &tt, const std::vector<double> &taus,
                                const std::vector<double> &svals, double dt) {
-    const int n = s->n;
     std::vector<LGate> G;
-    G.reserve(taus.size() + svals.size() * n);
-    auto ising = [&](double tau) {
-        if (tau == 0.0 || tt.d1.empty()) return;
-        LGate g;
-        g.kind = kKindIsing;
-        g.k = 0;
-        g.diagonal = true;
-        g.m.assign(1, cd(tau, 0.0));
-        G.push_back(g);
-    };
-    for (size_t k = 0; k < svals.size(); ++k) {
-        ising(taus[k]);
-        for (int q = 0; q < n; ++q) {
-            const double a = (1.0 - svals[k]) * tt.a0[q] + svals[k] * tt.a1[q];
-            if (a == 0.0) continue;
-            qs_gate g;
-            std::memset(&g, 0, sizeof(g));
-            g.kind = QS_GATE_RX;
-            g.n_targets = 1;
-            g.targets[0] = q;
-            g.param_index = -1;
-            g.params[0] = 2.0 * dt * a;
-            LGate lg;
-            QS_TRY(lower_gate(n, g, &lg));
-            G.push_back(lg);
-        }
-    }
-    ising(taus[svals.size()]);
+    QS_TRY(trotter_queue(s->n, tt.a0, tt.a1, taus, svals, dt, !tt.d1.empty(), &G));
     return run_tiled(s, G, nullptr, 0);
 }
 

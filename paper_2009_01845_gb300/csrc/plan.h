@@ -24,6 +24,19 @@ qs_status run_trotter(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const q
 qs_status run_tiled(qs_state *s, const std::vector<LGate> &gates, const double *params_dev, int n_params,
                     int force_bit = -1, double *gpart = nullptr, double param_sign = 1.0);
 
+// The gate queue of a second-order Trotter evolution on the tiled path: per
+// step k an Ising phase exp(-i taus[k] E) (the merged half steps; none where
+// `ising` is false or the angle is 0), then RX(2 dt a_q(s_k)) on every qubit
+// with a_q(s) = (1 - s) a0[q] + s a1[q]; a last Ising phase taus[steps]. It is
+// written in the frame of S = diag(1, i) on every qubit: S X S^dag = Y, so
+// RX(t) = S^dag RY(t) S, and S commutes with the diagonal Ising phases; the
+// queue is S on every qubit, the steps with RY for RX, then S^dag on every
+// qubit. The RY layers are real rotations with no diagonal factors, applied as
+// three in-place shears: no diagonal block between the layers.
+qs_status trotter_queue(int n, const std::vector<double> &a0, const std::vector<double> &a1,
+                        const std::vector<double> &taus, const std::vector<double> &svals, double dt, bool ising,
+                        std::vector<LGate> *G);
+
 // Adiabatic evolution of a batch whose members have their own H1 (terms
 // h1[off[b] .. off[b+1]) for member b).
 qs_status run_adiabatic_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,

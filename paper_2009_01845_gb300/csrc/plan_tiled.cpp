@@ -107,6 +107,7 @@ struct Entry {
     int gi = -1;              // E_GATE / E_ROT: gate index
     int bit = -1;             // E_ROT: index bit
     double cg = 0.0, sg = 0.0;  // E_ROT: cos h, sin h of R = [[cos h, -sin h], [sin h, cos h]]
+    bool paeth = false;       // E_ROT: U = R (no diagonal factors), three shears
     std::vector<Factor> fac;  // E_BLOCK
 };
 
@@ -149,10 +150,12 @@ struct RotPlan {
     bool three, swap;
     cd dd0, dd1;
 };
-RotPlan rot_plan(double cg, double sg, int frame, bool allow_swap) {
+RotPlan rot_plan(double cg, double sg, int frame, bool allow_swap, bool paeth) {
     RotPlan q{};
     const double sc = sg * cg;
-    if (cg >= sg) {
+    if (paeth) {
+        allow_swap = false;
+    } else if (cg >= sg) {
         const double t = sg / cg;
         q.s1 = frame ? t : -t;
         q.s2 = frame ? -sc : sc;
@@ -165,7 +168,8 @@ RotPlan rot_plan(double cg, double sg, int frame, bool allow_swap) {
         q.s2 = frame ? sc : -sc;
         q.dd0 = frame ? -sg : -1.0 / sg;
         q.dd1 = frame ? 1.0 / sg : sg;
-    } else {
+    }
+    if (paeth || (cg < sg && !allow_swap)) {
         const double th = sg / (1.0 + cg);  // tan(h/2)
         q.three = true;
         q.s1 = frame ? th : -th;
@@ -213,15 +217,21 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
                 pf.push_back({Factor{DF_BIT, g.tbit[0], 0, g.m[0], g.m[3]}, (int)base.size()});
                 continue;
             }
-            pf.push_back({Factor{DF_BIT, g.tbit[0], 0, dr[0], dr[1]}, (int)base.size()});
+            // a real rotation marked for three shears has no factors at all (the
+            // lanes are free, so it always runs on a register bit)
+            const auto one = [](const cd &v) { return std::abs(v - cd(1.0)) < 1e-15; };
+            const bool paeth = g.paeth && one(dr[1]) && one(dl[0]) && one(dl[1]);
+            if (!paeth) pf.push_back({Factor{DF_BIT, g.tbit[0], 0, dr[0], dr[1]}, (int)base.size()});
             Entry e{E_ROT};
             e.gi = gi;
             e.bit = g.tbit[0];
             e.cg = cg;
             e.sg = sg;
+            e.paeth = paeth;
             base.push_back(e);
             blocks_bits.push_back(1ull << g.tbit[0]);
             is_grad.push_back(0);
+            if (paeth) continue;
             Factor fl{DF_BIT, g.tbit[0], 0, dl[0], dl[1]};
             fl.rot = gi;
             pf.push_back({fl, (int)base.size()});
@@ -678,11 +688,42 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         return QS_OK;
     };
 
+    // Third shears of three-shear rotations wait (slot, coefficient) until an
+    // entry other than a rotation on another register bit comes, or the stage
+    // ends; then they go out as one op (rotations on other bits commute with
+    // them, so a run of rotations costs two ops, not one per rotation).
+    std::vector<std::pair<int, R>> third;
+    auto flush_third = [&]() {
+        if (third.empty()) return true;
+        if (nops + 1 > kTileMaxOps || nmat + RB > kTileMaxMat) return false;
+        TileOp ro;
+        std::memset(&ro, 0, sizeof(ro));
+        ro.type = TOP_ROTS_R;
+        ro.m = nmat;
+        for (int x = 0; x < RB; ++x) put(cd(0.0, 0.0));
+        for (const auto &t3 : third) {
+            ro.a |= (uint8_t)(1u << t3.first);
+            P.mat[ro.m + t3.first] = mkc<R>(t3.second, (R)0);
+        }
+        P.op[nops++] = ro;
+        P.st[nst - 1].op_end = (uint16_t)nops;
+        third.clear();
+        return true;
+    };
     // the first stage reads the tile with lanes on the 5 lowest bits
     open_stage(choose(0, (ne ? needl[0] : 0u) & highmask, highmask), natural);
     for (int i = 0; i < ne; ++i) {
         const Entry &e = ent[i];
         const int oi = opener(i);
+        if (!third.empty()) {
+            bool keep = e.kind == E_ROT && !(oi < ne && (needl[oi] & ~cur) != 0);
+            if (keep) {
+                const int lb3 = loc_of[e.bit];
+                keep = ((cur >> lb3) & 1u) != 0;
+                for (const auto &t3 : third) keep = keep && t3.first != regidx(lb3);
+            }
+            if (!keep && !flush_third()) return overflow();
+        }
         if (oi < ne && (needl[oi] & ~cur) != 0) {
             if (nst >= kTileMaxStages) return overflow();
             if (free_lanes) {
@@ -745,13 +786,13 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 if (e2.kind != E_GATE) continue;
                 allow = cls[e2.gi] != G_ISING && !((qubit_bits(G[e2.gi]) >> e.bit) & 1ull);
             }
-            const RotPlan q = rot_plan(e.cg, e.sg, (int)((curF >> j) & 1u), allow);
+            const RotPlan q = rot_plan(e.cg, e.sg, (int)((curF >> j) & 1u), allow, e.paeth);
             if (q.swap) curF ^= 1u << j;
             rot_dd[e.gi] = std::make_pair(q.dd0, q.dd1);
             // (a swap alone, cos h = 0, is all frame: no op)
             if ((q.s1 != 0.0 || q.s2 != 0.0) && !push_rot(mkc<R>((R)q.s1, (R)q.s2))) return overflow();
             // the third shear of the three-shear form: one more x += s1 y
-            if (q.three && !push_rot(mkc<R>((R)q.s1, (R)0))) return overflow();
+            if (q.three) third.push_back({j, (R)q.s1});
             continue;
         } else if (e.kind == E_BLOCK) {
             // constants (base, per-register-bit ratios) for the factors on
@@ -1033,6 +1074,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
         P.op[nops++] = op;
         P.st[nst - 1].op_end = (uint16_t)nops;
     }
+    if (!flush_third()) return overflow();
     // the last stage stores the tile through its own lane map when every warp
     // store covers whole 32-byte sectors (index bits 0 and 1 on lanes for
     // complex64, bit 0 for complex128); otherwise one more stage puts the lanes
@@ -1215,6 +1257,46 @@ static std::vector<std::vector<int>> run_orders(const std::vector<LGate> &G, con
         if (o != gates) out.push_back(o);
     }
     return out;
+}
+
+qs_status trotter_queue(int n, const std::vector<double> &a0, const std::vector<double> &a1,
+                        const std::vector<double> &taus, const std::vector<double> &svals, double dt, bool ising,
+                        std::vector<LGate> *G) {
+    G->clear();
+    auto one_qubit = [&](int kind, int q, double angle) {
+        qs_gate g;
+        std::memset(&g, 0, sizeof(g));
+        g.kind = kind;
+        g.n_targets = 1;
+        g.targets[0] = q;
+        g.param_index = -1;
+        g.params[0] = angle;
+        LGate lg;
+        QS_TRY(lower_gate(n, g, &lg));
+        lg.paeth = kind == QS_GATE_RY;
+        G->push_back(lg);
+        return QS_OK;
+    };
+    auto ising_phase = [&](double tau) {
+        if (tau == 0.0 || !ising) return;
+        LGate g;
+        g.kind = kKindIsing;
+        g.k = 0;
+        g.diagonal = true;
+        g.m.assign(1, cd(tau, 0.0));
+        G->push_back(g);
+    };
+    for (int q = 0; q < n; ++q) QS_TRY(one_qubit(QS_GATE_S, q, 0.0));
+    for (size_t k = 0; k < svals.size(); ++k) {
+        ising_phase(taus[k]);
+        for (int q = 0; q < n; ++q) {
+            const double a = (1.0 - svals[k]) * a0[q] + svals[k] * a1[q];
+            if (a != 0.0) QS_TRY(one_qubit(QS_GATE_RY, q, 2.0 * dt * a));
+        }
+    }
+    ising_phase(taus[svals.size()]);
+    for (int q = 0; q < n; ++q) QS_TRY(one_qubit(QS_GATE_SDG, q, 0.0));
+    return QS_OK;
 }
 
 qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *params, int n_params, int force_bit,

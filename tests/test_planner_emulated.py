@@ -46,6 +46,8 @@ def emu(tmp_path_factory):
                               ctypes.c_void_p]
     lib.emu_trotter.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
+    lib.emu_apply_flags.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_int]
     lib.emu_last_error.restype = ctypes.c_char_p
     return lib
 
@@ -182,3 +184,30 @@ def test_register_frame(emu, dtype, n, seed):
     got = run_emulated(emu, n, gates, dtype, psi0)
     want = oracle.run_circuit(n, gates, psi0)
     assert np.max(np.abs(got - want)) < TOL[dtype] * 3
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [13, 14])
+def test_three_shear_rotations(emu, dtype, n):
+    """Real rotations marked for three in-place shears (as the Trotter layers
+    are): runs of RY on several qubits, the same qubit rotated twice in a row
+    (the deferred third shear must go out first), small and near-pi angles,
+    with CZ and RZ between some runs."""
+    r = qi.rng(n)
+    gates = []
+    for l in range(8):
+        qs = r.permutation(n)[:7]
+        for q in qs:
+            gates.append(qi.Gate("RY", (int(q),), (), (float(r.uniform(0.01, 3.1)),)))
+            if r.uniform() < 0.4:
+                gates.append(qi.Gate("RY", (int(q),), (), (float(r.uniform(0.01, 3.1)),)))
+        if l % 3 == 2:
+            gates.append(qi.Gate("CZ", (l % n, (l + 1) % n)))
+            gates.append(qi.Gate("RZ", ((l + 5) % n,), (), (float(r.uniform(0, 6.28)),)))
+    psi0 = qi.random_state(n, n + 3)
+    psi = np.array(psi0, dtype=np.complex128)
+    arr, keep = qsim.marshal_gates(gates)
+    st = emu.emu_apply_flags(n, dtype, arr, len(gates), psi.ctypes.data, 1)
+    assert st == 0, emu.emu_last_error().decode()
+    want = oracle.run_circuit(n, gates, psi0)
+    assert np.max(np.abs(psi - want)) < TOL[dtype] * 3

@@ -340,9 +340,17 @@ static int g_calls = 0;
 
 extern "C" {
 
+int emu_apply_flags(int n, int dtype, const qs_gate *gates, int count, double *psi, int flags);
+
 // psi (complex128, 2^n) <- circuit(psi) through the planner's tiled passes,
 // planned for complex64 (dtype 0) or complex128 (dtype 1) descriptors
 int emu_apply(int n, int dtype, const qs_gate *gates, int count, double *psi) {
+    return emu_apply_flags(n, dtype, gates, count, psi, 0);
+}
+
+// the same with RY gates marked for three in-place shears (flags & 1), as the
+// Trotter queue marks its layers
+int emu_apply_flags(int n, int dtype, const qs_gate *gates, int count, double *psi, int flags) {
     qs_state s;
     s.n = n;
     s.ms = n;
@@ -350,8 +358,10 @@ int emu_apply(int n, int dtype, const qs_gate *gates, int count, double *psi) {
     s.dtype = (qs_dtype)dtype;
     s.data = psi;
     std::vector<LGate> G(count);
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (lower_gate(n, gates[i], &G[i]) != QS_OK) return -1;
+        G[i].paeth = (flags & 1) && gates[i].kind == QS_GATE_RY;
+    }
     ++g_calls;
     return (int)run_tiled(&s, G, nullptr, 0);
 }
@@ -417,10 +427,11 @@ int emu_sweep(int n, int dtype, const qs_gate *gates, int count, double *buf, do
     return 0;
 }
 
-// Adiabatic evolution as the library's tiled Trotter path plans it: per step
-// k (s_k = (k + 1/2) dt / T) an Ising phase with the merged half steps, then
-// RX(2 dt a_q(s_k)) on every qubit, a_q(s) = (1 - s) a0[q] + s a1[q]; the
-// Ising table (index bits: J[a n + b], h[n], constant) is shared by the state.
+// Adiabatic evolution through the library's tiled Trotter queue (trotter_queue:
+// per step k, s_k = (k + 1/2) dt / T, an Ising phase with the merged half steps,
+// then RX(2 dt a_q(s_k)) on every qubit, a_q(s) = (1 - s) a0[q] + s a1[q],
+// written as RY layers in the frame of S on every qubit); the Ising table
+// (index bits: J[a n + b], h[n], constant) is shared by the state.
 int emu_trotter(int n, int dtype, const double *a0, const double *a1, const double *table, double T, double dt,
                 int steps, double *psi) {
     std::vector<double> svals, taus;
@@ -429,32 +440,9 @@ int emu_trotter(int n, int dtype, const double *a0, const double *a1, const doub
     for (int k = 0; k + 1 < steps; ++k) taus.push_back(0.5 * dt * (svals[k] + svals[k + 1]));
     taus.push_back(0.5 * dt * svals[steps - 1]);
     std::vector<LGate> G;
-    auto ising = [&](double tau) {
-        LGate g;
-        g.kind = kKindIsing;
-        g.k = 0;
-        g.diagonal = true;
-        g.m.assign(1, cdd(tau, 0.0));
-        G.push_back(g);
-    };
-    for (int k = 0; k < steps; ++k) {
-        ising(taus[k]);
-        for (int q = 0; q < n; ++q) {
-            const double a = (1.0 - svals[k]) * a0[q] + svals[k] * a1[q];
-            if (a == 0.0) continue;
-            qs_gate g;
-            std::memset(&g, 0, sizeof(g));
-            g.kind = QS_GATE_RX;
-            g.n_targets = 1;
-            g.targets[0] = q;
-            g.param_index = -1;
-            g.params[0] = 2.0 * dt * a;
-            LGate lg;
-            if (lower_gate(n, g, &lg) != QS_OK) return -1;
-            G.push_back(lg);
-        }
-    }
-    ising(taus[steps]);
+    if (trotter_queue(n, std::vector<double>(a0, a0 + n), std::vector<double>(a1, a1 + n), taus, svals, dt, true,
+                      &G) != QS_OK)
+        return -1;
     qs_state s;
     s.n = n;
     s.ms = n;
