@@ -184,63 +184,54 @@ template <typename R> __device__ __forceinline__ V<R> conjc(V<R> v) { return mkc
 
 // psi_x *= exp(-i tau E(x)) for an Ising energy E(x) = c + sum_i h_i z_i +
 // sum_{i<j} J_ij z_i z_j, z_i = 1 - 2 x_i. Split over the tile: the outside bits
-// give per-tile fields s_g on the tile bits and a per-tile constant; the
-// thread's lane/warp bits add their mutual coupling energy and their fields on
-// the register bits, which depend on the member only and come from the op's
-// table (filled once per pass by ising_table_kernel), like the register-pair
-// phases. Then E = C + sum_j w_j - 2 sum_{j: r_j = 1} w_j + Q[r] per register,
-// a product of per-thread factors walked over the registers in Gray-code
-// order; angles are evaluated in FP64.
+// give fields s_g on the tile bits and an energy of their own (per tile); the
+// thread's lane/warp bits add their mutual coupling and their fields on the
+// register bits (per thread pattern); the register bits couple among
+// themselves (per register index). With w_j the whole field on register bit j,
+// E = C + sum_j w_j - 2 sum_{j: r_j = 1} w_j + Q[r], so the phase is a base
+// times a factor u_j per set register bit times q[r]. The op's table (filled
+// once per pass by ising_table_kernel) holds every part as a unit complex
+// number; here they are only multiplied, with no angle or energy in the loop.
 template <typename R, int RB>
 __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, const TileOp &op, const TileStage &st,
-                                            uint64_t tbase, uint64_t member, int lane, int warp, double *s_g,
-                                            double *s_eo, V<R> *s_qp) {
+                                            uint64_t tile, uint64_t member, int lane, int warp, V<R> *s_e,
+                                            V<R> *s_qp) {
     constexpr int NR = 1 << RB;
-    const double tau = __longlong_as_double((long long)op.tmask);
-    const int nq = p.nq;
-    const double *J = p.ising + member * p.ising_stride;
-    const double *hv = J + (size_t)nq * nq;
-    const double *tab = p.ising_thr + ((size_t)op.m * (p.total_tiles >> p.n_free) + member) * p.ising_thr_stride;
+    constexpr int WB = TileCfg<R>::WB;
+    constexpr int T = 32 << WB;
+    const double2 *tab = reinterpret_cast<const double2 *>(
+        p.ising_thr + ((size_t)op.m * (p.total_tiles >> p.n_free) + member) * p.ising_thr_stride);
+    const double2 *qp = tab + (size_t)T * (1 + RB);
+    const double2 *tile_row = qp + NR + (size_t)(tile & ((1ull << p.n_free) - 1ull)) * (p.k + 1);
     const int tid = threadIdx.x;
-    if (tid < p.k) {
-        const int g = p.gbit[tid];
-        double acc = hv[g];
-        for (int o = 0; o < nq; ++o)
-            if (!((p.tile_mask >> o) & 1ull)) acc += ((tbase >> o) & 1ull) ? -J[g * nq + o] : J[g * nq + o];
-        s_g[tid] = acc;
-    } else if (tid >= 32 && tid < 64) {
-        double acc = 0.0;
-        for (int o = tid - 32; o < nq; o += 32) {
-            if ((p.tile_mask >> o) & 1ull) continue;
-            double row = hv[o];
-            for (int o2 = o + 1; o2 < nq; ++o2)
-                if (!((p.tile_mask >> o2) & 1ull)) row += ((tbase >> o2) & 1ull) ? -J[o * nq + o2] : J[o * nq + o2];
-            acc += ((tbase >> o) & 1ull) ? -row : row;
-        }
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-        if (tid == 32) *s_eo = acc + hv[nq];
-    } else if (tid >= 64 && tid < 64 + NR) {
-        const int r = tid - 64;
-        const double *qp = tab + (size_t)(32 << TileCfg<R>::WB) * (1 + RB);
-        s_qp[r] = mkc<R>((R)qp[2 * r], (R)qp[2 * r + 1]);
+    if (tid <= p.k) {
+        const double2 v = tile_row[tid];
+        s_e[tid] = mkc<R>((R)v.x, (R)v.y);
+    } else if (tid >= 32 && tid < 32 + NR) {
+        const double2 v = qp[tid - 32];
+        s_qp[tid - 32] = mkc<R>((R)v.x, (R)v.y);
     }
     __syncthreads();
-    constexpr int WB = TileCfg<R>::WB;
-    const double *row = tab + (size_t)tid * (1 + RB);
-    double C = *s_eo + row[0];
+    const double2 *row = tab + (size_t)tid * (1 + RB);
+    V<R> base = cmul<R>(s_e[p.k], mkc<R>((R)row[0].x, (R)row[0].y));
 #pragma unroll
-    for (int i = 0; i < 5; ++i) C += ((lane >> i) & 1) ? -s_g[st.lloc[i]] : s_g[st.lloc[i]];
+    for (int i = 0; i < kTileLaneBits; ++i) {
+        const V<R> e = s_e[st.lloc[i]];
+        base = cmul<R>(base, ((lane >> i) & 1) ? conjc<R>(e) : e);
+    }
 #pragma unroll
-    for (int w = 0; w < WB; ++w) C += ((warp >> w) & 1) ? -s_g[st.wloc[w]] : s_g[st.wloc[w]];
-    double wsum = 0.0;
+    for (int w = 0; w < WB; ++w) {
+        const V<R> e = s_e[st.wloc[w]];
+        base = cmul<R>(base, ((warp >> w) & 1) ? conjc<R>(e) : e);
+    }
     V<R> u[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) {
-        const double wj = s_g[st.rloc[j]] + row[1 + j];
-        wsum += wj;
-        u[j] = expi<R>(2.0 * tau * wj);
+        const V<R> e = s_e[st.rloc[j]];
+        base = cmul<R>(base, e);
+        const V<R> ec = conjc<R>(e);
+        u[j] = cmul<R>(cmul<R>(ec, ec), mkc<R>((R)row[1 + j].x, (R)row[1 + j].y));
     }
-    const V<R> base = expi<R>(-tau * (C + wsum));
 #pragma unroll
     for (int hb = 0; hb < NR / 8; ++hb) {
         V<R> q = base;
@@ -262,45 +253,82 @@ __device__ __forceinline__ void ising_phase(V<R> *a, const TileParams<R> &p, con
     __syncthreads();
 }
 
-// The Ising op's tile-independent parts, one CTA per member, one thread per
-// thread pattern (lane bits, then warp bits): the coupling energy among the
-// pattern's bits and their field on every register bit (FP64); threads below
-// 2^rb also the (cos, sin) of -tau times the register-pair energy.
+// The Ising op's tables (see ising_thr_stride), per member (blockIdx.y), in
+// FP64: block 0, one thread per thread pattern (lane bits, then warp bits), the
+// pattern's coupling energy and fields, and the register-pair energies; blocks
+// 1.., one thread per tile, the fields of the outside bits on the tile bits and
+// the outside energy. Every energy x is stored as exp(-i tau x).
 __global__ void __launch_bounds__(256) ising_table_kernel(const __grid_constant__ IsingTabP tp) {
-    const int member = blockIdx.x, tid = threadIdx.x;
+    const int member = blockIdx.y, tid = threadIdx.x;
     const int nq = tp.nq;
     const double *J = tp.ising + (size_t)member * tp.ising_stride;
-    double *base = tp.out + (size_t)member * tp.stride;
-    double z[kTileLaneBits + kTileMaxWarpBits];
-    for (int i = 0; i < tp.tb; ++i) z[i] = ((tid >> i) & 1) ? -1.0 : 1.0;
-    double e = 0.0;
-    for (int i = 0; i < tp.tb; ++i)
-        for (int j = i + 1; j < tp.tb; ++j) e += J[tp.tg[i] * nq + tp.tg[j]] * z[i] * z[j];
-    double *row = base + (size_t)tid * (1 + tp.rb);
-    row[0] = e;
-    for (int j = 0; j < tp.rb; ++j) {
-        double w = 0.0;
-        for (int i = 0; i < tp.tb; ++i) w += J[tp.rg[j] * nq + tp.tg[i]] * z[i];
-        row[1 + j] = w;
+    const double *hv = J + (size_t)nq * nq;
+    double2 *base = reinterpret_cast<double2 *>(tp.out + (size_t)member * tp.stride);
+    auto put = [&](double2 *dst, double x) {
+        if (tp.single) {
+            const V<float> v = expi<float>(-tp.tau * x);
+            *dst = make_double2(v.x, v.y);
+        } else {
+            const V<double> v = expi<double>(-tp.tau * x);
+            *dst = make_double2(v.x, v.y);
+        }
+    };
+    if (blockIdx.x == 0) {
+        double z[kTileLaneBits + kTileMaxWarpBits];
+        for (int i = 0; i < tp.tb; ++i) z[i] = ((tid >> i) & 1) ? -1.0 : 1.0;
+        double e = 0.0;
+        for (int i = 0; i < tp.tb; ++i)
+            for (int j = i + 1; j < tp.tb; ++j) e += J[tp.tg[i] * nq + tp.tg[j]] * z[i] * z[j];
+        double2 *row = base + (size_t)tid * (1 + tp.rb);
+        double wsum = 0.0;
+        for (int j = 0; j < tp.rb; ++j) {
+            double w = 0.0;
+            for (int i = 0; i < tp.tb; ++i) w += J[tp.rg[j] * nq + tp.tg[i]] * z[i];
+            wsum += w;
+            put(&row[1 + j], -2.0 * w);
+        }
+        put(&row[0], e + wsum);
+        if (tid < (1 << tp.rb)) {
+            double q = 0.0;
+            for (int i = 0; i < tp.rb; ++i)
+                for (int j = i + 1; j < tp.rb; ++j) {
+                    const double c = J[tp.rg[i] * nq + tp.rg[j]];
+                    q += (((tid >> i) ^ (tid >> j)) & 1) ? -c : c;
+                }
+            put(base + (size_t)blockDim.x * (1 + tp.rb) + tid, q);
+        }
+        return;
     }
-    if (tid < (1 << tp.rb)) {
-        double q = 0.0;
-        for (int i = 0; i < tp.rb; ++i)
-            for (int j = i + 1; j < tp.rb; ++j) {
-                const double c = J[tp.rg[i] * nq + tp.rg[j]];
-                q += (((tid >> i) ^ (tid >> j)) & 1) ? -c : c;
-            }
-        const V<double> v = expi<double>(-tp.tau * q);
-        double *qp = base + (size_t)blockDim.x * (1 + tp.rb);
-        qp[2 * tid] = v.x;
-        qp[2 * tid + 1] = v.y;
+    const uint64_t t = (uint64_t)(blockIdx.x - 1) * blockDim.x + tid;
+    if (t >= (1ull << tp.n_free)) return;
+    const uint64_t tbase = expand_bits(t, tp.tins);  // the tile's outside bits
+    uint64_t tmask = 0;
+    for (int i = 0; i < tp.k; ++i) tmask |= 1ull << tp.gb[i];
+    double2 *row = base + (size_t)blockDim.x * (1 + tp.rb) + (1 << tp.rb) + t * (tp.k + 1);
+    for (int i = 0; i < tp.k; ++i) {
+        const int g = tp.gb[i];
+        double acc = hv[g];
+        for (int o = 0; o < nq; ++o)
+            if (!((tmask >> o) & 1ull)) acc += ((tbase >> o) & 1ull) ? -J[g * nq + o] : J[g * nq + o];
+        put(&row[i], acc);
     }
+    double eo = hv[nq];
+    for (int o = 0; o < nq; ++o) {
+        if ((tmask >> o) & 1ull) continue;
+        const double zo = ((tbase >> o) & 1ull) ? -1.0 : 1.0;
+        double r = hv[o];
+        for (int o2 = o + 1; o2 < nq; ++o2)
+            if (!((tmask >> o2) & 1ull)) r += ((tbase >> o2) & 1ull) ? -J[o * nq + o2] : J[o * nq + o2];
+        eo += zo * r;
+    }
+    put(&row[tp.k], eo);
 }
 
 qs_status k_ising_table(qs_state *s, const IsingTabP &tp) {
     if (tp.members <= 0) return QS_OK;
     ProfScope _ps(s->stream, KC_TROTTER_DIAG);
-    ising_table_kernel<<<tp.members, 256, 0, s->stream>>>(tp);
+    const dim3 grid(1 + (unsigned)(((1ull << tp.n_free) + 255) / 256), (unsigned)tp.members);
+    ising_table_kernel<<<grid, 256, 0, s->stream>>>(tp);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }
@@ -559,8 +587,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
     uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw + (sizeof(V<R>) << p.k));
     uint16_t *ltab = reinterpret_cast<uint16_t *>(tab + p.n_stages * (NW * 32));
     __shared__ R gsm[kTileMaxGrad][NW];
-    __shared__ double s_g[16];
-    __shared__ double s_eo;
+    __shared__ V<R> s_e[16];
     __shared__ V<R> s_qp[NR];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -687,8 +714,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
                         if (req_ok()) dispatch_swap<R, RB>(a, op.a, op.b, op.mr);
                     break;
                 case TOP_ISING:
-                    if constexpr (FULL)
-                        ising_phase<R, RB>(a, p, op, st, tbase, t >> p.n_free, lane, warp, s_g, &s_eo, s_qp);
+                    if constexpr (FULL) ising_phase<R, RB>(a, p, op, st, t, t >> p.n_free, lane, warp, s_e, s_qp);
                     break;
                 case TOP_ROTS_R: {
                     // rotations on distinct register bits (they commute): bit j of

@@ -1175,7 +1175,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     if (nising > 0) {
         // the Ising ops' tile-independent tables, once per pass
         const int threads = tile_threads(s->dtype);
-        const uint32_t stride = ising_thr_stride(RB, threads);
+        const uint32_t stride = ising_thr_stride(RB, threads, k, P.n_free);
         const size_t doubles = (size_t)nising * s->batch * stride;
         if (s->ithr_bytes < doubles * sizeof(double)) {
             if (s->ithr) {
@@ -1200,12 +1200,17 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
                 for (int i = 0; i < kTileLaneBits; ++i) tp.tg[i] = (int8_t)P.gbit[P.st[st].lloc[i]];
                 for (int w = 0; w < TileCfg<R>::WB; ++w) tp.tg[kTileLaneBits + w] = (int8_t)P.gbit[P.st[st].wloc[w]];
                 for (int j = 0; j < RB; ++j) tp.rg[j] = (int8_t)P.gbit[P.st[st].rloc[j]];
+                tp.k = k;
+                tp.n_free = P.n_free;
+                for (int i = 0; i < k; ++i) tp.gb[i] = (int8_t)P.gbit[i];
+                tp.tins = P.tins;
                 std::memcpy(&tp.tau, &op.tmask, sizeof(double));
                 tp.ising = s->itab;
                 tp.ising_stride = s->ising_stride;
                 tp.nq = n;
                 tp.stride = stride;
                 tp.members = s->batch;
+                tp.single = sizeof(R) == 4 ? 1 : 0;
                 tp.out = s->ithr + (size_t)op.m * s->batch * stride;
                 QS_TRY(k_ising_table(s, tp));
             }

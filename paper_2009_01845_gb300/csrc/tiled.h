@@ -174,11 +174,9 @@ template <typename R> struct TileParams {
     const double *ising;
     uint32_t ising_stride;
     int nq;
-    // per Ising op (index in op.m) and member: the tile-independent parts,
-    // ising_thr_stride doubles per member: for each thread (256) the coupling
-    // energy among its lane/warp bits and, per register bit j, the field those
-    // bits put on j; then (cos, sin) of -tau times the register-pair energy of
-    // each register index
+    // per Ising op (index in op.m) and member, ising_thr_stride doubles (see
+    // ising_thr_stride): the op's phase factors as complex pairs, per thread
+    // pattern, per register index and per tile
     const double *ising_thr;
     uint32_t ising_thr_stride;
     uint64_t tile_mask;   // global bits of the tile
@@ -191,12 +189,15 @@ template <typename R> struct TileParams {
 static_assert(sizeof(TileParams<double>) <= 32700, "kernel parameter block too large");
 
 // Inputs of the Ising-table kernel for one op: global bits of the stage's
-// thread bits (lanes 0..4, then warps) and register bits, tau, and where the
-// op's tables start.
+// thread bits (lanes 0..4, then warps) and register bits, the pass's tile bits
+// (k of them, global positions gb, inserted into a tile number by tins), tau,
+// and where the op's tables start.
 struct IsingTabP {
     int8_t tg[kTileLaneBits + kTileMaxWarpBits];
     int8_t rg[6];
-    int tb, rb;
+    int8_t gb[16];
+    int tb, rb, k, n_free;
+    InsertBits tins;
     double tau;
     const double *ising;
     uint32_t ising_stride;
@@ -204,8 +205,18 @@ struct IsingTabP {
     double *out;
     uint32_t stride;   // doubles per member
     int members;
+    int single;        // the state is complex64: sin and cos in FP32 (of the FP64-reduced angle)
 };
 
-inline uint32_t ising_thr_stride(int rb, int threads) { return (uint32_t)(threads * (1 + rb) + 2 * (1 << rb)); }
+// The Ising op's tables, per member, as (cos, sin) pairs of exp(-i tau x):
+// for each thread pattern (threads of them) x = the coupling energy among its
+// lane/warp bits plus the fields those bits put on the register bits, then
+// for each register bit j, x = -2 times that field on j; for each register
+// index x = its register-pair energy; for each tile (2^n_free) and each of the
+// k tile bits, x = the field the outside bits and h put on it, then x = the
+// tile's outside energy (couplings among outside bits, their h, the constant).
+inline uint32_t ising_thr_stride(int rb, int threads, int k, int n_free) {
+    return (uint32_t)(2 * threads * (1 + rb) + 2 * (1 << rb) + ((uint64_t)2 * (k + 1) << n_free));
+}
 
 }  // namespace qsim
