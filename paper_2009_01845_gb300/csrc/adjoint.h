@@ -24,6 +24,10 @@ template <typename R> struct PauliApplyP {
     uint64_t zb[kPAMaxTerms];
     uint64_t gx[kPAMaxGroups];
     int gbeg[kPAMaxGroups + 1];
+    // groups whose terms have no Z bits: their coefficient sum, a constant
+    R gcre[kPAMaxGroups];
+    R gcim[kPAMaxGroups];
+    uint8_t gconst[kPAMaxGroups];
     int ng;
     int n;
     int ms;

@@ -23,25 +23,36 @@ static unsigned grid_cap(uint64_t work, int threads) {
 
 // ------------------------------------------------------------------ lambda = H phi
 // (P phi)[y] = i^{#Y} (-1)^{popcount((y ^ m) & z)} phi[y ^ m] for a term (c, m, z).
-template <typename R>
+// U: the index type within a member (32-bit while n <= 32); groups of terms
+// without Z bits (pure X) add a constant coefficient.
+template <typename R, typename U>
 __global__ void __launch_bounds__(256) pauli_apply_kernel(const V<R> *__restrict__ src, V<R> *__restrict__ dst,
                                                           const __grid_constant__ PauliApplyP<R> p) {
     const uint64_t mask = (1ull << p.n) - 1ull;
     for (uint64_t i = global_tid(); i < p.total; i += global_stride()) {
-        const uint64_t y = i & mask;
-        const uint64_t mb = (i >> p.n) << p.ms;
-        V<R> acc = p.accumulate ? dst[mb | y] : mkc<R>(0, 0);
+        const U y = (U)(i & mask);
+        const V<R> *sm = src + ((i >> p.n) << p.ms);
+        V<R> *dm = dst + ((i >> p.n) << p.ms);
+        V<R> acc = p.accumulate ? dm[y] : mkc<R>(0, 0);
         for (int g = 0; g < p.ng; ++g) {
-            const uint64_t x = y ^ p.gx[g];
-            R fr = 0, fi = 0;
-            for (int t = p.gbeg[g]; t < p.gbeg[g + 1]; ++t) {
-                const bool odd = __popcll(x & p.zb[t]) & 1;
-                fr += odd ? -p.cre[t] : p.cre[t];
-                fi += odd ? -p.cim[t] : p.cim[t];
+            const U x = y ^ (U)p.gx[g];
+            R fr, fi;
+            if (p.gconst[g]) {
+                fr = p.gcre[g];
+                fi = p.gcim[g];
+            } else {
+                fr = 0;
+                fi = 0;
+                for (int t = p.gbeg[g]; t < p.gbeg[g + 1]; ++t) {
+                    const bool odd = (sizeof(U) == 4 ? __popc((uint32_t)(x & (U)p.zb[t]))
+                                                     : __popcll((uint64_t)(x & (U)p.zb[t]))) & 1;
+                    fr += odd ? -p.cre[t] : p.cre[t];
+                    fi += odd ? -p.cim[t] : p.cim[t];
+                }
             }
-            acc = cmadd<R>(mkc<R>(fr, fi), src[mb | x], acc);
+            acc = cmadd<R>(mkc<R>(fr, fi), sm[x], acc);
         }
-        dst[mb | y] = acc;
+        dm[y] = acc;
     }
 }
 
@@ -76,6 +87,8 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
                nt + (int)groups[gi].size() <= kPAMaxTerms) {
             p.gx[p.ng] = masks[gi];
             p.gbeg[p.ng] = nt;
+            p.gconst[p.ng] = 1;
+            double sre = 0.0, sim = 0.0;
             for (size_t t : groups[gi]) {
                 const qs_pauli_term &tm = terms[t];
                 const int ny = __builtin_popcountll(tm.x_mask & tm.z_mask) & 3;
@@ -87,8 +100,13 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
                 for (int q = 0; q < n; ++q)
                     if ((tm.z_mask >> q) & 1ull) zb |= 1ull << (n - 1 - q);
                 p.zb[nt] = zb;
+                if (zb != 0) p.gconst[p.ng] = 0;
+                sre += re[ny];
+                sim += im[ny];
                 ++nt;
             }
+            p.gcre[p.ng] = (R)sre;
+            p.gcim[p.ng] = (R)sim;
             ++p.ng;
             ++gi;
         }
@@ -102,7 +120,12 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
         p.total = total;
         p.accumulate = first ? 0 : 1;
         first = false;
-        pauli_apply_kernel<R><<<grid_cap(total, 256), 256, 0, st>>>((const V<R> *)src.data, (V<R> *)dst.data, p);
+        if (n <= 32)
+            pauli_apply_kernel<R, uint32_t>
+                <<<grid_cap(total, 256), 256, 0, st>>>((const V<R> *)src.data, (V<R> *)dst.data, p);
+        else
+            pauli_apply_kernel<R, uint64_t>
+                <<<grid_cap(total, 256), 256, 0, st>>>((const V<R> *)src.data, (V<R> *)dst.data, p);
         QS_CUDA_TRY(cudaGetLastError());
     }
     return QS_OK;
