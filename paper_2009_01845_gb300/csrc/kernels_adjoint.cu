@@ -56,6 +56,61 @@ __global__ void __launch_bounds__(256) pauli_apply_kernel(const V<R> *__restrict
     }
 }
 
+// The same over tiles of 2^kPATileBits consecutive amplitudes of a member held
+// in shared memory: partners y ^ m whose mask m stays inside the tile's bits
+// come from shared memory, the others from global memory (for a transverse
+// field on n qubits, n - kPATileBits of the n X groups), so DRAM and L2 see
+// far fewer partner reads. Loads and stores are coalesced (thread tid takes
+// offsets tid + 256 j).
+template <typename R> struct PATile { static constexpr int kBits = sizeof(R) == 4 ? 12 : 11; };
+
+template <typename R>
+__global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__restrict__ src, V<R> *__restrict__ dst,
+                                                               const __grid_constant__ PauliApplyP<R> p) {
+    constexpr int K = PATile<R>::kBits;
+    constexpr int PER = (1 << K) / 256;
+    __shared__ V<R> tile[1 << K];
+    const uint32_t lowm = (1u << K) - 1u;
+    const uint64_t tiles = p.total >> K;
+    const int tshift = p.n - K;  // tiles per member: 2^tshift
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint64_t moff = (t >> tshift) << p.ms;
+        const uint32_t yb = (uint32_t)((t & ((1ull << tshift) - 1ull)) << K);
+        const V<R> *sm = src + moff;
+        V<R> *dm = dst + moff;
+        __syncthreads();  // the previous tile's readers are done
+#pragma unroll
+        for (int j = 0; j < PER; ++j) tile[threadIdx.x + 256 * j] = sm[yb + threadIdx.x + 256 * j];
+        __syncthreads();
+#pragma unroll 2
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t yl = threadIdx.x + 256 * j;
+            const uint32_t y = yb | yl;
+            V<R> acc = p.accumulate ? dm[y] : mkc<R>(0, 0);
+            for (int g = 0; g < p.ng; ++g) {
+                const uint32_t m = (uint32_t)p.gx[g];
+                const uint32_t x = y ^ m;
+                R fr, fi;
+                if (p.gconst[g]) {
+                    fr = p.gcre[g];
+                    fi = p.gcim[g];
+                } else {
+                    fr = 0;
+                    fi = 0;
+                    for (int tt = p.gbeg[g]; tt < p.gbeg[g + 1]; ++tt) {
+                        const bool odd = __popc(x & (uint32_t)p.zb[tt]) & 1;
+                        fr += odd ? -p.cre[tt] : p.cre[tt];
+                        fi += odd ? -p.cim[tt] : p.cim[tt];
+                    }
+                }
+                const V<R> v = (m & ~lowm) == 0 ? tile[yl ^ m] : sm[x];
+                acc = cmadd<R>(mkc<R>(fr, fi), v, acc);
+            }
+            dm[y] = acc;
+        }
+    }
+}
+
 template <typename R>
 static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const qs_pauli_term *terms, size_t count,
                                cudaStream_t st) {
@@ -120,7 +175,10 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
         p.total = total;
         p.accumulate = first ? 0 : 1;
         first = false;
-        if (n <= 32)
+        if (n >= PATile<R>::kBits && n <= 32)
+            pauli_apply_tile_kernel<R>
+                <<<grid_cap(total >> PATile<R>::kBits, 1), 256, 0, st>>>((const V<R> *)src.data, (V<R> *)dst.data, p);
+        else if (n <= 32)
             pauli_apply_kernel<R, uint32_t>
                 <<<grid_cap(total, 256), 256, 0, st>>>((const V<R> *)src.data, (V<R> *)dst.data, p);
         else
