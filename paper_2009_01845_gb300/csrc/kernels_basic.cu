@@ -497,6 +497,12 @@ template <typename R> struct ExpP {
     // one- and two-bit terms: bits 0-7 first Z bit a, 8-15 second bit b (= a
     // for one bit), bit 16: two bits; parity = ((x >> a) ^ ((x >> b) & two)) & 1
     uint32_t zw[kMaxTermsPerLaunch];
+    // diagonal group (xb = 0), chunked: the varying terms sorted by cm, the
+    // chunk bits their Z bits include (bit i = index bit kExpChunkLo + i);
+    // vord[vmb[m] .. vmb[m+1]) are the ones with cm = m
+    uint8_t cm[kMaxTermsPerLaunch];
+    uint8_t vord[kMaxTermsPerLaunch];
+    int vmb[17];
     int nt;
     int nv;           // terms [0, nv) touch the chunk bits (see expect_partial_kernel)
     int nvf, nff;     // [0, nvf) and [nv, nff): one- and two-bit terms; the rest general
@@ -554,6 +560,17 @@ template <typename R> static void exp_order_terms(ExpP<R> *p) {
         if (pass == 0) q.nvf = k;
         if (pass == 1) q.nv = k;
         if (pass == 2) q.nff = k;
+    }
+    if (q.xb == 0) {
+        for (int t = 0; t < q.nv; ++t)
+            q.cm[t] = (uint8_t)((q.zb[t] >> kExpChunkLo) & ((1u << kExpChunkBits) - 1u));
+        int k2 = 0;
+        for (int m = 0; m < (1 << kExpChunkBits); ++m) {
+            q.vmb[m] = k2;
+            for (int t = 0; t < q.nv; ++t)
+                if (q.cm[t] == m) q.vord[k2++] = (uint8_t)t;
+        }
+        q.vmb[1 << kExpChunkBits] = k2;
     }
     *p = q;
 }
@@ -625,13 +642,32 @@ __device__ __forceinline__ double2 expect_body(const V<R> *__restrict__ q, const
                 V<R> av[1 << kExpChunkBits];
 #pragma unroll
                 for (int c = 0; c < (1 << kExpChunkBits); ++c) av[c] = q[j0 | ((U)c << kExpChunkLo)];
+                // varying terms: sign from the bits outside the chunk (x with chunk
+                // bits 0), summed per chunk-bit mask m into F[m]; then
+                // f(c) = f0 + sum_m F[m] (-1)^{popcount(c & m)}, the Walsh-Hadamard
+                // transform of F (no per-amplitude term evaluation)
+                R F[1 << kExpChunkBits];
 #pragma unroll
-                for (int c = 0; c < (1 << kExpChunkBits); ++c) {
-                    const U x = j0 | ((U)c << kExpChunkLo);
-                    R fr = f0r, fi = 0, gr = 0, gi = 0;
-                    exp_range<R, U>(p, true, x, fr, fi, gr, gi);
-                    rr = fma(fr, fma(av[c].x, av[c].x, av[c].y * av[c].y), rr);
+                for (int m = 0; m < (1 << kExpChunkBits); ++m) {
+                    R acc = 0;
+                    for (int k = p.vmb[m]; k < p.vmb[m + 1]; ++k) {
+                        const int t = p.vord[k];
+                        acc += term_odd(p, t, (uint64_t)j0) ? -p.cre[t] : p.cre[t];
+                    }
+                    F[m] = acc;
                 }
+#pragma unroll
+                for (int h = 1; h < (1 << kExpChunkBits); h <<= 1)
+#pragma unroll
+                    for (int i = 0; i < (1 << kExpChunkBits); ++i)
+                        if (!(i & h)) {
+                            const R u = F[i], v = F[i | h];
+                            F[i] = u + v;
+                            F[i | h] = u - v;
+                        }
+#pragma unroll
+                for (int c = 0; c < (1 << kExpChunkBits); ++c)
+                    rr = fma(f0r + F[c], fma(av[c].x, av[c].x, av[c].y * av[c].y), rr);
             } else {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -683,7 +719,7 @@ __device__ __forceinline__ double2 expect_body(const V<R> *__restrict__ q, const
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads) expect_partial_kernel(const V<R> *__restrict__ psi,
+__global__ void __launch_bounds__(kRedThreads, 2) expect_partial_kernel(const V<R> *__restrict__ psi,
                                                                      const __grid_constant__ ExpP<R> p,
                                                                      double2 *__restrict__ part) {
     const V<R> *q = psi + ((uint64_t)blockIdx.y << p.ms);
@@ -769,6 +805,9 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, d
                 std::memcpy(&pf.zn, &p.zn, sizeof(p.zn));
                 std::memcpy(&pf.ys, &p.ys, sizeof(p.ys));
                 std::memcpy(&pf.zw, &p.zw, sizeof(p.zw));
+                std::memcpy(&pf.cm, &p.cm, sizeof(p.cm));
+                std::memcpy(&pf.vord, &p.vord, sizeof(p.vord));
+                std::memcpy(&pf.vmb, &p.vmb, sizeof(p.vmb));
                 pf.nv = p.nv;
                 pf.nvf = p.nvf;
                 pf.nff = p.nff;
