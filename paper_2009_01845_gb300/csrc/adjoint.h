@@ -28,6 +28,13 @@ template <typename R> struct PauliApplyP {
     R gcre[kPAMaxGroups];
     R gcim[kPAMaxGroups];
     uint8_t gconst[kPAMaxGroups];
+    // the group of Z-only terms (X mask 0), or -1; for the shared-memory tile
+    // kernel its terms sorted by the bits 8 .. 8 + log2(tile / 256) - 1 their Z
+    // masks include (the bits that tell a thread's outputs apart): dord[dmb[m]
+    // .. dmb[m+1]) are the ones with mask m
+    int gdiag;
+    uint16_t dord[kPAMaxTerms];
+    int dmb[17];
     int ng;
     int n;
     int ms;

@@ -82,7 +82,36 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
 #pragma unroll
         for (int j = 0; j < PER; ++j) tile[threadIdx.x + 256 * j] = sm[yb + threadIdx.x + 256 * j];
         __syncthreads();
-#pragma unroll 2
+        // Z-only group: coefficient of output j = f(j), from the terms' signs on
+        // the other bits summed per mask of bits 8.. and a Walsh-Hadamard
+        // transform over the PER outputs of this thread
+        R Dr[PER], Di[PER];
+        if (p.gdiag >= 0) {
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                R ar = 0, ai = 0;
+                for (int k = p.dmb[m]; k < p.dmb[m + 1]; ++k) {
+                    const int tt = p.dord[k];
+                    const bool odd = __popc((yb | threadIdx.x) & (uint32_t)p.zb[tt]) & 1;
+                    ar += odd ? -p.cre[tt] : p.cre[tt];
+                    ai += odd ? -p.cim[tt] : p.cim[tt];
+                }
+                Dr[m] = ar;
+                Di[m] = ai;
+            }
+#pragma unroll
+            for (int h = 1; h < PER; h <<= 1)
+#pragma unroll
+                for (int i = 0; i < PER; ++i)
+                    if (!(i & h)) {
+                        const R ur = Dr[i], vr = Dr[i | h], ui = Di[i], vi = Di[i | h];
+                        Dr[i] = ur + vr;
+                        Dr[i | h] = ur - vr;
+                        Di[i] = ui + vi;
+                        Di[i | h] = ui - vi;
+                    }
+        }
+#pragma unroll
         for (int j = 0; j < PER; ++j) {
             const uint32_t yl = threadIdx.x + 256 * j;
             const uint32_t y = yb | yl;
@@ -91,7 +120,10 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
                 const uint32_t m = (uint32_t)p.gx[g];
                 const uint32_t x = y ^ m;
                 R fr, fi;
-                if (p.gconst[g]) {
+                if (g == p.gdiag) {
+                    fr = Dr[j];
+                    fi = Di[j];
+                } else if (p.gconst[g]) {
                     fr = p.gcre[g];
                     fi = p.gcim[g];
                 } else {
@@ -170,6 +202,19 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
             return QS_ERR_UNSUPPORTED;
         }
         p.gbeg[p.ng] = nt;
+        p.gdiag = -1;
+        for (int g = 0; g < p.ng; ++g)
+            if (p.gx[g] == 0 && !p.gconst[g]) p.gdiag = g;
+        if (p.gdiag >= 0) {
+            constexpr int cb = PATile<R>::kBits - 8;  // log2 of outputs per thread
+            int k2 = 0;
+            for (int m = 0; m < (1 << cb); ++m) {
+                p.dmb[m] = k2;
+                for (int t = p.gbeg[p.gdiag]; t < p.gbeg[p.gdiag + 1]; ++t)
+                    if ((int)((p.zb[t] >> 8) & ((1u << cb) - 1u)) == m) p.dord[k2++] = (uint16_t)t;
+            }
+            p.dmb[1 << cb] = k2;
+        }
         p.n = n;
         p.ms = src.ms;
         p.total = total;
