@@ -87,9 +87,9 @@ struct PassPlan {
 }  // namespace
 
 // ------------------------------------------------------------------ entries
-// A pass is emitted from a list of entries: original gates, scaled rotations
-// (the real rotation of an uncontrolled one-qubit gate, see split_1q), and
-// diagonal blocks (products of one-bit diagonals and phase factors).
+// A pass is emitted from a list of entries: original gates, rotations (the
+// real rotation of an uncontrolled one-qubit gate, see split_1q and rot_plan),
+// and diagonal blocks (products of one-bit diagonals and phase factors).
 namespace {
 
 enum EKind { E_GATE, E_ROT, E_BLOCK };
@@ -184,7 +184,7 @@ uint64_t factor_bits(const Factor &f) { return f.type == DF_BIT ? (1ull << f.bit
 }  // namespace
 
 // Split the gates of a pass into entries. With `algebra`, uncontrolled
-// one-qubit gates become D_R, a scaled rotation and D_L; those diagonals,
+// one-qubit gates become D_R, a real rotation and D_L; those diagonals,
 // uncontrolled one-bit diagonal gates and phase gates become factors. Returns
 // the other entries in queue order and, in *facs, every factor with the range
 // of positions it may be applied at: a cut at position p means "just before
@@ -259,9 +259,10 @@ static std::vector<Entry> build_entries(const std::vector<LGate> &G, const std::
         // a gradient op <lambda|P|phi> is unchanged by a unitary diagonal
         // applied to both phi and lambda when the diagonal commutes with P: Z
         // and projector generators commute with every diagonal, X and Y with
-        // the diagonals that do not involve their target. (A scaled factor,
-        // the D_L of a factored gate, never crosses a gradient op: the
-        // readout is bilinear in the state.)
+        // the diagonals that do not involve their target. (The D_L of a
+        // factored gate, which carries the real diagonal of its rotation's
+        // shears, never crosses a gradient op: the readout is bilinear in the
+        // state.)
         if (c == G_GRAD) nb = (g.grad_gen == GEN_X || g.grad_gen == GEN_Y) ? (1ull << g.tbit[0]) : 0ull;
         blocks_bits.push_back(nb);
     }
@@ -1137,7 +1138,7 @@ static qs_status emit_and_run(qs_state *s, const std::vector<LGate> &G, const st
     }
     if (prof_enabled()) {
         // algorithmic flops per amplitude: 16 for a 2x2 complex gate, 64 for 4x4,
-        // 6 for a diagonal factor, 4 for a scaled rotation, 12 for a diagonal
+        // 6 for a diagonal factor, 4 for a rotation, 12 for a diagonal
         // block; scaled by the touched fraction 2^-(required bits)
         const double amps = (double)((uint64_t)s->batch << n);
         double fl = 0.0;
