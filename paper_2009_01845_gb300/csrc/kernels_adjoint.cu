@@ -111,35 +111,44 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
                         Di[i | h] = ui - vi;
                     }
         }
+        // groups outer, this thread's PER outputs inner: the PER partner loads of
+        // one X mask are independent and in flight together
+        V<R> acc[PER];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const uint32_t yl = threadIdx.x + 256 * j;
-            const uint32_t y = yb | yl;
-            V<R> acc = p.accumulate ? dm[y] : mkc<R>(0, 0);
-            for (int g = 0; g < p.ng; ++g) {
-                const uint32_t m = (uint32_t)p.gx[g];
-                const uint32_t x = y ^ m;
-                R fr, fi;
-                if (g == p.gdiag) {
-                    fr = Dr[j];
-                    fi = Di[j];
-                } else if (p.gconst[g]) {
-                    fr = p.gcre[g];
-                    fi = p.gcim[g];
-                } else {
-                    fr = 0;
-                    fi = 0;
+        for (int j = 0; j < PER; ++j) acc[j] = p.accumulate ? dm[yb | (threadIdx.x + 256 * j)] : mkc<R>(0, 0);
+        for (int g = 0; g < p.ng; ++g) {
+            const uint32_t m = (uint32_t)p.gx[g];
+            V<R> v[PER];
+            if ((m & ~lowm) == 0) {
+#pragma unroll
+                for (int j = 0; j < PER; ++j) v[j] = tile[(threadIdx.x + 256 * j) ^ m];
+            } else {
+#pragma unroll
+                for (int j = 0; j < PER; ++j) v[j] = sm[(yb | (threadIdx.x + 256 * j)) ^ m];
+            }
+            if (g == p.gdiag) {
+#pragma unroll
+                for (int j = 0; j < PER; ++j) acc[j] = cmadd<R>(mkc<R>(Dr[j], Di[j]), v[j], acc[j]);
+            } else if (p.gconst[g]) {
+                const V<R> c = mkc<R>(p.gcre[g], p.gcim[g]);
+#pragma unroll
+                for (int j = 0; j < PER; ++j) acc[j] = cmadd<R>(c, v[j], acc[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < PER; ++j) {
+                    const uint32_t x = (yb | (threadIdx.x + 256 * j)) ^ m;
+                    R fr = 0, fi = 0;
                     for (int tt = p.gbeg[g]; tt < p.gbeg[g + 1]; ++tt) {
                         const bool odd = __popc(x & (uint32_t)p.zb[tt]) & 1;
                         fr += odd ? -p.cre[tt] : p.cre[tt];
                         fi += odd ? -p.cim[tt] : p.cim[tt];
                     }
+                    acc[j] = cmadd<R>(mkc<R>(fr, fi), v[j], acc[j]);
                 }
-                const V<R> v = (m & ~lowm) == 0 ? tile[yl ^ m] : sm[x];
-                acc = cmadd<R>(mkc<R>(fr, fi), v, acc);
             }
-            dm[y] = acc;
         }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) dm[yb | (threadIdx.x + 256 * j)] = acc[j];
     }
 }
 
