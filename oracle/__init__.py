@@ -19,7 +19,11 @@ What it computes, and where the Qibo paper defines it:
     adjoint sweep must reproduce them (the paper differentiates through its
     native backends only, Sec. 2.3);
   * the fused matrix of a gate sequence on a qubit set (Sec. 2.4, "Gate
-    fusion": the product of the gates' matrices), ``fused_matrix``.
+    fusion": the product of the gates' matrices), ``fused_matrix``;
+  * measurements (Sec. 2.4, "Measurements", and Sec. 3.3): the outcome
+    probabilities of a group of qubits traced over the others,
+    ``marginal_probabilities``, and samples of the measurement of every qubit
+    drawn from the state's distribution for given uniforms, ``sample``.
 
 Readings where the paper is silent are stated next to the code that takes them
 (qubit order, matrix index order and gate conventions in ``statevec.c`` and
@@ -326,3 +330,37 @@ def fused_matrix(gates, qubits) -> np.ndarray:
     for col in range(1 << m):
         U[:, col] = run_circuit(m, local, basis_state(m, col))
     return U
+
+
+# ---------------------------------------------------------------- measurements
+def marginal_probabilities(psi: np.ndarray, n: int, qubits) -> np.ndarray:
+    """Outcome probabilities of the qubit group ``qubits`` (Sec. 2.4,
+    "Measurements": the outcome probability traced over the unmeasured
+    qubits): out[y] = sum of |psi[x]|^2 over the x whose qubits[j] has the value
+    of bit (m-1-j) of y (qubits[0] the most significant bit of y, as qubit 0 is
+    of the basis index). The probability tensor, one axis per qubit (axis q =
+    qubit q), is summed over the other axes and its remaining axes are put in
+    the group's order."""
+    _check_state(psi, n)
+    qubits = [int(q) for q in qubits]
+    if not qubits or len(set(qubits)) != len(qubits) or any(q < 0 or q >= n for q in qubits):
+        raise ValueError("qubits must be distinct and in range")
+    p = (np.abs(psi) ** 2).reshape((2,) * n)
+    rest = tuple(q for q in range(n) if q not in qubits)
+    marg = p.sum(axis=rest) if rest else p
+    kept = [q for q in range(n) if q in qubits]  # axis order after the sum
+    marg = np.transpose(marg, [kept.index(q) for q in qubits])
+    return np.ascontiguousarray(marg).reshape(-1)
+
+
+def sample(psi: np.ndarray, n: int, uniforms) -> np.ndarray:
+    """Samples of the measurement of every qubit (Sec. 2.4, "Measurements";
+    Sec. 3.3 samples the final state's distribution): for each u in [0, 1)
+    the smallest basis index x with cdf(x) > u * cdf(2^n - 1), cdf the
+    cumulative sum of |psi|^2 in index order (FP64). The uniforms are the
+    caller's random numbers; the mapping from them is deterministic."""
+    _check_state(psi, n)
+    cdf = np.cumsum(np.abs(psi) ** 2)
+    u = np.asarray(uniforms, dtype=np.float64)
+    x = np.searchsorted(cdf, u * cdf[-1], side="right")
+    return np.minimum(x, (1 << n) - 1).astype(np.uint64)
