@@ -195,6 +195,31 @@ qs_status qs_plan_destroy(qs_plan *p);
 qs_status qs_probabilities(qs_state *s, double *out, int on_device);
 /* sum_x |psi_x|^2 per batch member (FP64 accumulation); out: host, batch doubles. */
 qs_status qs_norm2(qs_state *s, double *out);
+
+/* Outcome probabilities of a group of qubits, traced over the others (Sec. 2.4,
+   "Measurements": qubits grouped in one register, "a trace-out of the outcome
+   probability in unmeasured qubits"), per batch member:
+   out[b * 2^m + y] = sum of |psi_b[x]|^2 over the x whose qubits[j] equals bit
+   (m-1-j) of y (qubits[0] is the most significant bit of y, as qubit 0 is of
+   the basis index). FP64 accumulation over per-block partial sums in a fixed
+   order (the order inside a block is not fixed: results may differ between
+   runs in the last bits). 1 <= m <= QS_MARGINAL_MAX_QUBITS, qubits distinct and
+   in [0, n), else QS_ERR_ARG. out: host (on_device = 0; the call synchronises)
+   or device pointer to batch * 2^m doubles. */
+#define QS_MARGINAL_MAX_QUBITS 12
+qs_status qs_marginal_probabilities(qs_state *s, const int *qubits, int m, double *out, int on_device);
+
+/* Samples of the measurement of every qubit of batch member `member` (Sec. 2.4,
+   "Measurements": sampling the final state vector; Sec. 3.3): for each uniform
+   u in [0, 1), the smallest basis index x with cdf(x) > u * cdf(2^n - 1), where
+   cdf(x) = sum_{x' <= x} |psi[x']|^2 (prefix sums in FP64 over blocks of 4096
+   amplitudes). The caller draws the uniforms, so equal uniforms give equal
+   samples (away from ties at a block boundary, where the prefix sum's
+   rounding decides). uniforms and out: `shots` values each, both in host
+   memory (on_device = 0; the call synchronises) or both in device memory.
+   member outside [0, batch), or a NULL pointer with shots > 0: QS_ERR_ARG. */
+qs_status qs_sample(qs_state *s, int member, const double *uniforms, size_t shots, uint64_t *out,
+                    int on_device);
 /* <psi|H|psi> per batch member for H = sum_t coeff_t P_t (FP64 accumulation).
    out_re/out_im: host arrays of batch doubles (out_im may be NULL). */
 qs_status qs_expectation(qs_state *s, const qs_pauli_term *terms, size_t count,

@@ -306,6 +306,73 @@ qs_status qs_probabilities(qs_state *s, double *out, int on_device) {
     QS_GUARD_END
 }
 
+qs_status qs_marginal_probabilities(qs_state *s, const int *qubits, int m, double *out, int on_device) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!out || !qubits) {
+        set_error("null argument");
+        return QS_ERR_ARG;
+    }
+    if (m < 1 || m > QS_MARGINAL_MAX_QUBITS || m > s->n) {
+        set_error("group of %d qubits: 1 to %d and at most n", m, QS_MARGINAL_MAX_QUBITS);
+        return QS_ERR_ARG;
+    }
+    int bitpos[QS_MARGINAL_MAX_QUBITS];
+    uint64_t seen = 0;
+    for (int j = 0; j < m; ++j) {
+        const int q = qubits[j];
+        if (q < 0 || q >= s->n || ((seen >> q) & 1ull)) {
+            set_error("qubit %d out of range or repeated", q);
+            return QS_ERR_ARG;
+        }
+        seen |= 1ull << q;
+        bitpos[j] = s->n - 1 - q;
+    }
+    const size_t total = (size_t)s->batch << m;
+    if (on_device) return k_marginal(s, bitpos, m, out);
+    double *tmp = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync(&tmp, total * sizeof(double), s->stream));
+    qs_status st = k_marginal(s, bitpos, m, tmp);
+    if (st == QS_OK) st = read_back(s, tmp, out, total);
+    cudaFreeAsync(tmp, s->stream);
+    return st;
+    QS_GUARD_END
+}
+
+qs_status qs_sample(qs_state *s, int member, const double *uniforms, size_t shots, uint64_t *out, int on_device) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (member < 0 || member >= s->batch) {
+        set_error("member %d outside the batch of %d", member, s->batch);
+        return QS_ERR_ARG;
+    }
+    if (shots == 0) return QS_OK;
+    if (!uniforms || !out) {
+        set_error("null argument");
+        return QS_ERR_ARG;
+    }
+    if (on_device) return k_sample(s, member, uniforms, shots, out);
+    auto ok = [](cudaError_t e, const char *what) { return e == cudaSuccess ? QS_OK : cuda_status(e, what); };
+    double *ud = nullptr;
+    uint64_t *od = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync(&ud, shots * sizeof(double), s->stream));
+    qs_status st = ok(cudaMallocAsync(&od, shots * sizeof(uint64_t), s->stream), "sample buffer");
+    if (st == QS_OK)
+        st = ok(cudaMemcpyAsync(ud, uniforms, shots * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+                "uniforms copy");
+    if (st == QS_OK) st = k_sample(s, member, ud, shots, od);
+    if (st == QS_OK)
+        st = ok(cudaMemcpyAsync(out, od, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream),
+                "samples copy");
+    if (st == QS_OK) st = ok(cudaStreamSynchronize(s->stream), "sample sync");
+    cudaFreeAsync(ud, s->stream);
+    if (od) cudaFreeAsync(od, s->stream);
+    return st;
+    QS_GUARD_END
+}
+
 qs_status qs_norm2(qs_state *s, double *out) {
     QS_GUARD_BEGIN
     clear_error();

@@ -111,6 +111,12 @@ qs_status k_expectation(qs_state *s, const qs_pauli_term *terms, size_t count,
                         double **out_dev);               // 2 * batch doubles (re, im)
 qs_status ensure_scratch(qs_state *s, size_t doubles);
 qs_status ensure_gtab(qs_state *s, size_t bytes);
+// measurements (kernels_measure.cu): marginal probabilities of the qubits at
+// index bits bitpos[0..m) per member into out_dev (batch * 2^m doubles);
+// samples of member `member` for the uniforms u_dev into out_dev
+constexpr int kMarginalMaxQubits = QS_MARGINAL_MAX_QUBITS;
+qs_status k_marginal(qs_state *s, const int *bitpos, int m, double *out_dev);
+qs_status k_sample(qs_state *s, int member, const double *u_dev, uint64_t shots, uint64_t *out_dev);
 // Per-member matrices of batched-parameter gates, 4 entries per slot: RX/RY the
 // row-major 2x2, RZ its diagonal (d0, d1), U1/CU1 the phase of the all-ones
 // block in entry 0. slot j uses column pidx[j] of the parameter

@@ -69,6 +69,8 @@ _SIGS = {
     "qs_apply_gates_batched": ([P, P, ctypes.c_size_t, P, ctypes.c_int, P], None),
     "qs_probabilities": ([P, P, ctypes.c_int], None),
     "qs_norm2": ([P, P], None),
+    "qs_marginal_probabilities": ([P, P, ctypes.c_int, P, ctypes.c_int], None),
+    "qs_sample": ([P, ctypes.c_int, P, ctypes.c_size_t, P, ctypes.c_int], None),
     "qs_expectation": ([P, P, ctypes.c_size_t, P, P], None),
     "qs_expectation_noalloc": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, ctypes.c_size_t, P, P],
                                None),
@@ -280,6 +282,33 @@ class State:
         out = np.empty(self.batch << self.n, dtype=np.float64)
         _check(self.lib.qs_probabilities(self.handle, ctypes.c_void_p(out.ctypes.data), 0))
         return out.reshape(self.batch, 1 << self.n) if self.batch > 1 else out
+
+    def marginal_probabilities(self, qubits):
+        """Outcome probabilities of the qubit group `qubits` (qubits[0] the most
+        significant bit of the outcome), per member: shape (2^m,) or (batch, 2^m)."""
+        q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32))
+        m = int(q.size)
+        out = np.empty(self.batch << m, dtype=np.float64)
+        _check(self.lib.qs_marginal_probabilities(self.handle, ctypes.c_void_p(q.ctypes.data), m,
+                                                  ctypes.c_void_p(out.ctypes.data), 0))
+        return out.reshape(self.batch, 1 << m) if self.batch > 1 else out
+
+    def sample(self, uniforms, member: int = 0):
+        """Measurement samples (basis indices) of member `member` for the given
+        uniforms in [0, 1): host arrays (numpy) or device tensors (torch, float64;
+        the result is then a device int64 tensor)."""
+        if hasattr(uniforms, "data_ptr"):
+            import torch
+            u = uniforms.contiguous()
+            out = torch.empty(u.numel(), dtype=torch.int64, device=u.device)
+            _check(self.lib.qs_sample(self.handle, member, ctypes.c_void_p(u.data_ptr()), u.numel(),
+                                      ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+        out = np.empty(u.size, dtype=np.uint64)
+        _check(self.lib.qs_sample(self.handle, member, ctypes.c_void_p(u.ctypes.data), u.size,
+                                  ctypes.c_void_p(out.ctypes.data), 0))
+        return out
 
     def norm2(self) -> np.ndarray:
         out = np.empty(self.batch, dtype=np.float64)
