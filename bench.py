@@ -18,7 +18,7 @@ simulator) on the host cores on a bounded sample of the same workload.
 
 ``--only NAME`` runs one secondary workload alone (variational_adjoint,
 adiabatic_batch, fused_tc, unfused_passes, qft_n18_c128,
-random_layer_c128_n33) and prints its result as one JSON line: for
+random_layer_c128_n33, measurement) and prints its result as one JSON line: for
 profiling those kernels; it is not the benchmark line.
 """
 from __future__ import annotations
@@ -667,6 +667,51 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def measurement(n: int = 32, reps: int = 3) -> dict:
+    """Measurement simulation (Sec. 3.3): H on every qubit at n = 32 complex64
+    (the paper's sampling benchmark), then samples of all qubits for 10^3 ..
+    10^7 device-side uniforms (seed 13), and the outcome probabilities of a
+    12-qubit and a 1-qubit group; CUDA-event times, median of `reps`, state
+    preparation excluded (as the paper subtracts it). A sampling call reads the
+    state once for its block sums, then each shot scans part of one block."""
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    st = qsim.State(n, dtype="c64").init_basis(0)
+    st.apply([qi.Gate("H", (q,)) for q in range(n)], mode="tiled")
+    torch.cuda.synchronize()
+    bw, _ = measured_peaks()
+    state_gb = (1 << n) * 8 / 1e9
+
+    def med(fn):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {"workload": f"H on every qubit, n={n}, complex64; samples of all qubits; group marginals",
+           "sampling": [], "marginals": []}
+    g = torch.Generator(device="cuda").manual_seed(13)
+    for shots in (10 ** 3, 10 ** 5, 10 ** 6, 10 ** 7):
+        u = torch.rand(shots, dtype=torch.float64, device="cuda", generator=g)
+        st.sample(u)  # warm-up
+        ms = med(lambda: st.sample(u))
+        out["sampling"].append({"shots": shots, "ms": ms, "shots_per_s": shots / (ms / 1000.0)})
+    for grp in (list(range(12)), [n - 1]):
+        st.marginal_probabilities(grp)
+        ms = med(lambda: st.marginal_probabilities(grp))
+        out["marginals"].append({"qubits": len(grp), "ms": ms, "GBps": state_gb / (ms / 1000.0),
+                                 "frac_of_measured_hbm": state_gb / (ms / 1000.0) / bw})
+    st.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 SECONDARY = {
     "variational_adjoint": lambda: variational_adjoint(),
     "adiabatic_batch": lambda: adiabatic_batch(),
@@ -674,6 +719,7 @@ SECONDARY = {
     "unfused_passes": lambda: unfused_passes(),
     "qft_n18_c128": lambda: qft_n18(),
     "random_layer_c128_n33": lambda: random_layer_c128(),
+    "measurement": lambda: measurement(),
 }
 
 

@@ -2,9 +2,9 @@
 // outcome probabilities of a group of qubits traced over the others; Sec. 3.3
 // times the sampling):
 //   * marginal_partial_kernel / marginal_finalize_kernel: per-block histograms
-//     of |psi|^2 over the group's outcome in shared memory (a warp whose 32
-//     amplitudes share one outcome adds their sum once), then a fixed-order sum
-//     of the blocks' histograms (FP64);
+//     of |psi|^2 over the group's outcome in shared memory (each thread adds a
+//     run's sum when its outcome changes), then a fixed-order sum of the
+//     blocks' histograms (FP64);
 //   * block_sums_kernel, scan kernels, sample_kernel: |psi|^2 summed over
 //     blocks of kSampleBlock amplitudes, their exclusive prefix sums in FP64
 //     (a two-level scan), and one warp per shot: a binary search over the block
@@ -33,6 +33,12 @@ struct MargP {
     uint64_t per;  // amplitudes per member
 };
 
+// Each block takes a contiguous range of the member's amplitudes; thread tid
+// reads x = start + tid + 256 i (coalesced), so its index bits 0..7 are fixed
+// and its outcome y changes only when x crosses a boundary of a group bit
+// above them: the thread sums |psi|^2 while y stays the same (runs of 64 in
+// the state's precision, then FP64) and adds the sum to the block's shared
+// histogram when y changes.
 template <typename R>
 __global__ void __launch_bounds__(256) marginal_partial_kernel(const V<R> *__restrict__ psi, const MargP p,
                                                                double *__restrict__ part) {
@@ -41,28 +47,47 @@ __global__ void __launch_bounds__(256) marginal_partial_kernel(const V<R> *__res
     for (int i = threadIdx.x; i < bins; i += blockDim.x) h[i] = 0.0;
     __syncthreads();
     const V<R> *q = psi + ((uint64_t)blockIdx.y << p.ms);
-    const int lane = threadIdx.x & 31;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // whole warps step together (the loop bound is rounded up to a warp), so
-    // the shuffles below always see 32 lanes; lanes past the end add nothing
-    const uint64_t end = (p.per + 31) & ~31ull;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < end; x += stride) {
-        R pr = 0;
-        if (x < p.per) {
-            const V<R> a = q[x];
-            pr = a.x * a.x + a.y * a.y;
-        }
-        uint32_t y = 0;
-        for (int j = 0; j < p.m; ++j) y |= (uint32_t)((x >> p.pos[j]) & 1ull) << (p.m - 1 - j);
-        const uint32_t y0 = __shfl_sync(0xffffffffu, y, 0);
-        if (__all_sync(0xffffffffu, y == y0)) {
+    const uint64_t span = ((p.per + gridDim.x - 1) / gridDim.x + 255) & ~255ull;
+    const uint64_t start = (uint64_t)blockIdx.x * span;
+    const uint64_t end = start + span < p.per ? start + span : p.per;
+    uint32_t ycur = 0xffffffffu;
+    double accd = 0.0;
+    R accf = 0;
+    int run = 0;
+    constexpr int U = 8;  // loads in flight per thread
+    for (uint64_t x0 = start + threadIdx.x; x0 < end; x0 += (uint64_t)U * blockDim.x) {
+        R pr[U];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
-            if (lane == 0) atomicAdd(&h[y0], (double)pr);
-        } else if (x < p.per) {
-            atomicAdd(&h[y], (double)pr);
+        for (int k = 0; k < U; ++k) {
+            const uint64_t x = x0 + (uint64_t)k * blockDim.x;
+            pr[k] = 0;
+            if (x < end) {
+                const V<R> a = q[x];
+                pr[k] = a.x * a.x + a.y * a.y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint64_t x = x0 + (uint64_t)k * blockDim.x;
+            if (x >= end) break;
+            uint32_t y = 0;
+            for (int j = 0; j < p.m; ++j) y |= (uint32_t)((x >> p.pos[j]) & 1ull) << (p.m - 1 - j);
+            if (y != ycur) {
+                if (ycur != 0xffffffffu) atomicAdd(&h[ycur], accd + (double)accf);
+                ycur = y;
+                accd = 0.0;
+                accf = 0;
+                run = 0;
+            }
+            accf += pr[k];
+            if (++run == 64) {
+                accd += (double)accf;
+                accf = 0;
+                run = 0;
+            }
         }
     }
+    if (ycur != 0xffffffffu) atomicAdd(&h[ycur], accd + (double)accf);
     __syncthreads();
     double *out = part + ((uint64_t)blockIdx.y * gridDim.x + blockIdx.x) * bins;
     for (int i = threadIdx.x; i < bins; i += blockDim.x) out[i] = h[i];
@@ -87,7 +112,7 @@ qs_status k_marginal(qs_state *s, const int *bitpos, int m, double *out_dev) {
     p.per = 1ull << s->n;
     const int bins = 1 << m;
     const uint64_t want = std::max<uint64_t>(1, p.per / (256 * 32));
-    const int parts = (int)std::min<uint64_t>(want, (uint64_t)std::max(1, 2 * sms_of(s->device) / s->batch));
+    const int parts = (int)std::min<uint64_t>(want, (uint64_t)std::max(1, 4 * sms_of(s->device) / s->batch));
     QS_TRY(ensure_scratch(s, (size_t)s->batch * parts * bins));
     ProfScope _ps(s->stream, KC_REDUCE, (double)(s->batch * p.per) * (s->dtype == QS_C64 ? 8 : 16),
                   3.0 * s->batch * p.per);
