@@ -2,9 +2,9 @@
 // outcome probabilities of a group of qubits traced over the others; Sec. 3.3
 // times the sampling):
 //   * marginal_partial_kernel / marginal_finalize_kernel: per-block histograms
-//     of |psi|^2 over the group's outcome in shared memory (each thread adds a
-//     run's sum when its outcome changes), then a fixed-order sum of the
-//     blocks' histograms (FP64);
+//     of |psi|^2 over the group's outcome in shared memory (each thread adds
+//     the sum of a run of amplitudes with one outcome), then a fixed-order sum
+//     of the blocks' histograms (FP64);
 //   * block_sums_kernel, scan kernels, sample_kernel: |psi|^2 summed over
 //     blocks of kSampleBlock amplitudes, their exclusive prefix sums in FP64
 //     (a two-level scan), and one warp per shot: a binary search over the block
@@ -33,12 +33,13 @@ struct MargP {
     uint64_t per;  // amplitudes per member
 };
 
-// Each block takes a contiguous range of the member's amplitudes; thread tid
-// reads x = start + tid + 256 i (coalesced), so its index bits 0..7 are fixed
-// and its outcome y changes only when x crosses a boundary of a group bit
-// above them: the thread sums |psi|^2 while y stays the same (runs of 64 in
-// the state's precision, then FP64) and adds the sum to the block's shared
-// histogram when y changes.
+// Each block takes a contiguous range of the member's amplitudes (a multiple
+// of 256 long); thread tid reads x = start + tid + 256 i (coalesced), so its
+// index bits 0..7 are fixed and its outcome y changes only where x crosses a
+// multiple of 2^pmin, pmin the lowest group bit above bit 7. The thread walks
+// those runs: y is formed once per run, the run's |psi|^2 is summed (runs of
+// 64 in the state's precision, then FP64; 8 loads in flight) and added to the
+// block's shared histogram.
 template <typename R>
 __global__ void __launch_bounds__(256) marginal_partial_kernel(const V<R> *__restrict__ psi, const MargP p,
                                                                double *__restrict__ part) {
@@ -50,44 +51,43 @@ __global__ void __launch_bounds__(256) marginal_partial_kernel(const V<R> *__res
     const uint64_t span = ((p.per + gridDim.x - 1) / gridDim.x + 255) & ~255ull;
     const uint64_t start = (uint64_t)blockIdx.x * span;
     const uint64_t end = start + span < p.per ? start + span : p.per;
-    uint32_t ycur = 0xffffffffu;
-    double accd = 0.0;
-    R accf = 0;
-    int run = 0;
+    int pmin = 63;
+    for (int j = 0; j < p.m; ++j)
+        if (p.pos[j] >= 8 && p.pos[j] < pmin) pmin = p.pos[j];
     constexpr int U = 8;  // loads in flight per thread
-    for (uint64_t x0 = start + threadIdx.x; x0 < end; x0 += (uint64_t)U * blockDim.x) {
-        R pr[U];
+    for (uint64_t x0 = start + threadIdx.x; x0 < end;) {
+        uint32_t y = 0;
+        for (int j = 0; j < p.m; ++j) y |= (uint32_t)((x0 >> p.pos[j]) & 1ull) << (p.m - 1 - j);
+        // the run ends at the next multiple of 2^pmin (or the range's end)
+        const uint64_t bound = ((x0 >> pmin) + 1) << pmin;
+        const uint64_t rend = bound < end ? bound : end;
+        double accd = 0.0;
+        R accf = 0;
+        int run = 0;
+        uint64_t x = x0;
+        for (; x < rend; x += (uint64_t)U * blockDim.x) {
+            R pr[U];
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const uint64_t x = x0 + (uint64_t)k * blockDim.x;
-            pr[k] = 0;
-            if (x < end) {
-                const V<R> a = q[x];
-                pr[k] = a.x * a.x + a.y * a.y;
+            for (int k = 0; k < U; ++k) {
+                const uint64_t xk = x + (uint64_t)k * blockDim.x;
+                pr[k] = 0;
+                if (xk < rend) {
+                    const V<R> a = q[xk];
+                    pr[k] = a.x * a.x + a.y * a.y;
+                }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const uint64_t x = x0 + (uint64_t)k * blockDim.x;
-            if (x >= end) break;
-            uint32_t y = 0;
-            for (int j = 0; j < p.m; ++j) y |= (uint32_t)((x >> p.pos[j]) & 1ull) << (p.m - 1 - j);
-            if (y != ycur) {
-                if (ycur != 0xffffffffu) atomicAdd(&h[ycur], accd + (double)accf);
-                ycur = y;
-                accd = 0.0;
-                accf = 0;
-                run = 0;
-            }
-            accf += pr[k];
-            if (++run == 64) {
+            for (int k = 0; k < U; ++k) accf += pr[k];
+            run += U;
+            if (run >= 64) {
                 accd += (double)accf;
                 accf = 0;
                 run = 0;
             }
         }
+        atomicAdd(&h[y], accd + (double)accf);
+        x0 = rend + threadIdx.x;  // rend is a multiple of 256 unless it is the range's end
     }
-    if (ycur != 0xffffffffu) atomicAdd(&h[ycur], accd + (double)accf);
     __syncthreads();
     double *out = part + ((uint64_t)blockIdx.y * gridDim.x + blockIdx.x) * bins;
     for (int i = threadIdx.x; i < bins; i += blockDim.x) out[i] = h[i];
