@@ -76,6 +76,18 @@ def test_random_layer_circuit(emu, dtype, n):
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
+def test_random_layer_window_passes(emu, dtype):
+    """n = 18 > 13 tile bits: passes whose high tile bits are a window of
+    consecutive index bits (the light cone of a nearest-neighbour circuit)
+    next to greedily chosen ones, with frames, flips and blocks across them."""
+    n = 18
+    gates = qi.random_layer_circuit(n, 12, seed=3)
+    got = run_emulated(emu, n, gates, dtype)
+    want = oracle.run_circuit(n, gates)
+    assert np.max(np.abs(got - want)) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("n,seed", [(13, 1), (14, 2), (15, 3)])
 def test_random_mixed_circuit(emu, dtype, n, seed):
     gates = qi.random_mixed_circuit(n, 160, seed=seed, max_controls=2)
