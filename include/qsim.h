@@ -6,7 +6,8 @@
  *     updated in place, 2^n complex numbers of memory);
  *   - gate application: Eq. (1) of Sec. 2.3, controls as in Sec. 2.4
  *     ("Controlled gates"), fused blocks as in Sec. 2.4 ("Gate fusion");
- *   - probabilities: Sec. 2.4 ("Measurements");
+ *   - probabilities, outcome probabilities of qubit groups and measurement
+ *     samples: Sec. 2.4 ("Measurements"), Sec. 3.3;
  *   - Pauli-sum expectation values: Sec. 2.4 ("Callbacks", Energy);
  *   - Trotter steps of H(s) = (1-s) H0 + s H1: Sec. 2.6, Eqs. (4)-(6);
  *   - adjoint gradients and batched execution have no counterpart in the
