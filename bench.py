@@ -169,9 +169,15 @@ def tiled_traffic(a):
 
 
 def roofline(name, rec, a, clk):
-    """Roofline of one kernel class: whichever of HBM time (algorithmic bytes /
-    measured copy bandwidth) and ALU time (algorithmic flops / peak of the
-    state's arithmetic type) is larger bounds it."""
+    """Roofline of the dominant kernel class. The bound is HBM bandwidth: the
+    class's algorithmic bytes (one read and one write of the state per pass,
+    B(n, b) = 2 * 2^n * b) over its CUDA-event time, against the measured copy
+    bandwidth. A secondary ALU figure reports the same launches' arithmetic:
+    flops are the implementation's own count of its rotation / diagonal-block
+    decomposition (4 per amplitude per rotation, 12 per diagonal block, ...),
+    and the peak is the unit count times the sampled SM clock (FP32: 152 SMs x
+    128 lanes x 2 flops per FMA; complex128: FP64 at 1.19 TFLOP/s, an FP64 FMA
+    loop timed on this GPU)."""
     tot_ms, launches, nbytes, nflops = rec
     if not launches or tot_ms <= 0:
         return None
@@ -181,32 +187,30 @@ def roofline(name, rec, a, clk):
     t = tot_ms / 1000.0
     gbs = nbytes / t / 1e9
     tfl = nflops / t / 1e12
-    f_hbm, f_alu = gbs / bw, tfl / alu
-    base = {"kernel": name, "launches_per_step": launches / a.steps, "avg_launch_ms": tot_ms / launches,
-            "bytes_per_launch": nbytes / launches, "flops_per_launch": nflops / launches,
-            "hbm": {"achieved": gbs, "peak": bw, "unit": "GB/s", "frac": f_hbm,
-                    "peak_source": f"{bw_src} (MEASURED_PEAKS hbm_gbs)"},
-            "alu": {"achieved": tfl, "peak": alu, "unit": "TFLOP/s", "frac": f_alu,
-                    "peak_source": ("FP32: 152 SMs x 128 lanes x 2 x median SM clock" if a.dtype == "c64"
-                                    else "FP64 FMA microbenchmark on GB300")},
+    return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": bw, "unit": "GB/s", "frac": gbs / bw,
+            "peak_source": f"{bw_src}: MEASURED_PEAKS hbm_gbs",
             "traffic": tiled_traffic(a) if name == "tiled" else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                              "profiles/launches_random_layer_n32_c64.md (null if the kernel sources changed)"}
-    if nbytes / (bw * 1e9) >= nflops / (alu * 1e12):
-        base.update({"bound": "hbm", "achieved": gbs, "peak": bw, "unit": "GB/s", "frac": f_hbm})
-    else:
-        base.update({"bound": "alu", "achieved": tfl, "peak": alu, "unit": "TFLOP/s", "frac": f_alu})
-    return base
+                              "profiles/launches_random_layer_n32_c64.md (null if the kernel sources changed)",
+            "launches_per_step": launches / a.steps, "avg_launch_ms": tot_ms / launches,
+            "bytes_per_launch": nbytes / launches,
+            "alu": {"achieved": tfl, "peak": alu, "unit": "TFLOP/s", "frac": tfl / alu,
+                    "flops_per_launch": nflops / launches,
+                    "flops_source": "the implementation's own count of its decomposition",
+                    "peak_source": ("FP32 units: 152 SMs x 128 lanes x 2 x median SM clock" if a.dtype == "c64"
+                                    else "FP64 FMA loop timed on GB300")}}
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(a, budget_s: float = 15.0):
-    """Time the oracle (plain C complex128, one thread) on a bounded sample of
-    the workload: the same circuit family at n_s qubits, first gates in order,
-    until ~budget_s; per-gate time scaled by 2^(n - n_s) to the full n."""
+def oracle_sample(a, budget_s: float = 12.0, threads: int = 1, n_s: int = 24):
+    """Time the oracle (plain C complex128, unfused) on a bounded sample of the
+    workload: the same circuit family at n_s qubits, first gates in order,
+    until ~budget_s, with `threads` threads on the gate loop; per-gate time
+    scaled by 2^(n - n_s) to the full n (gate cost is linear in 2^n)."""
     import oracle
     from paper_2009_01845_gb300 import inputs as qi
-    n_s = min(a.n, 24)
+    n_s = min(a.n, n_s)
+    used = oracle.set_threads(threads)
     gates = qi.random_layer_circuit(n_s, a.layers, seed=2)
     psi = oracle.zero_state(n_s)
     done, t0 = 0, time.perf_counter()
@@ -216,28 +220,55 @@ def oracle_sample(a, budget_s: float = 15.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    oracle.set_threads(1)
     per_gate_full = dt / done * 2.0 ** (a.n - n_s)
-    return {"value": 1.0 / per_gate_full, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done} gates of the same circuit at n={n_s} (complex128, "
+    return {"value": 1.0 / per_gate_full, "unit": UNIT, "cores": used, "kind": "oracle",
+            "extrapolated_from_n": n_s, "wall_s": dt,
+            "sample": f"first {done} gates of the same circuit at n={n_s} (complex128, {used} thread(s), "
                       f"{dt:.1f} s), per-gate time scaled by 2^{a.n - n_s} to n={a.n}"}
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(a):
+    """The oracle on all host cores (gate loop split by OpenMP), and on one
+    core for reference; ~25 s of CPU work in total."""
+    allc = oracle_sample(a, budget_s=12.0, threads=host_cores())
+    one = oracle_sample(a, budget_s=8.0, threads=1)
+    allc["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
+    return allc
+
+
 def run_reference(a):
+    """The reference arm: the oracle (the plain complex128 unfused simulator)
+    on all host cores. A step is a bounded sample of the workload: the first
+    gates of the same circuit at n = 24, whose per-gate time is scaled by
+    2^(n - 24) to give the metric at the full n (labelled by
+    extrapolated_from_n). ms_per_step is the sample's own wall time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     per_step = []
+    budget = max(2.0, 60.0 / max(1, a.steps + a.warmup))
+    cores = host_cores()
     for i in range(a.warmup + a.steps):
-        r = oracle_sample(a, budget_s=max(2.0, 60.0 / max(1, a.steps + a.warmup)))
+        r = oracle_sample(a, budget_s=budget, threads=cores)
         if i >= a.warmup:
             per_step.append(r)
     v = statistics.median(x["value"] for x in per_step)
-    ms = 1000.0 * (a.layers * a.n + a.layers * (a.n - 1) // 2 + 0) / v if v else None
+    ms = 1000.0 * statistics.mean(x["wall_s"] for x in per_step)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(a),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": workload_config(a), "extrapolated_from_n": per_step[-1]["extrapolated_from_n"],
+            "step": "a bounded sample of the workload: the circuit's first gates at n=24, per-gate time "
+                    "scaled by 2^(n-24); ms_per_step is that sample's wall time",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": per_step[-1]["cores"], "kind": "oracle",
                              "sample": per_step[-1]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -282,8 +313,11 @@ def variational_adjoint(steps: int = 5) -> dict:
     torch.cuda.synchronize()
     qsim.profile_enable(False)
     prof = qsim.profile_collect()
+    t_hpsi = prof.get("hpsi", (0.0,))[0]
     return {"workload": "variational n=20, 10 layers, batch 256, complex64, TFIM g=1",
-            "forward_ms": t_fwd, "forward_plus_adjoint_ms": t_full,
+            "forward_ms": t_fwd, "forward_plus_adjoint_ms": t_full, "hpsi_ms": t_hpsi,
+            # the reverse sweep plus lambda = H psi, over the forward without it
+            "adjoint_incl_hpsi_over_forward": (t_full - t_fwd + t_hpsi) / (t_fwd - t_hpsi),
             "adjoint_over_forward": (t_full - t_fwd) / t_fwd, "total_over_forward": t_full / t_fwd,
             "gradients_per_s": B * P / (t_full / 1000.0),
             "kernels_full_call": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
@@ -319,7 +353,11 @@ def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
     batched()
     torch.cuda.synchronize()
     qsim.profile_enable(False)
-    prof_b = {k: {"ms": v[0], "launches": v[1]} for k, v in qsim.profile_collect().items() if v[1]}
+    prof_raw = qsim.profile_collect()
+    prof_b = {k: {"ms": v[0], "launches": v[1], "GB": v[2] / 1e9} for k, v in prof_raw.items() if v[1]}
+    # algorithmic bytes: every tiled pass reads and writes its members' states once
+    alg_bytes = sum(v[2] for v in prof_raw.values())
+    bw, _ = measured_peaks()
     solo = {w: qsim.State(w, dtype=dtype) for w in widths}
 
     def sequential():
@@ -351,6 +389,10 @@ def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
             "instance_steps_per_s_batched": isteps / (t_b / 1000.0),
             "instance_steps_per_s_sequential": isteps / (t_s / 1000.0),
             "projected_full_run_s_batched": t_b / 1000.0 * 1000 / steps,
+            "algorithmic_GB_per_step": alg_bytes / steps / 1e9,
+            "batched_hbm_frac": alg_bytes / (t_b / 1000.0) / 1e9 / bw,
+            "tiled_hbm_frac": (prof_raw["tiled"][2] / (prof_raw["tiled"][0] / 1000.0) / 1e9 / bw
+                               if prof_raw.get("tiled", (0,))[0] else None),
             "kernels_batched_run": prof_b,
             "widths": {int(w): len(ix) for w, ix in groups.items()},
             "smallest_instance": {"n": m0, "final_energy": e_final, "ground_energy": float(gmin),
@@ -519,6 +561,56 @@ def random_layer_c128(n: int = 33, layers: int = 2) -> dict:
     return out
 
 
+def summary(line: dict) -> dict:
+    """A compact digest of the line: headline, roofline, and one or two
+    figures per secondary workload."""
+    def get(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    def rnd(x, k=4):
+        return None if x is None else float(f"{x:.{k}g}")
+
+    sec = line.get("secondary", {})
+    out = {"gate_per_s": rnd(line["value"]), "ms_per_step": rnd(line["ms_per_step"]),
+           "tiled_hbm_frac": rnd(get(line, "roofline", "frac"), 3),
+           "tiled_alu_frac": rnd(get(line, "roofline", "alu", "frac"), 3),
+           "e2e_gate_per_s": rnd(get(line, "e2e", "value")),
+           "cpu_gate_per_s": rnd(get(line, "cpu_baseline", "value")),
+           "cpu_cores": get(line, "cpu_baseline", "cores")}
+    va = sec.get("variational_adjoint")
+    if va:
+        out["adjoint"] = {"fwd_ms": rnd(va["forward_ms"]), "full_ms": rnd(va["forward_plus_adjoint_ms"]),
+                          "adj_incl_hpsi_over_fwd": rnd(va["adjoint_incl_hpsi_over_forward"], 3),
+                          "total_over_fwd": rnd(va["total_over_forward"], 3)}
+    ab = sec.get("adiabatic_batch")
+    if ab:
+        out["adiabatic"] = {k: rnd(v) for k, v in ab.items() if k.startswith("instance_steps") or
+                            k.endswith("hbm_frac")}
+    ft = sec.get("fused_tc")
+    if ft:
+        out["fused_tc"] = {"fused_gate_per_s": rnd(get(ft, "fused", "gate_apps_per_s")),
+                           "tiled_gate_per_s": rnd(get(ft, "tiled", "gate_apps_per_s")),
+                           "fused_pass_ms": rnd(get(ft, "fused", "avg_pass_ms"))}
+    up = sec.get("unfused_passes")
+    if up:
+        out["unfused_hbm_frac"] = {f'{p["dtype"]} {p["gate"]}': rnd(p["frac_of_measured_hbm"], 3)
+                                   for p in up["passes"]}
+    q = sec.get("qft_n18_c128")
+    if q:
+        out["qft_n18_gate_per_s"] = {k: rnd(v["gate_apps_per_s"]) for k, v in q.items() if isinstance(v, dict)}
+    rc = sec.get("random_layer_c128_n33")
+    if rc:
+        out["c128_n33_gate_per_s"] = {k: rnd(v["gate_apps_per_s"]) for k, v in rc.items() if isinstance(v, dict)}
+    ms = sec.get("measurement")
+    if ms:
+        out["marginal_hbm_frac"] = [rnd(m["frac_of_measured_hbm"], 3) for m in ms["marginals"]]
+    return out
+
+
 # ------------------------------------------------------------------ multi-rank helpers
 def max_over_ranks(x: float, world: int) -> float:
     """The maximum of x over all ranks (the slowest replica sets the job's
@@ -638,7 +730,7 @@ def run_ours(a):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = oracle_sample(a)
+        cpu = cpu_baseline(a)
     secondary = {}
     if not a.no_secondary:
         st.close()
@@ -660,6 +752,8 @@ def run_ours(a):
                             for k, v in prof.items() if v[1]},
                 "energy_zz": float(out_re[0]), "norm2": float(out_n[0]),
                 "secondary": secondary}
+        # the key figures once more, last, so that a truncated log keeps them
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if a.no_secondary:
         st.close()

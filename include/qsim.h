@@ -87,6 +87,9 @@ typedef int32_t qs_dtype;
 
 #define QS_MAX_TARGETS 5
 #define QS_MAX_QUBITS 40
+/* Largest batch of one handle: the per-member reductions put the member on the
+   second grid dimension, whose extent CUDA limits to 65535. */
+#define QS_MAX_BATCH 65535
 
 /* One gate of a queue (Eq. (1); a circuit is an ordered queue, Sec. 2.3). */
 typedef struct qs_gate {
@@ -132,7 +135,8 @@ const char *qs_version(void);
 /* ---------------------------------------------------------------- states */
 /* Allocate a batch of `batch` states of n qubits (batch * 2^n amplitudes) on the
    current CUDA device; the library owns and frees the memory. Contents are
-   undefined until initialised. QS_ERR_OOM if the allocation fails. */
+   undefined until initialised. 1 <= batch <= QS_MAX_BATCH and
+   batch * 2^n <= 2^46, else QS_ERR_ARG; QS_ERR_OOM if the allocation fails. */
 qs_status qs_state_create(int n, int batch, qs_dtype dtype, void *cuda_stream, qs_state **out);
 /* Wrap caller-owned device memory of batch * 2^n amplitudes (16-byte aligned);
    the handle never frees it and it must outlive the handle. */
@@ -198,8 +202,8 @@ qs_status qs_probabilities(qs_state *s, double *out, int on_device);
 qs_status qs_norm2(qs_state *s, double *out);
 
 /* Outcome probabilities of a group of qubits, traced over the others (Sec. 2.4,
-   "Measurements": qubits grouped in one register, "a trace-out of the outcome
-   probability in unmeasured qubits"), per batch member:
+   Measurements: the qubits of one register are measured together and the
+   probability is summed over the unmeasured ones), per batch member:
    out[b * 2^m + y] = sum of |psi_b[x]|^2 over the x whose qubits[j] equals bit
    (m-1-j) of y (qubits[0] is the most significant bit of y, as qubit 0 is of
    the basis index). FP64 accumulation over per-block partial sums in a fixed
@@ -218,7 +222,10 @@ qs_status qs_marginal_probabilities(qs_state *s, const int *qubits, int m, doubl
    samples (away from ties at a block boundary, where the prefix sum's
    rounding decides). uniforms and out: `shots` values each, both in host
    memory (on_device = 0; the call synchronises) or both in device memory.
-   member outside [0, batch), or a NULL pointer with shots > 0: QS_ERR_ARG. */
+   member outside [0, batch), a NULL pointer with shots > 0, or (host
+   uniforms) a uniform that is not in [0, 1): QS_ERR_ARG. Device uniforms are
+   not checked: one below 0 is taken as 0 and one of 1 or above, or NaN, as 1,
+   so every sample is an outcome of nonzero probability (for a nonzero state). */
 qs_status qs_sample(qs_state *s, int member, const double *uniforms, size_t shots, uint64_t *out,
                     int on_device);
 /* <psi|H|psi> per batch member for H = sum_t coeff_t P_t (FP64 accumulation).
@@ -236,8 +243,8 @@ qs_status qs_expectation(qs_state *s, const qs_pauli_term *terms, size_t count,
    needs no handle and calls no cudaMalloc/cudaFree or other allocator: its
    partial sums live in one fixed device array of QS_NOALLOC_MAX_PARTIALS
    (65536) double2 entries (1 MiB) that every GPU loading this library holds
-   until the process exits, so batch must be <= QS_NOALLOC_MAX_PARTIALS
-   (larger: QS_ERR_ARG). The first call on a device looks up that array's
+   until the process exits; batch must be <= QS_MAX_BATCH (65535, the grid
+   limit every batched read-out shares; larger: QS_ERR_ARG). The first call on a device looks up that array's
    device address (a runtime query, not an allocation); make that first call
    before any stream capture. Every call shares the array and leaves its
    partial sums in it (each call overwrites the slots it uses before summing
@@ -303,7 +310,8 @@ qs_status qs_adiabatic_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
 /* Tracing aid (no counterpart in the paper). While enabled, every kernel launch
    of the library is bracketed by CUDA events on the launching stream, grouped
    by kernel class (dense, phase, diag, swap, param, tiled, fused_tc, reduce,
-   trotter_diag, adjoint, init). Process-wide. */
+   trotter_diag, adjoint, hpsi = the adjoint's lambda = H psi, init).
+   Process-wide. */
 qs_status qs_profile_enable(int on);
 /* Wait for the recorded launches, write per-class total milliseconds, launch
    counts, algorithmic bytes (the HBM reads + writes each operation needs) and

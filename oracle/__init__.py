@@ -56,14 +56,24 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the C core with gcc (plain -O2, single-threaded)."""
+    """Compile the C core with gcc (plain -O2; OpenMP for the optional
+    all-cores gate loop, single-threaded unless ``set_threads`` asks)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC,
-                               "-o", tmp, "-lm"])
+        try:
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC,
+                                   "-o", tmp, "-lm"])
+        except subprocess.CalledProcessError:
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
+
+
+def set_threads(t: int) -> int:
+    """Threads for gate application (1 = the plain single-threaded loop);
+    returns the number in effect. Results do not depend on it."""
+    return int(_load().orc_set_threads(int(t)))
 
 
 def _load():
@@ -74,6 +84,8 @@ def _load():
             P = ctypes.c_void_p
             lib.orc_apply_matrix.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P]
             lib.orc_apply_matrix.restype = ctypes.c_int
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
+            lib.orc_set_threads.restype = ctypes.c_int
             lib.orc_probabilities.argtypes = [P, ctypes.c_int, P]
             lib.orc_norm2.argtypes = [P, ctypes.c_int]
             lib.orc_norm2.restype = ctypes.c_double
@@ -358,9 +370,15 @@ def sample(psi: np.ndarray, n: int, uniforms) -> np.ndarray:
     Sec. 3.3 samples the final state's distribution): for each u in [0, 1)
     the smallest basis index x with cdf(x) > u * cdf(2^n - 1), cdf the
     cumulative sum of |psi|^2 in index order (FP64). The uniforms are the
-    caller's random numbers; the mapping from them is deterministic."""
+    caller's random numbers; the mapping from them is deterministic. For
+    u < 1 the target u * total lies below the total, so such an x exists and
+    has nonzero probability; where rounding puts the target at the total, the
+    answer in exact arithmetic is the last outcome of nonzero probability."""
     _check_state(psi, n)
-    cdf = np.cumsum(np.abs(psi) ** 2)
+    p = np.abs(psi) ** 2
+    cdf = np.cumsum(p)
     u = np.asarray(uniforms, dtype=np.float64)
     x = np.searchsorted(cdf, u * cdf[-1], side="right")
-    return np.minimum(x, (1 << n) - 1).astype(np.uint64)
+    nz = np.flatnonzero(p > 0)
+    last = int(nz[-1]) if nz.size else (1 << n) - 1
+    return np.where(x >= (1 << n), last, x).astype(np.uint64)

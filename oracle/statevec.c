@@ -16,7 +16,10 @@
  *   - a controlled gate acts only on the index groups whose control bits are all
  *     1 (Sec. 2.4, "Controlled gates").
  * Every routine below is the textbook definition written out with plain loops:
- * no blocking, no fusion, no reordering.
+ * no blocking, no fusion, no reordering. Gate application may split its loop
+ * over index groups across threads (orc_set_threads; default 1): every group
+ * is read and written by one thread, so the result does not depend on the
+ * thread count. The reductions stay single-threaded (fixed summation order).
  */
 #include <complex.h>
 #include <math.h>
@@ -24,6 +27,21 @@
 #include <stdlib.h>
 
 typedef double complex cplx;
+
+static int orc_threads = 1;
+
+/* Threads for gate application (the CPU baseline's all-cores run); returns
+   the number in effect (1 where the build has no OpenMP). */
+int orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    orc_threads = t > 0 ? t : 1;
+#else
+    (void)t;
+    orc_threads = 1;
+#endif
+    return orc_threads;
+}
 
 static uint64_t qubit_bit(int n, int q) { return 1ull << (n - 1 - q); }
 
@@ -59,8 +77,11 @@ int orc_apply_matrix(cplx *psi, int n, int k, const int *targets,
         offset[l] = o;
     }
 
-    cplx in[64], out[64];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(orc_threads) if (orc_threads > 1)
+#endif
     for (uint64_t i = 0; i < dim; ++i) {
+        cplx in[64], out[64];
         if (i & tmask) continue;             /* i is the group's base index */
         if ((i & cmask) != cmask) continue;  /* controls not all 1: unchanged */
         for (int c = 0; c < K; ++c) in[c] = psi[i | offset[c]];

@@ -47,8 +47,9 @@ static qs_status check_shape(int n, int batch, qs_dtype dtype) {
         set_error("n = %d outside [1, %d]", n, QS_MAX_QUBITS);
         return QS_ERR_ARG;
     }
-    if (batch < 1 || batch > (1 << 24)) {
-        set_error("batch = %d outside [1, 2^24]", batch);
+    if (batch < 1 || batch > QS_MAX_BATCH) {
+        set_error("batch = %d outside [1, %d] (members are a grid dimension of at most 65535)", batch,
+                  QS_MAX_BATCH);
         return QS_ERR_ARG;
     }
     if (dtype != QS_C64 && dtype != QS_C128) {
@@ -354,6 +355,11 @@ qs_status qs_sample(qs_state *s, int member, const double *uniforms, size_t shot
         return QS_ERR_ARG;
     }
     if (on_device) return k_sample(s, member, uniforms, shots, out);
+    for (size_t i = 0; i < shots; ++i)
+        if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) {
+            set_error("uniform %zu = %g is not in [0, 1)", i, uniforms[i]);
+            return QS_ERR_ARG;
+        }
     auto ok = [](cudaError_t e, const char *what) { return e == cudaSuccess ? QS_OK : cuda_status(e, what); };
     double *ud = nullptr;
     uint64_t *od = nullptr;

@@ -172,7 +172,7 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
         groups[gi].push_back(t);
     }
     const uint64_t total = (uint64_t)src.batch << n;
-    ProfScope _ps(st, KC_ADJOINT, 2.0 * total * sizeof(V<R>), 8.0 * total * (double)count);
+    ProfScope _ps(st, KC_HPSI, 2.0 * total * sizeof(V<R>), 8.0 * total * (double)count);
     bool first = true;
     size_t gi = 0;
     while (gi < masks.size() || first) {

@@ -1223,9 +1223,9 @@ extern "C" qs_status qs_expectation_noalloc(const void *psi_dev, int n, int batc
             set_error("bad n or dtype");
             return QS_ERR_ARG;
         }
-        if (batch < 1 || batch > kNoAllocMaxPartials) {
-            set_error("batch = %d outside [1, %d] (the fixed scratch holds %d partial sums)", batch,
-                      kNoAllocMaxPartials, kNoAllocMaxPartials);
+        if (batch < 1 || batch > QS_MAX_BATCH) {
+            set_error("batch = %d outside [1, %d] (members are a grid dimension of at most %d)", batch,
+                      QS_MAX_BATCH, QS_MAX_BATCH);
             return QS_ERR_ARG;
         }
         if ((uint64_t)batch > (1ull << (46 - n))) {

@@ -113,15 +113,23 @@ qs_status k_marginal(qs_state *s, const int *bitpos, int m, double *out_dev) {
     const int bins = 1 << m;
     const uint64_t want = std::max<uint64_t>(1, p.per / (256 * 32));
     const int parts = (int)std::min<uint64_t>(want, (uint64_t)std::max(1, 4 * sms_of(s->device) / s->batch));
-    QS_TRY(ensure_scratch(s, (size_t)s->batch * parts * bins));
+    // one part per member (large batches): the partial histograms are the
+    // result, written straight into out_dev with no scratch; otherwise the
+    // scratch holds batch * parts <= 4 x SMs histograms
+    double *part = out_dev;
+    if (parts > 1) {
+        QS_TRY(ensure_scratch(s, (size_t)s->batch * parts * bins));
+        part = s->scratch;
+    }
     ProfScope _ps(s->stream, KC_REDUCE, (double)(s->batch * p.per) * (s->dtype == QS_C64 ? 8 : 16),
                   3.0 * s->batch * p.per);
     const dim3 grid((unsigned)parts, (unsigned)s->batch);
     if (s->dtype == QS_C64)
-        marginal_partial_kernel<float><<<grid, 256, 0, s->stream>>>((const float2 *)s->data, p, s->scratch);
+        marginal_partial_kernel<float><<<grid, 256, 0, s->stream>>>((const float2 *)s->data, p, part);
     else
-        marginal_partial_kernel<double><<<grid, 256, 0, s->stream>>>((const double2 *)s->data, p, s->scratch);
+        marginal_partial_kernel<double><<<grid, 256, 0, s->stream>>>((const double2 *)s->data, p, part);
     QS_CUDA_TRY(cudaGetLastError());
+    if (parts == 1) return QS_OK;
     const dim3 g2((unsigned)((bins + 255) / 256), (unsigned)s->batch);
     marginal_finalize_kernel<<<g2, 256, 0, s->stream>>>(s->scratch, parts, bins, out_dev);
     QS_CUDA_TRY(cudaGetLastError());
@@ -217,13 +225,21 @@ __global__ void __launch_bounds__(256) sample_kernel(const V<R> *__restrict__ q,
     if (w >= shots) return;
     const int lane = threadIdx.x & 31;
     const double total = pre[nb - 1] + bsum[nb - 1];
-    const double target = u[w] * total;
+    // a uniform outside [0, 1) is clamped: below 0 to 0, 1 or above (or NaN) to 1
+    double uu = u[w];
+    if (!(uu < 1.0)) uu = 1.0;
+    if (uu < 0.0) uu = 0.0;
+    const double target = uu * total;
     uint64_t lo = 0, hi = nb - 1;  // the last block whose exclusive prefix is <= target
     while (lo < hi) {
         const uint64_t mid = (lo + hi + 1) >> 1;
         if (pre[mid] <= target) lo = mid;
         else hi = mid - 1;
     }
+    // the prefix sums are monotone only up to rounding, so the search can end
+    // in a block of zero probability: step back to the last block before it
+    // that has some (its last nonzero outcome is then the sample)
+    while (lo > 0 && !(bsum[lo] > 0.0)) --lo;
     const V<R> *b = q + lo * L;
     double running = pre[lo];
     uint64_t found = ~0ull, last_nz = lo * L;
@@ -239,7 +255,10 @@ __global__ void __launch_bounds__(256) sample_kernel(const V<R> *__restrict__ q,
             const R t = __shfl_up_sync(0xffffffffu, sc, o);
             if (lane >= o) sc += t;
         }
-        const unsigned hit = __ballot_sync(0xffffffffu, running + (double)sc > target);
+        // only a lane of nonzero probability can be the sample: the scan's
+        // rounding differs between lanes, so a zero lane after the target's
+        // position can compare above it while the nonzero lane before did not
+        const unsigned hit = __ballot_sync(0xffffffffu, pr > (R)0 && running + (double)sc > target);
         const unsigned nz = __ballot_sync(0xffffffffu, pr > (R)0);
         if (nz) last_nz = lo * L + c + (31 - __clz(nz));
         if (hit) {

@@ -26,7 +26,7 @@ double g_bytes[KC_COUNT];
 double g_flops[KC_COUNT];
 
 const char *kNames[KC_COUNT] = {"init", "dense", "phase", "diag", "swap", "param",
-                                "tiled", "fused_tc", "reduce", "trotter_diag", "adjoint"};
+                                "tiled", "fused_tc", "reduce", "trotter_diag", "adjoint", "hpsi"};
 
 cudaEvent_t take() {
     if (!g_pool.empty()) {

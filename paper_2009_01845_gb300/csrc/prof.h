@@ -18,6 +18,7 @@ enum KClass {
     KC_REDUCE,
     KC_TROTTER_DIAG,
     KC_ADJOINT,
+    KC_HPSI,     // lambda = H psi of the adjoint (Pauli-sum application)
     KC_COUNT
 };
 

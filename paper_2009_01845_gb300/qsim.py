@@ -397,6 +397,10 @@ class EnergyGradient:
         self.gate_arr, self._keep = marshal_gates(gates, param_index)
         self.count = len(gates)
         self.term_arr, self.n_terms = marshal_terms(terms)
+        # run counter, and the run whose forward state (psi, lambda) ``work``
+        # still holds (None once a sweep or a full run has consumed it)
+        self.generation = 0
+        self.forward_generation = None
 
     def run(self, params, mode: str = "full", init_zero: bool = True, ckpt_every: int = 0, energy=None,
             grad=None):
@@ -410,15 +414,28 @@ class EnergyGradient:
         if mode != "forward" and grad is None:
             grad = torch.empty(self.batch, npar, dtype=torch.float64, device="cuda")
         ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        if mode == "sweep" and self.forward_generation is None:
+            raise RuntimeError("sweep needs a forward run whose state is still in the work buffer")
+        self.generation += 1
+        self.forward_generation = None
         _check(self.lib.qs_energy_gradient(self.state.handle, self.gate_arr, self.count, ptr(params), npar,
                                            self.term_arr, self.n_terms, 1 if init_zero else 0, ptr(energy),
                                            ptr(grad), int(ckpt_every), GRAD_MODE[mode]))
+        if mode == "forward":
+            self.forward_generation = self.generation
         return energy, grad
 
 
 def energy_function():
     """torch.autograd.Function computing E(theta) per batch member; backward
-    runs the adjoint reverse sweep (one sweep for all parameters)."""
+    runs the adjoint reverse sweep (one sweep for all parameters).
+
+    The sweep continues from the forward state left in the engine's work
+    buffer. Each forward records the engine's run counter; a backward whose
+    forward is no longer the engine's last run (another forward on the same
+    engine came in between, or an earlier backward already swept it, as with
+    retain_graph) runs the forward again from its saved parameters first, so
+    every backward sweeps the state of its own forward."""
     import torch
 
     class _Energy(torch.autograd.Function):
@@ -426,13 +443,17 @@ def energy_function():
         def forward(ctx, params, engine):
             energy, _ = engine.run(params, mode="forward")
             ctx.engine = engine
+            ctx.generation = engine.generation
             ctx.save_for_backward(params)
             return energy
 
         @staticmethod
         def backward(ctx, g_energy):
             (params,) = ctx.saved_tensors
-            _, grad = ctx.engine.run(params, mode="sweep")
+            eng = ctx.engine
+            if eng.forward_generation is None or eng.forward_generation != ctx.generation:
+                eng.run(params, mode="forward")
+            _, grad = eng.run(params, mode="sweep")
             return g_energy[:, None] * grad, None
 
     return _Energy

@@ -79,6 +79,62 @@ def test_samples_match_oracle(qs, dtype, n):
     assert not np.any(np.abs(psi[got.astype(np.int64)]) == 0)
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_samples_with_zero_probability_tail(qs, dtype):
+    """The last blocks of 4096 amplitudes have zero probability and the
+    uniforms come close to 1: every sample is an outcome of nonzero
+    probability (the last one for u -> 1). Device uniforms outside [0, 1) are
+    clamped (below 0 -> the first such outcome; 1, above 1 or NaN -> the last);
+    host uniforms outside [0, 1) are rejected."""
+    import torch
+    n = 14
+    psi0 = qi.random_state(n, 91)
+    psi0[:5] = 0
+    psi0[2 * 4096 + 123:] = 0
+    psi0 /= np.linalg.norm(psi0)
+    st = qs.State(n, dtype=dtype).set(psi0)
+    psi = np.ascontiguousarray(st.get().astype(np.complex128))
+    nz = np.flatnonzero(np.abs(psi) > 0)
+    u = np.array([np.nextafter(1.0, 0.0), 1.0 - 1e-12, 1.0 - 1e-9, 0.0, 0.5])
+    got = st.sample(u)
+    check_samples(psi, n, u, got)
+    assert np.all(np.abs(psi[got.astype(np.int64)]) > 0)
+    assert int(got[0]) == nz[-1] and int(got[3]) == nz[0]
+    ud = torch.tensor([-0.5, 1.0, 1.5, float("nan"), np.nextafter(1.0, 0.0)], dtype=torch.float64, device="cuda")
+    dev = st.sample(ud).cpu().numpy()
+    assert list(dev[:4]) == [nz[0], nz[-1], nz[-1], nz[-1]] and dev[4] == nz[-1]
+    for bad in (-0.5, 1.0, float("nan")):
+        with pytest.raises(qs.QsimError):
+            st.sample(np.array([0.5, bad]))
+
+
+def test_marginals_full_size_ghz_and_basis(qs):
+    """n = 28 complex64 (long per-thread runs, capped parts): a basis state's
+    group marginal is one-hot at the group's bits of x, and GHZ's is 1/2 at
+    all-zeros and all-ones, for groups with index bits below and above bit 8."""
+    n = 28
+    groups = [[n - 1 - b for b in (0, 3, 8, 9, 20, 27)], [n - 1 - b for b in range(2, 14)], [n - 1 - 8],
+              [n - 1 - b for b in (27, 7, 8)]]
+    st = qs.State(n, dtype="c64")
+    x = int(qi.rng(33).integers(0, 1 << n))
+    st.init_basis(x)
+    for g in groups:
+        got = st.marginal_probabilities(g)
+        y = 0
+        for q in g:
+            y = (y << 1) | ((x >> (n - 1 - q)) & 1)
+        want = np.zeros(1 << len(g))
+        want[y] = 1.0
+        assert np.max(np.abs(got - want)) < 1e-6, g
+    ghz = [qi.Gate("H", (0,))] + [qi.Gate("X", (q,), (q - 1,)) for q in range(1, n)]
+    st.init_basis(0).apply(ghz)
+    for g in groups:
+        got = st.marginal_probabilities(g)
+        want = np.zeros(1 << len(g))
+        want[0] = want[-1] = 0.5
+        assert np.max(np.abs(got - want)) < 1e-6, g
+
+
 def test_samples_device_tensors_equal_host(qs):
     import torch
     n = 16

@@ -150,7 +150,7 @@ def test_adiabatic_evolution(qs, dtype):
     h1 = qi.random_ising_terms(n, qi.rng(8))
     want = oracle.adiabatic_evolve(oracle.plus_state(n), n, h0, h1, T, dt)
     st = qs.State(n, dtype=dtype).init_plus().adiabatic_evolve(h0, h1, T, dt)
-    close(st.get(), want, dtype, scale=10.0)   # 20 steps of merged diagonals
+    close(st.get(), want, dtype)
 
 
 def test_trotter_rejects_unsupported_terms(qs):
@@ -268,3 +268,25 @@ def test_tiled_batch_of_states(qs, dtype):
     got = st.get()
     for b in range(B):
         close(got[b], oracle.apply_circuit(psis[b].copy(), n, gates), dtype)
+
+
+def test_largest_batch_read_outs(qs):
+    """batch = 65535, the largest a handle accepts (the member is a grid
+    dimension): norm, probabilities, expectation and group marginals of every
+    member against the oracle's definitions; 65536 is rejected."""
+    n, batch = 1, 65535
+    r = qi.rng(23)
+    psis = r.normal(size=(batch, 2)) + 1j * r.normal(size=(batch, 2))
+    psis /= np.linalg.norm(psis, axis=1, keepdims=True)
+    st = qs.State(n, batch=batch, dtype="c128").set(psis)
+    p = np.abs(psis) ** 2
+    np.testing.assert_allclose(st.norm2(), p.sum(axis=1), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(st.probabilities(), p, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(st.marginal_probabilities([0]), p, rtol=0, atol=1e-15)
+    terms = [(0.7, 1, 0), (-0.4, 0, 1), (0.25, 1, 1)]
+    e = st.expectation(terms)
+    for b in range(0, batch, 4099):
+        assert abs(e[b] - oracle.expectation(np.ascontiguousarray(psis[b]), n, terms)) < 1e-12
+    with pytest.raises(qs.QsimError) as ex:
+        qs.State(n, batch=batch + 1, dtype="c128")
+    assert ex.value.status == 1

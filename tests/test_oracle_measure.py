@@ -74,6 +74,9 @@ def test_sample_is_monotone_and_skips_zero_probability():
     assert np.all(np.diff(x.astype(np.int64)) >= 0)
     assert not set(x.tolist()) & {0, 1, 7, 30, 31}
     assert oracle.sample(psi, n, [0.0])[0] == 2  # the first outcome with probability > 0
+    # u just below 1 (the target can round to the total): the last outcome
+    # with probability > 0, never the zero-probability tail
+    assert oracle.sample(psi, n, [np.nextafter(1.0, 0.0)])[0] == 29
 
 
 def test_sample_chi_squared():

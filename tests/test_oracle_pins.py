@@ -446,3 +446,20 @@ def test_fused_matrix_is_product_of_kronecker_operators():
     a = oracle.apply_circuit(psi.copy(), n, gates)
     b = oracle.apply_matrix(psi.copy(), n, qubits, U)
     assert np.max(np.abs(a - b)) < 1e-13
+
+
+def test_gate_loop_threads_do_not_change_the_result():
+    """The CPU baseline's all-cores run splits the gate loop over index groups
+    across threads; every group is one thread's, so the state is bit-identical
+    to the single-threaded loop."""
+    n = 12
+    gates = qi.random_mixed_circuit(n, 40, seed=71, max_controls=2, max_unitary_k=3)
+    psi0 = qi.random_state(n, 72)
+    one = oracle.apply_circuit(psi0.copy(), n, gates)
+    used = oracle.set_threads(4)
+    try:
+        many = oracle.apply_circuit(psi0.copy(), n, gates)
+    finally:
+        oracle.set_threads(1)
+    assert used >= 1
+    assert np.array_equal(one, many)
