@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--mode", default="auto", choices=["auto", "unfused", "tiled", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-jit", action="store_true",
+                    help="run every tiled pass on the generic kernel (no specialised pass kernels)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the secondary workloads (variational adjoint)")
     ap.add_argument("--only", default=None, choices=sorted(SECONDARY),
@@ -275,9 +277,31 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------------ secondary workloads
-def _time_cuda(fn, steps: int, warmup: int = 2) -> float:
-    """Mean ms of fn() over `steps` calls, CUDA events on the current stream."""
+def specialise(fn, fold: bool = False):
+    """Run fn once with every new tiled pass structure queued for a
+    specialised kernel, wait for the compiles, and go back to the default
+    policy: later runs of passes of those structures use the specialised
+    kernels. fold: run it a second time, which queues kernels with the passes'
+    values compiled in as well (for a circuit that repeats with fixed angles)."""
+    from paper_2009_01845_gb300 import qsim
+    qsim.jit_set_policy("eager", fold=fold)
+    try:
+        fn()
+        qsim.jit_wait()
+        if fold:
+            fn()
+            qsim.jit_wait()
+    finally:
+        qsim.jit_set_policy("tiered")
+
+
+def _time_cuda(fn, steps: int, warmup: int = 2, jit: bool = True) -> float:
+    """Mean ms of fn() over `steps` calls, CUDA events on the current stream;
+    the warm-up specialises fn's tiled passes first unless jit is False."""
     import torch
+    if jit and warmup > 0:
+        specialise(fn)
+        warmup -= 1
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
@@ -327,8 +351,9 @@ def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
     """Adiabatic evolution batch: 64 instances, n ~ U{16..26} (seed 5), H0 = -sum X,
     H1 = sum J_ij Z_i Z_j + sum h_i Z_i with J, h ~ N(0, 1), linear schedule,
     T = 10, dt = 0.01, |+>^n. Timed on the first `steps` of the 1000 steps
-    (each step costs the same), grouped by width into one batched call per width
-    ("batched"), and instance by instance ("sequential"). Reports instance-steps/s;
+    (each step costs the same): all widths in one call, side by side on streams
+    of their own ("one_call"), one batched call per width in turn ("batched"),
+    and instance by instance ("sequential"). Reports instance-steps/s;
     also the final energy and the ground-state overlap of the smallest
     instance after all 1000 steps (ground state by brute force over 2^16)."""
     import numpy as np
@@ -347,6 +372,17 @@ def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
                                                          steps=steps)
 
     t_b = _time_cuda(batched, 1, warmup=1)
+    # every width in one call: the handles evolve side by side on their own streams
+    h0s = [inst[groups[w][0]][1] for w in widths]
+    h1s = [inst[i][2] for w in widths for i in groups[w]]
+    order = [states[w] for w in widths]
+
+    def one_call():
+        for st_ in order:
+            st_.init_plus()
+        qsim.adiabatic_run_batch(order, h0s, h1s, T, dt, steps=steps)
+
+    t_o = _time_cuda(one_call, 1, warmup=1)
     # device time by kernel class of one batched run (the rest of t_b is host work)
     qsim.profile_collect()
     qsim.profile_enable(True)
@@ -385,7 +421,9 @@ def adiabatic_batch(steps: int = 100, dtype: str = "c64") -> dict:
     isteps = 64 * steps
     return {"workload": f"adiabatic batch: 64 instances n in [16,26] (seed 5), T=10, dt=0.01, {dtype}, "
                         f"first {steps} of 1000 second-order Trotter steps timed",
-            "batched_ms": t_b, "sequential_ms": t_s,
+            "one_call_ms": t_o, "batched_ms": t_b, "sequential_ms": t_s,
+            "instance_steps_per_s_one_call": isteps / (t_o / 1000.0),
+            "one_call_hbm_frac": alg_bytes / (t_o / 1000.0) / 1e9 / bw,
             "instance_steps_per_s_batched": isteps / (t_b / 1000.0),
             "instance_steps_per_s_sequential": isteps / (t_s / 1000.0),
             "projected_full_run_s_batched": t_b / 1000.0 * 1000 / steps,
@@ -576,6 +614,7 @@ def summary(line: dict) -> dict:
 
     sec = line.get("secondary", {})
     out = {"gate_per_s": rnd(line["value"]), "ms_per_step": rnd(line["ms_per_step"]),
+           "pass_kernels": get(line, "pass_kernels", "timed_region"),
            "tiled_hbm_frac": rnd(get(line, "roofline", "frac"), 3),
            "tiled_alu_frac": rnd(get(line, "roofline", "alu", "frac"), 3),
            "e2e_gate_per_s": rnd(get(line, "e2e", "value")),
@@ -586,10 +625,11 @@ def summary(line: dict) -> dict:
         out["adjoint"] = {"fwd_ms": rnd(va["forward_ms"]), "full_ms": rnd(va["forward_plus_adjoint_ms"]),
                           "adj_incl_hpsi_over_fwd": rnd(va["adjoint_incl_hpsi_over_forward"], 3),
                           "total_over_fwd": rnd(va["total_over_forward"], 3)}
-    ab = sec.get("adiabatic_batch")
-    if ab:
-        out["adiabatic"] = {k: rnd(v) for k, v in ab.items() if k.startswith("instance_steps") or
-                            k.endswith("hbm_frac")}
+    for key, name in (("adiabatic_batch", "adiabatic"), ("adiabatic_batch_c128", "adiabatic_c128")):
+        ab = sec.get(key)
+        if ab:
+            out[name] = {k: rnd(v) for k, v in ab.items() if k.startswith("instance_steps") or
+                         k.endswith("hbm_frac")}
     ft = sec.get("fused_tc")
     if ft:
         out["fused_tc"] = {"fused_gate_per_s": rnd(get(ft, "fused", "gate_apps_per_s")),
@@ -675,9 +715,17 @@ def run_ours(a):
         qsim._check(st.lib.qs_norm2(st.handle, ctypes.c_void_p(out_n.ctypes.data)))
         qsim._check(st.lib.qs_expectation(st.handle, zz_arr, zz_n, ctypes.c_void_p(out_re.ctypes.data), None))
 
-    for _ in range(a.warmup):
-        step()
+    # warm-up: the first step queues a specialised kernel for every tiled pass
+    # and waits for the compiles; the rest run as the timed steps do
+    if a.no_jit:
+        qsim.jit_set_policy("off")
+    for i in range(a.warmup):
+        if i == 0 and not a.no_jit:
+            specialise(step, fold=True)  # the step repeats one circuit with fixed angles
+        else:
+            step()
     torch.cuda.synchronize()
+    jit_after_warmup = qsim.jit_stats()
     if abs(out_n[0] - 1.0) > 1e-3:
         raise RuntimeError(f"norm drifted: {out_n[0]}")
 
@@ -698,6 +746,8 @@ def run_ours(a):
     clk = clocks.stop()
     qsim.profile_enable(False)
     prof = qsim.profile_collect()
+    jit_timed = {k: v - jit_after_warmup[k] for k, v in qsim.jit_stats().items()
+                 if k in ("specialised_launches", "generic_launches")}
     ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, world)
     value = whole_job_value(world, len(gates), ms)
 
@@ -751,6 +801,10 @@ def run_ours(a):
                                 "GB_per_step": v[2] / a.steps / 1e9, "GFLOP_per_step": v[3] / a.steps / 1e9}
                             for k, v in prof.items() if v[1]},
                 "energy_zz": float(out_re[0]), "norm2": float(out_n[0]),
+                "pass_kernels": {"timed_region": jit_timed,
+                                 "compiled": jit_after_warmup["compiled"],
+                                 "compile_seconds": jit_after_warmup["compile_seconds"],
+                                 "failed": jit_after_warmup["failed"]},
                 "secondary": secondary}
         # the key figures once more, last, so that a truncated log keeps them
         line["summary"] = summary(line)
@@ -809,6 +863,7 @@ def measurement(n: int = 32, reps: int = 3) -> dict:
 SECONDARY = {
     "variational_adjoint": lambda: variational_adjoint(),
     "adiabatic_batch": lambda: adiabatic_batch(),
+    "adiabatic_batch_c128": lambda: adiabatic_batch(steps=50, dtype="c128"),
     "fused_tc": lambda: fused_tc(),
     "unfused_passes": lambda: unfused_passes(),
     "qft_n18_c128": lambda: qft_n18(),

@@ -322,6 +322,109 @@ qs_status qs_profile_collect(double *total_ms, long long *launches, double *byte
 const char *qs_profile_class_name(int c);
 int qs_profile_class_count(void);
 
+/* Adiabatic evolution of instances of different widths in one call (Sec. 2.6,
+   Eq. (4)): handle i holds states[i]->batch instances of its own width, all
+   handles of one dtype on one device, none sharing memory. Handle i's members
+   share H0 = the h0_counts[i] terms of h0 that follow handle i-1's; member j,
+   counted over all handles in order, has its own H1 = the h1_counts[j] terms
+   of h1 that follow member j-1's. Schedule, splitting, step count and the
+   restrictions on the terms are those of qs_adiabatic_evolve_batch, per
+   handle. The handles evolve side by side on streams of their own, forked
+   from states[0]'s stream (after each handle's own earlier work) and joined
+   back into states[0]'s stream and each handle's own; steps are enqueued in
+   chunks of 10 per handle in turn, so every width has work on the GPU from
+   the start. Chunks close and reopen their half-step diagonals (the GPU merges
+   them only inside a chunk), which changes only rounding. Asynchronous. */
+qs_status qs_adiabatic_run_batch(qs_state *const *states, int n_states, const qs_pauli_term *h0,
+                                 const size_t *h0_counts, const qs_pauli_term *h1, const size_t *h1_counts,
+                                 double T, double dt, int steps);
+
+/* ---------------------------------------------------------------- density matrices */
+/* Density matrices and noise channels (Sec. 2.4, "Density matrices and
+   noise"). A density matrix rho of n qubits (1 <= n <= 20) is a handle of
+   2n qubits holding the 4^n entries of rho row-major: entry (r, c) at index
+   r 2^n + c (per batch member, 4^n entries each), r and c basis integers with
+   qubit 0 the most significant bit. qs_state_get/qs_state_set move those
+   entries. On a density handle:
+     - qs_state_init_basis(x) sets |x><x| (x < 2^n); qs_state_init_plus sets
+       |+><+| (every entry 2^-n);
+     - qs_apply_gates applies rho -> U rho U^dag for every gate U (qubits in
+       [0, n)): U on the row qubits and its complex conjugate on the column
+       qubits, on the ordinary gate kernels (any mode);
+     - qs_probabilities returns the diagonal (batch * 2^n doubles), and
+       qs_expectation Tr(rho H) (FP64 accumulation; Im ~ 0 for Hermitian rho);
+     - qs_norm2 returns sum |rho_rc|^2 = Tr(rho^2), the purity;
+     - batched parameters, measurements (marginals, samples), Trotter
+       evolution, gradients and plans are not supported (QS_ERR_UNSUPPORTED). */
+qs_status qs_density_create(int n, int batch, qs_dtype dtype, void *cuda_stream, qs_state **out);
+/* Wrap caller-owned device memory of batch * 4^n amplitudes (16-byte aligned). */
+qs_status qs_density_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *cuda_stream, qs_state **out);
+/* rho_b = |psi_b><psi_b| from batch * 2^n amplitudes of the handle's dtype,
+   host (on_device = 0; the call synchronises) or device memory. */
+qs_status qs_density_init_pure(qs_state *s, const void *psi, int on_device);
+/* Tr(rho_b) per member (FP64); out: host, batch doubles. */
+qs_status qs_density_trace(qs_state *s, double *out);
+
+/* A quantum channel in Kraus form on one or two qubits: rho -> sum_i K_i rho
+   K_i^dag. kraus: host pointer to n_kraus matrices of 2^k x 2^k complex128
+   (interleaved, row-major, local index as for gates: targets[0] the most
+   significant bit), read during the call; sum_i K_i^dag K_i must equal the
+   identity within 1e-8 (trace preserving), else QS_ERR_ARG. */
+typedef struct qs_channel {
+    int32_t n_targets;     /* 1 or 2 */
+    int32_t targets[2];    /* distinct qubits in [0, n) */
+    int32_t n_kraus;       /* 1 .. 4^n_targets */
+    const double *kraus;
+} qs_channel;
+/* Apply channels in order to every member of a density handle (anything
+   else: QS_ERR_ARG). Each channel runs as one superoperator sum_i K_i (x)
+   conj(K_i) on the row and column copies of its targets (a 4 x 4 or 16 x 16
+   matrix on the 2n-qubit vector), on the ordinary gate kernels. opts as in
+   qs_apply_gates. */
+qs_status qs_apply_channels(qs_state *s, const qs_channel *channels, size_t count, const qs_opts *opts);
+
+/* ---------------------------------------------------------------- pass specialisation */
+/* Run-time specialisation of the tiled passes (no counterpart in the paper).
+   A tiled pass is first run by a generic kernel that decodes its ops at run
+   time; a kernel specialised for the pass's structure (its ops, bits and
+   stage maps compiled in with NVRTC for the device; its angles and matrix
+   entries passed as parameters) computes the same result with far fewer
+   instructions. Kernels are cached per pass structure for the process, so
+   passes that differ only in their values share one (e.g. the steps of a
+   Trotter evolution). The policy says when a structure gets a kernel:
+   QS_JIT_OFF never; QS_JIT_TIERED (default) in the background once it is
+   launched a second time; QS_JIT_EAGER in the background at its first
+   launch; QS_JIT_SYNC before its first launch (the launching call waits for
+   the compile). Until a kernel is ready the generic kernel runs the pass, so
+   results never wait on a compile except under QS_JIT_SYNC. qs_plan_create
+   with autotuning specialises the passes in its timing runs, before it
+   captures them (unless the policy is QS_JIT_OFF); a plan captures whichever
+   kernels are ready. With QS_JIT_FOLD or-ed into the policy, a pass launched
+   a second time with the same values also gets a kernel with its values
+   compiled in (a few percent faster, e.g. for a circuit run many times with
+   fixed angles; queued in the background; one kernel per set of values). The
+   environment variable QSIM_JIT = off, tiered, eager or sync (with "+fold"
+   appended for QS_JIT_FOLD) sets the initial policy. Process-wide. */
+#define QS_JIT_OFF 0
+#define QS_JIT_TIERED 1
+#define QS_JIT_EAGER 2
+#define QS_JIT_SYNC 3
+#define QS_JIT_FOLD 8
+qs_status qs_jit_set_policy(int policy);
+/* Block until every queued background compile has finished. */
+qs_status qs_jit_wait(void);
+/* Drop the queued compiles that have not started (their passes stay on the
+   generic kernel until queued again) and wait for the ones in progress. A
+   program that exits while a compile runs should call this (or qs_jit_wait)
+   first; the library also waits for them at exit. */
+qs_status qs_jit_cancel(void);
+/* Counters since the process started: tiled passes launched on specialised
+   and on generic kernels, kernels compiled, compiles (or loads) that failed
+   (their passes stay on the generic kernel), and seconds spent compiling
+   (summed over threads). NULL outputs are skipped. */
+qs_status qs_jit_stats(long long *specialised_launches, long long *generic_launches, long long *compiled,
+                       long long *failed, double *compile_seconds);
+
 /* Batched adiabatic evolution (Sec. 2.6, Eq. (4)) of a batch whose members have
    their own H1: member b uses the h1_counts[b] terms that follow member b-1's in
    `h1`; H0 is shared. Same schedule, splitting and step count as

@@ -127,6 +127,42 @@ qs_status qs_state_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *s
     QS_GUARD_END
 }
 
+static qs_status check_density_n(int n) {
+    if (n < 1 || 2 * n > QS_MAX_QUBITS) {
+        set_error("density matrix of n = %d qubits: 1 <= n <= %d", n, QS_MAX_QUBITS / 2);
+        return QS_ERR_ARG;
+    }
+    return QS_OK;
+}
+
+qs_status qs_density_create(int n, int batch, qs_dtype dtype, void *stream, qs_state **out) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_density_n(n));
+    QS_TRY(qs_state_create(2 * n, batch, dtype, stream, out));
+    (*out)->dm = n;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_density_wrap(int n, int batch, qs_dtype dtype, void *dev_ptr, void *stream, qs_state **out) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_density_n(n));
+    QS_TRY(qs_state_wrap(2 * n, batch, dtype, dev_ptr, stream, out));
+    (*out)->dm = n;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+static qs_status not_for_density(const qs_state *s, const char *what) {
+    if (s && s->dm) {
+        set_error("%s is not supported on a density matrix", what);
+        return QS_ERR_UNSUPPORTED;
+    }
+    return QS_OK;
+}
+
 qs_status qs_state_destroy(qs_state *s) {
     QS_GUARD_BEGIN
     if (!s) return QS_OK;
@@ -165,6 +201,13 @@ qs_status qs_state_init_basis(qs_state *s, uint64_t x) {
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(s));
+    if (s->dm) {  // |x><x|: entry (x, x)
+        if ((x >> s->dm) != 0) {
+            set_error("basis index %llu >= 2^%d", (unsigned long long)x, s->dm);
+            return QS_ERR_ARG;
+        }
+        return k_init_basis(s, x * ((1ull << s->dm) + 1ull));
+    }
     if (s->n < 64 && (x >> s->n) != 0) {
         set_error("basis index %llu >= 2^%d", (unsigned long long)x, s->n);
         return QS_ERR_ARG;
@@ -211,20 +254,53 @@ qs_status qs_state_get(const qs_state *s, void *dst, int on_device) {
     QS_GUARD_END
 }
 
+// flags of a lowered matrix (as lower_gate sets them)
+static void matrix_flags(LGate *g) {
+    const int K = 1 << g->k;
+    bool diag = true, phase = true;
+    for (int r = 0; r < K; ++r)
+        for (int c = 0; c < K; ++c) {
+            const cd v = g->m[r * K + c];
+            if (r != c && v != cd(0.0)) diag = false;
+            if (r == c && r != K - 1 && v != cd(1.0)) phase = false;
+        }
+    g->diagonal = diag;
+    g->phase_only = diag && phase;
+}
+
+// On a density matrix of dm qubits (a 2 dm-qubit vector, row qubit q = vector
+// qubit q, column qubit q = vector qubit dm + q), U rho U^dag is U on the row
+// bits (index bits dm .. 2 dm - 1) and conj(U) on the column bits.
+static void density_pair(int dm, const LGate &g, LGate *row, LGate *col) {
+    *row = g;
+    for (int j = 0; j < g.k; ++j) row->tbit[j] = g.tbit[j] + dm;
+    row->cmask = g.cmask << dm;
+    *col = g;
+    for (auto &v : col->m) v = std::conj(v);
+    col->kind = QS_GATE_UNITARY;
+    matrix_flags(col);
+}
+
 static qs_status lower_all(const qs_state *s, const qs_gate *gates, size_t count, std::vector<LGate> *out) {
     if (count && !gates) {
         set_error("null gate array");
         return QS_ERR_ARG;
     }
+    const int n = s->dm ? s->dm : s->n;
     out->resize(count);
     for (size_t i = 0; i < count; ++i) {
-        qs_status st = lower_gate(s->n, gates[i], &(*out)[i]);
+        qs_status st = lower_gate(n, gates[i], &(*out)[i]);
         if (st != QS_OK) {
             char buf[512];
             std::snprintf(buf, sizeof(buf), "gate %zu: %s", i, qs_last_error());
             set_error("%s", buf);
             return st;
         }
+    }
+    if (s->dm) {
+        std::vector<LGate> both(2 * count);
+        for (size_t i = 0; i < count; ++i) density_pair(s->dm, (*out)[i], &both[2 * i], &both[2 * i + 1]);
+        out->swap(both);
     }
     return QS_OK;
 }
@@ -261,6 +337,7 @@ qs_status qs_apply_gates_batched(qs_state *s, const qs_gate *gates, size_t count
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(s));
+    QS_TRY(not_for_density(s, "batched parameters"));
     int mode;
     QS_TRY(check_opts(opts, &mode));
     std::vector<LGate> lg;
@@ -296,11 +373,12 @@ qs_status qs_probabilities(qs_state *s, double *out, int on_device) {
         set_error("null output");
         return QS_ERR_ARG;
     }
-    if (on_device) return k_probabilities(s, out);
-    const size_t total = (size_t)s->batch << s->n;
+    auto probs = [&](double *dst) { return s->dm ? k_dm_probabilities(s, dst) : k_probabilities(s, dst); };
+    if (on_device) return probs(out);
+    const size_t total = (size_t)s->batch << (s->dm ? s->dm : s->n);
     double *tmp = nullptr;
     QS_CUDA_TRY(cudaMallocAsync(&tmp, total * sizeof(double), s->stream));
-    qs_status st = k_probabilities(s, tmp);
+    qs_status st = probs(tmp);
     if (st == QS_OK) st = read_back(s, tmp, out, total);
     cudaFreeAsync(tmp, s->stream);
     return st;
@@ -311,6 +389,7 @@ qs_status qs_marginal_probabilities(qs_state *s, const int *qubits, int m, doubl
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(s));
+    QS_TRY(not_for_density(s, "marginal probabilities"));
     if (!out || !qubits) {
         set_error("null argument");
         return QS_ERR_ARG;
@@ -345,6 +424,7 @@ qs_status qs_sample(qs_state *s, int member, const double *uniforms, size_t shot
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(s));
+    QS_TRY(not_for_density(s, "sampling"));
     if (member < 0 || member >= s->batch) {
         set_error("member %d outside the batch of %d", member, s->batch);
         return QS_ERR_ARG;
@@ -401,8 +481,9 @@ static qs_status check_terms(const qs_state *s, const qs_pauli_term *t, size_t c
         set_error("null term array");
         return QS_ERR_ARG;
     }
+    const int n = s->dm ? s->dm : s->n;
     for (size_t i = 0; i < count; ++i) {
-        if (s->n < 64 && ((t[i].x_mask | t[i].z_mask) >> s->n) != 0) {
+        if (n < 64 && ((t[i].x_mask | t[i].z_mask) >> n) != 0) {
             set_error("term %zu names a qubit >= n", i);
             return QS_ERR_ARG;
         }
@@ -425,7 +506,10 @@ qs_status qs_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, 
     QS_TRY(check_terms(s, terms, count));
     QS_TRY(ensure_host_pinned(s, (size_t)2 * s->batch));
     double *dev = nullptr;
-    QS_TRY(k_expectation(s, terms, count, &dev));
+    if (s->dm)
+        QS_TRY(k_dm_expectation(s, terms, count, &dev));
+    else
+        QS_TRY(k_expectation(s, terms, count, &dev));
     QS_TRY(read_back(s, dev, s->host_pinned, 2 * (size_t)s->batch));
     for (int b = 0; b < s->batch; ++b) {
         out_re[b] = s->host_pinned[2 * b];
@@ -441,6 +525,7 @@ qs_status qs_energy_gradient(qs_state *w, const qs_gate *gates, size_t count, co
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(w));
+    QS_TRY(not_for_density(w, "the adjoint gradient"));
     if (w->n < 2) {
         set_error("the work handle needs n + 1 >= 2 qubits");
         return QS_ERR_ARG;
@@ -493,6 +578,7 @@ qs_status qs_trotter_step(qs_state *s, const qs_pauli_term *h0, size_t n_h0, con
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(s));
+    QS_TRY(not_for_density(s, "Trotter evolution"));
     QS_TRY(check_terms(s, h0, n_h0));
     QS_TRY(check_terms(s, h1, n_h1));
     if (!std::isfinite(s_val) || !std::isfinite(dt)) {
@@ -508,6 +594,7 @@ qs_status qs_adiabatic_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(s));
+    QS_TRY(not_for_density(s, "Trotter evolution"));
     QS_TRY(check_terms(s, h0, n_h0));
     QS_TRY(check_terms(s, h1, n_h1));
     if (!(T > 0) || !(dt > 0) || !std::isfinite(T) || !std::isfinite(dt)) {
@@ -530,6 +617,7 @@ qs_status qs_adiabatic_evolve_batch(qs_state *s, const qs_pauli_term *h0, size_t
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(s));
+    QS_TRY(not_for_density(s, "Trotter evolution"));
     if (!h1_counts) {
         set_error("null h1_counts");
         return QS_ERR_ARG;
@@ -550,6 +638,191 @@ qs_status qs_adiabatic_evolve_batch(qs_state *s, const qs_pauli_term *h0, size_t
     const long run = steps < 0 ? K : std::min<long>(K, steps);
     if (run == 0) return QS_OK;
     return run_adiabatic_batch(s, h0, n_h0, h1, off.data(), dt, T, (int)run);
+    QS_GUARD_END
+}
+
+
+qs_status qs_adiabatic_run_batch(qs_state *const *states, int n_states, const qs_pauli_term *h0,
+                                 const size_t *h0_counts, const qs_pauli_term *h1, const size_t *h1_counts, double T,
+                                 double dt, int steps) {
+    QS_GUARD_BEGIN
+    clear_error();
+    if (n_states < 1 || !states || !h0_counts || !h1_counts) {
+        set_error("need at least one state handle and the term counts");
+        return QS_ERR_ARG;
+    }
+    std::vector<size_t> h0_off(n_states + 1, 0);
+    std::vector<size_t> h1_off(1, 0);
+    for (int i = 0; i < n_states; ++i) {
+        qs_state *s = states[i];
+        QS_TRY(check_state(s));
+        QS_TRY(not_for_density(s, "Trotter evolution"));
+        if (s->dtype != states[0]->dtype || s->device != states[0]->device) {
+            set_error("handle %d: every handle needs the dtype and device of handle 0", i);
+            return QS_ERR_ARG;
+        }
+        for (int j = 0; j < i; ++j)
+            if (states[j] == s || states[j]->data == s->data) {
+                set_error("handles %d and %d share their amplitudes", j, i);
+                return QS_ERR_ARG;
+            }
+        h0_off[i + 1] = h0_off[i] + h0_counts[i];
+        QS_TRY(check_terms(s, h0 + h0_off[i], h0_counts[i]));
+        for (int b = 0; b < s->batch; ++b) {
+            const size_t m = h1_off.size() - 1;
+            h1_off.push_back(h1_off[m] + h1_counts[m]);
+            QS_TRY(check_terms(s, h1 + h1_off[m], h1_counts[m]));
+        }
+    }
+    if ((h0_off[n_states] && !h0) || (h1_off.back() && !h1)) {
+        set_error("null term array");
+        return QS_ERR_ARG;
+    }
+    if (!(T > 0) || !(dt > 0) || !std::isfinite(T) || !std::isfinite(dt)) {
+        set_error("T and dt must be positive and finite");
+        return QS_ERR_ARG;
+    }
+    const long K = std::lround(T / dt);
+    if (K < 1 || K > (1l << 30)) {
+        set_error("T/dt gives %ld steps", K);
+        return QS_ERR_ARG;
+    }
+    const long run = steps < 0 ? K : std::min<long>(K, steps);
+    if (run == 0) return QS_OK;
+    return run_adiabatic_multi(states, n_states, h0, h0_off.data(), h1, h1_off.data(), dt, T, (int)run, 10);
+    QS_GUARD_END
+}
+
+qs_status qs_density_init_pure(qs_state *s, const void *psi, int on_device) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!s->dm) {
+        set_error("not a density matrix");
+        return QS_ERR_ARG;
+    }
+    if (!psi) {
+        set_error("null state");
+        return QS_ERR_ARG;
+    }
+    if (on_device) return k_dm_init_pure(s, psi);
+    const size_t bytes = ((size_t)s->batch << s->dm) * (s->dtype == QS_C64 ? 8 : 16);
+    void *tmp = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync(&tmp, bytes, s->stream));
+    qs_status st = QS_OK;
+    const cudaError_t e = cudaMemcpyAsync(tmp, psi, bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) st = cuda_status(e, "state copy");
+    if (st == QS_OK) st = k_dm_init_pure(s, tmp);
+    cudaFreeAsync(tmp, s->stream);
+    if (st == QS_OK) QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return st;
+    QS_GUARD_END
+}
+
+qs_status qs_density_trace(qs_state *s, double *out) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!s->dm || !out) {
+        set_error(!out ? "null output" : "not a density matrix");
+        return QS_ERR_ARG;
+    }
+    QS_TRY(ensure_host_pinned(s, (size_t)s->batch));
+    double *dev = nullptr;
+    QS_TRY(k_dm_trace(s, &dev));
+    QS_TRY(read_back(s, dev, s->host_pinned, s->batch));
+    std::memcpy(out, s->host_pinned, sizeof(double) * s->batch);
+    return QS_OK;
+    QS_GUARD_END
+}
+
+// The superoperator of a channel on the vector of rho: targets first on the
+// row bits, then on the column bits; S[(r1, c1), (r2, c2)] = sum_i
+// K_i[r1, r2] conj(K_i[c1, c2]).
+static qs_status lower_channel(const qs_state *s, const qs_channel &ch, LGate *out) {
+    const int dm = s->dm, k = ch.n_targets;
+    if (k < 1 || k > 2) {
+        set_error("a channel acts on 1 or 2 qubits (got %d)", k);
+        return QS_ERR_ARG;
+    }
+    const int K = 1 << k;
+    if (ch.n_kraus < 1 || ch.n_kraus > K * K || !ch.kraus) {
+        set_error("a channel needs 1 to %d Kraus operators", K * K);
+        return QS_ERR_ARG;
+    }
+    for (int j = 0; j < k; ++j)
+        if (ch.targets[j] < 0 || ch.targets[j] >= dm || (j == 1 && ch.targets[1] == ch.targets[0])) {
+            set_error("channel target %d out of range or repeated", ch.targets[j]);
+            return QS_ERR_ARG;
+        }
+    std::vector<cd> kr((size_t)ch.n_kraus * K * K);
+    for (size_t i = 0; i < kr.size(); ++i) {
+        if (!std::isfinite(ch.kraus[2 * i]) || !std::isfinite(ch.kraus[2 * i + 1])) {
+            set_error("non-finite Kraus entry");
+            return QS_ERR_ARG;
+        }
+        kr[i] = cd(ch.kraus[2 * i], ch.kraus[2 * i + 1]);
+    }
+    for (int a = 0; a < K; ++a)  // sum_i K_i^dag K_i = I
+        for (int b = 0; b < K; ++b) {
+            cd acc = 0.0;
+            for (int i = 0; i < ch.n_kraus; ++i)
+                for (int r = 0; r < K; ++r)
+                    acc += std::conj(kr[((size_t)i * K + r) * K + a]) * kr[((size_t)i * K + r) * K + b];
+            if (std::abs(acc - cd(a == b ? 1.0 : 0.0)) > 1e-8) {
+                set_error("Kraus operators are not trace preserving (sum K^dag K differs from I by %g)",
+                          std::abs(acc - cd(a == b ? 1.0 : 0.0)));
+                return QS_ERR_ARG;
+            }
+        }
+    const int K2 = K * K;
+    out->k = 2 * k;
+    for (int j = 0; j < k; ++j) {
+        out->tbit[j] = dm - 1 - ch.targets[j] + dm;  // row copy
+        out->tbit[k + j] = dm - 1 - ch.targets[j];    // column copy
+    }
+    out->cmask = 0;
+    out->kind = QS_GATE_UNITARY;
+    out->param_index = -1;
+    out->m.assign((size_t)K2 * K2, cd(0.0));
+    for (int i = 0; i < ch.n_kraus; ++i) {
+        const cd *Ki = &kr[(size_t)i * K * K];
+        for (int r1 = 0; r1 < K; ++r1)
+            for (int c1 = 0; c1 < K; ++c1)
+                for (int r2 = 0; r2 < K; ++r2)
+                    for (int c2 = 0; c2 < K; ++c2)
+                        out->m[(size_t)(r1 * K + c1) * K2 + (r2 * K + c2)] += Ki[r1 * K + r2] * std::conj(Ki[c1 * K + c2]);
+    }
+    matrix_flags(out);
+    out->is_swap = false;
+    return QS_OK;
+}
+
+qs_status qs_apply_channels(qs_state *s, const qs_channel *channels, size_t count, const qs_opts *opts) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    if (!s->dm) {
+        set_error("channels act on density matrices (qs_density_create)");
+        return QS_ERR_ARG;
+    }
+    if (count && !channels) {
+        set_error("null channel array");
+        return QS_ERR_ARG;
+    }
+    int mode;
+    QS_TRY(check_opts(opts, &mode));
+    std::vector<LGate> lg(count);
+    for (size_t i = 0; i < count; ++i) {
+        const qs_status st = lower_channel(s, channels[i], &lg[i]);
+        if (st != QS_OK) {
+            char buf[512];
+            std::snprintf(buf, sizeof(buf), "channel %zu: %s", i, qs_last_error());
+            set_error("%s", buf);
+            return st;
+        }
+    }
+    return run_gates(s, lg, mode, opts, nullptr, 0);
     QS_GUARD_END
 }
 

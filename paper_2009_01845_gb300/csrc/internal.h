@@ -39,6 +39,9 @@ struct qs_state {
     // per-pass tables of the Ising op's tile-independent parts (see tiled.h)
     double *ithr = nullptr;
     size_t ithr_bytes = 0;
+    // density matrix of dm qubits (n = 2 dm: entry (r, c) at index r 2^dm + c);
+    // 0 for a state vector
+    int dm = 0;
 };
 
 namespace qsim {
@@ -128,6 +131,14 @@ qs_status k_param_table(qs_state *s, const std::vector<int> &pidx, const std::ve
 qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params_dev, int n_params,
                              double sign = 1.0);
 qs_status ensure_host_pinned(qs_state *s, size_t doubles);
+
+// density matrices (kernels_density.cu): rho = |psi><psi| from psi_dev (batch x
+// 2^dm amplitudes); the diagonal into out_dev (batch x 2^dm doubles); traces and
+// Tr(rho H) into the scratch (batch doubles; batch (re, im) pairs)
+qs_status k_dm_init_pure(qs_state *s, const void *psi_dev);
+qs_status k_dm_probabilities(qs_state *s, double *out_dev);
+qs_status k_dm_trace(qs_state *s, double **out_dev);
+qs_status k_dm_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, double **out_dev);
 
 // Trotter factors
 qs_status k_diagonal_evolution(qs_state *s, const std::vector<double> &coeff,

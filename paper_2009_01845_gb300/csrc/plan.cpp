@@ -192,14 +192,14 @@ qs_status run_trotter(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const q
 
 // Batched adiabatic evolution: member b evolves under its own H1 (terms
 // h1[off[b] .. off[b+1])). Every member's X terms must agree (one RX layer for
-// the batch); the Ising diagonals are per member.
-qs_status run_adiabatic_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
-                              const size_t *off, double dt, double T, int steps) {
+// the batch); the Ising diagonals are per member. Prepare validates the terms
+// and uploads the per-member Ising tables on the state's stream.
+static qs_status adiabatic_batch_prepare(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                                         const size_t *off, TrotterTerms *tt) {
     const int n = s->n;
     const size_t stride = (size_t)n * n + n + 1;
-    TrotterTerms tt;
-    QS_TRY(split_terms(n, h0, n_h0, &tt.d0, &tt.z0, &tt.a0));
-    if (!tt.d0.empty()) {
+    QS_TRY(split_terms(n, h0, n_h0, &tt->d0, &tt->z0, &tt->a0));
+    if (!tt->d0.empty()) {
         set_error("batched evolution needs an H0 without Z terms");
         return QS_ERR_UNSUPPORTED;
     }
@@ -214,13 +214,13 @@ qs_status run_adiabatic_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
         std::vector<double> a;
         QS_TRY(split_terms(n, h1 + off[b], off[b + 1] - off[b], &d, &z, &a));
         if (b == 0) {
-            tt.a1 = a;
-            tt.d1 = d;  // only its emptiness is used below
-        } else if (a != tt.a1) {
+            tt->a1 = a;
+            tt->d1 = d;  // only its emptiness is used below
+        } else if (a != tt->a1) {
             set_error("member %d: X terms of H1 differ from member 0", b);
             return QS_ERR_UNSUPPORTED;
         }
-        if (!d.empty()) tt.d1.assign(1, 1.0);
+        if (!d.empty()) tt->d1.assign(1, 1.0);
         if (!ising_table(n, d, z, tables.data() + stride * b)) {
             set_error("member %d: H1 has a Z term on more than two qubits", b);
             return QS_ERR_UNSUPPORTED;
@@ -228,14 +228,98 @@ qs_status run_adiabatic_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
     }
     QS_TRY(ensure_itab(s, tables.size()));
     s->ising_stride = (uint32_t)stride;
+    // (a copy from pageable host memory has read the table when it returns)
     QS_CUDA_TRY(cudaMemcpyAsync(s->itab, tables.data(), tables.size() * sizeof(double), cudaMemcpyHostToDevice,
                                 s->stream));
+    return QS_OK;
+}
+
+// Steps k0 .. k1-1 of the K-step linear schedule (step k at s_k = (k + 1/2)
+// dt / T): inside the range adjacent half diagonals are merged; the range opens
+// with its first half step and closes with its last, so consecutive ranges
+// compose to the whole evolution (up to rounding).
+static qs_status adiabatic_batch_steps(qs_state *s, const TrotterTerms &tt, double dt, double T, int k0, int k1) {
     std::vector<double> taus, svals;
-    for (int k = 0; k < steps; ++k) svals.push_back((k + 0.5) * dt / T);
+    for (int k = k0; k < k1; ++k) svals.push_back((k + 0.5) * dt / T);
+    const int m = (int)svals.size();
     taus.push_back(0.5 * dt * svals[0]);
-    for (int k = 0; k + 1 < steps; ++k) taus.push_back(0.5 * dt * (svals[k] + svals[k + 1]));
-    taus.push_back(0.5 * dt * svals[steps - 1]);
+    for (int k = 0; k + 1 < m; ++k) taus.push_back(0.5 * dt * (svals[k] + svals[k + 1]));
+    taus.push_back(0.5 * dt * svals[m - 1]);
     return trotter_tiled(s, tt, taus, svals, dt);
+}
+
+qs_status run_adiabatic_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                              const size_t *off, double dt, double T, int steps) {
+    TrotterTerms tt;
+    QS_TRY(adiabatic_batch_prepare(s, h0, n_h0, h1, off, &tt));
+    return adiabatic_batch_steps(s, tt, dt, T, 0, steps);
+}
+
+// Instances of several widths: one handle per width, each evolved on a stream
+// of its own, forked from states[0]'s stream and joined back into it (and into
+// each handle's own stream). The steps are enqueued in chunks, round robin over
+// the handles, so every stream has work queued early and the GPU runs the
+// widths side by side (no stream's queue grows long enough to block the host).
+qs_status run_adiabatic_multi(qs_state *const *states, int n_states, const qs_pauli_term *h0,
+                              const size_t *h0_off, const qs_pauli_term *h1, const size_t *h1_off, double dt,
+                              double T, int steps, int chunk) {
+    std::vector<cudaStream_t> own(n_states), work(n_states, nullptr);
+    std::vector<cudaEvent_t> done(n_states, nullptr);
+    cudaEvent_t fork = nullptr;
+    for (int i = 0; i < n_states; ++i) own[i] = states[i]->stream;
+    auto cleanup = [&]() {
+        for (int i = 0; i < n_states; ++i) {
+            states[i]->stream = own[i];
+            if (work[i]) cudaStreamDestroy(work[i]);  // released once its work completes
+            if (done[i]) cudaEventDestroy(done[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+    };
+    qs_status st = QS_OK;
+    auto cuda = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && st == QS_OK) st = cuda_status(e, what);
+        return st == QS_OK;
+    };
+    if (!cuda(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event") ||
+        !cuda(cudaEventRecord(fork, own[0]), "fork")) {
+        cleanup();
+        return st;
+    }
+    for (int i = 0; i < n_states && st == QS_OK; ++i) {
+        if (!cuda(cudaStreamCreateWithFlags(&work[i], cudaStreamNonBlocking), "stream") ||
+            !cuda(cudaStreamWaitEvent(work[i], fork, 0), "fork wait"))
+            break;
+        // the handle's own earlier work comes first too
+        cudaEvent_t e = nullptr;
+        if (own[i] != own[0]) {
+            if (!cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event")) break;
+            cuda(cudaEventRecord(e, own[i]), "record");
+            cuda(cudaStreamWaitEvent(work[i], e, 0), "wait");
+            cudaEventDestroy(e);
+        }
+        states[i]->stream = work[i];
+    }
+    std::vector<TrotterTerms> tt(n_states);
+    size_t m0 = 0;  // first member of handle i among all members
+    for (int i = 0; i < n_states && st == QS_OK; ++i) {
+        std::vector<size_t> off(states[i]->batch + 1);
+        for (int b = 0; b <= states[i]->batch; ++b) off[b] = h1_off[m0 + b] - h1_off[m0];
+        st = adiabatic_batch_prepare(states[i], h0 + h0_off[i], h0_off[i + 1] - h0_off[i], h1 + h1_off[m0],
+                                     off.data(), &tt[i]);
+        m0 += states[i]->batch;
+    }
+    for (int k0 = 0; k0 < steps && st == QS_OK; k0 += chunk)
+        for (int i = 0; i < n_states && st == QS_OK; ++i)
+            st = adiabatic_batch_steps(states[i], tt[i], dt, T, k0, std::min(steps, k0 + chunk));
+    for (int i = 0; i < n_states && work[i]; ++i) {
+        if (!cuda(cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming), "event") ||
+            !cuda(cudaEventRecord(done[i], work[i]), "join"))
+            break;
+        cuda(cudaStreamWaitEvent(own[0], done[i], 0), "join wait");
+        if (own[i] != own[0]) cuda(cudaStreamWaitEvent(own[i], done[i], 0), "join wait");
+    }
+    cleanup();
+    return st;
 }
 
 }  // namespace qsim

@@ -42,6 +42,15 @@ qs_status trotter_queue(int n, const std::vector<double> &a0, const std::vector<
 qs_status run_adiabatic_batch(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
                               const size_t *off, double dt, double T, int steps);
 
+// Adiabatic evolution of instances of several widths, one handle per width
+// (h0 terms of handle i: h0[h0_off[i] .. h0_off[i+1]); H1 of member j, counted
+// over all handles in order: h1[h1_off[j] .. h1_off[j+1])), the handles on
+// streams of their own run side by side; `chunk` steps are enqueued per handle
+// in turn.
+qs_status run_adiabatic_multi(qs_state *const *states, int n_states, const qs_pauli_term *h0,
+                              const size_t *h0_off, const qs_pauli_term *h1, const size_t *h1_off, double dt,
+                              double T, int steps, int chunk);
+
 // Free anything cached per state.
 void plan_cache_release(qs_state *s);
 

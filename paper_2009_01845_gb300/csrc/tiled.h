@@ -188,6 +188,34 @@ template <typename R> struct TileParams {
 
 static_assert(sizeof(TileParams<double>) <= 32700, "kernel parameter block too large");
 
+// Pointers a pass kernel needs at run time (not part of a pass's structure):
+// per-member matrices of batched-parameter gates, the gradient partials of the
+// adjoint sweep, and the Ising op's factor tables.
+template <typename R> struct TilePtrs {
+    const V<R> *pmat;
+    double *gpart;
+    const double *ising_thr;
+};
+
+// The values of a pass (matrix entries, diagonal-block factors), passed
+// beside a specialised kernel whose descriptor holds only the structure: one
+// kernel serves every pass of that structure (e.g. every step of a Trotter
+// evolution, whose angles change from step to step).
+template <typename R> struct TileVals {
+    V<R> mat[kTileMaxMat];
+    TileDFac<R> dfac[kTileMaxDFac];  // only v0, v1, v2 are read
+};
+static_assert(sizeof(TileVals<double>) <= 24576, "pass values exceed the kernel parameter budget");
+
+// Dynamic shared memory of a pass kernel: the tile (sizeof(V<R>) << k bytes),
+// then the transpose offsets, one word per (stage, thread), then the threads'
+// tile-local lane/warp bits per stage (16 bits per stage and thread).
+template <typename R>
+__host__ __device__ constexpr size_t tile_smem_bytes(int k, int n_stages) {
+    return (sizeof(V<R>) << k) +
+           (size_t)(n_stages > 0 ? n_stages : 1) * (32u << TileCfg<R>::WB) * (sizeof(uint32_t) + sizeof(uint16_t));
+}
+
 // Inputs of the Ising-table kernel for one op: global bits of the stage's
 // thread bits (lanes 0..4, then warps) and register bits, the pass's tile bits
 // (k of them, global positions gb, inserted into a tile number by tins), tau,

@@ -8,6 +8,7 @@ call fails, an exception is raised.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import threading
@@ -44,6 +45,11 @@ class CGate(ctypes.Structure):
 
 class CTerm(ctypes.Structure):
     _fields_ = [("coeff", ctypes.c_double), ("x_mask", ctypes.c_uint64), ("z_mask", ctypes.c_uint64)]
+
+
+class CChannel(ctypes.Structure):
+    _fields_ = [("n_targets", ctypes.c_int32), ("targets", ctypes.c_int32 * 2), ("n_kraus", ctypes.c_int32),
+                ("kraus", ctypes.c_void_p)]
 
 
 class COpts(ctypes.Structure):
@@ -86,6 +92,17 @@ _SIGS = {
     "qs_plan_execute": ([P], None),
     "qs_plan_info": ([P, P, P, P, P], None),
     "qs_plan_destroy": ([P], None),
+    "qs_adiabatic_run_batch": ([P, ctypes.c_int, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int],
+                               None),
+    "qs_density_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, P], None),
+    "qs_density_wrap": ([ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, P, P], None),
+    "qs_density_init_pure": ([P, P, ctypes.c_int], None),
+    "qs_density_trace": ([P, P], None),
+    "qs_apply_channels": ([P, P, ctypes.c_size_t, P], None),
+    "qs_jit_set_policy": ([ctypes.c_int], None),
+    "qs_jit_wait": ([], None),
+    "qs_jit_cancel": ([], None),
+    "qs_jit_stats": ([P, P, P, P, P], None),
     "qs_profile_enable": ([ctypes.c_int], None),
     "qs_profile_collect": ([P, P, P, P, ctypes.c_int], None),
     "qs_profile_class_name": ([ctypes.c_int], ctypes.c_char_p),
@@ -114,6 +131,9 @@ def load(build_if_missing: bool = False):
                 f.argtypes = args
                 f.restype = res if res is not None else ctypes.c_int32
             _lib = lib
+            # before the interpreter exits: drop queued pass compiles, let the
+            # running ones finish
+            atexit.register(lib.qs_jit_cancel)
     return _lib
 
 
@@ -346,6 +366,136 @@ class State:
         counts = (ctypes.c_size_t * self.batch)(*[len(h) for h in h1_per_member])
         _check(self.lib.qs_adiabatic_evolve_batch(self.handle, a0, n0, a1, counts, float(T), float(dt), int(steps)))
         return self
+
+
+def adiabatic_run_batch(states, h0s, h1s, T: float, dt: float, steps: int = -1):
+    """Evolve handles of different widths in one call (qs_adiabatic_run_batch):
+    states[i] has its H0 h0s[i]; h1s holds every member's H1, handle by handle."""
+    n = len(states)
+    if len(h0s) != n or len(h1s) != sum(st.batch for st in states):
+        raise ValueError("one H0 per handle and one H1 per member")
+    arr = (ctypes.c_void_p * n)(*[st.handle.value for st in states])
+    a0, _ = marshal_terms([t for h in h0s for t in h])
+    c0 = (ctypes.c_size_t * n)(*[len(h) for h in h0s])
+    a1, _ = marshal_terms([t for h in h1s for t in h])
+    c1 = (ctypes.c_size_t * len(h1s))(*[len(h) for h in h1s])
+    _check(load().qs_adiabatic_run_batch(arr, n, a0, c0, a1, c1, float(T), float(dt), int(steps)))
+    return states
+
+
+# ------------------------------------------------------------------ density matrices
+class DensityMatrix(State):
+    """A batch of n-qubit density matrices (Sec. 2.4, "Density matrices and
+    noise") in a torch CUDA tensor of batch * 4^n amplitudes, entry (r, c) of
+    member b at b 4^n + r 2^n + c; gates act as rho -> U rho U^dag, channels in
+    Kraus form; probabilities() is the diagonal, expectation() Tr(rho H),
+    norm2() the purity Tr(rho^2)."""
+
+    def __init__(self, n: int, batch: int = 1, dtype: str = "c64", tensor=None, stream=None):
+        import torch
+        self.lib = load()
+        self.n, self.batch, self.dtype = int(n), int(batch), dtype
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        if tensor is None:
+            tensor = torch.empty(self.batch << (2 * self.n), dtype=tdt, device="cuda")
+        if tensor.dtype != tdt or not tensor.is_cuda or not tensor.is_contiguous() or \
+                tensor.numel() != (self.batch << (2 * self.n)):
+            raise ValueError("density tensor must be a contiguous CUDA tensor of batch*4^n "
+                             f"{tdt} elements")
+        self.tensor = tensor
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(self.lib.qs_density_wrap(self.n, self.batch, DTYPE[dtype], ctypes.c_void_p(tensor.data_ptr()),
+                                        ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h)))
+        self.handle = h
+
+    def init_pure(self, psi):
+        """rho = |psi><psi| per member from a host array of batch * 2^n amplitudes."""
+        npdt = np.complex64 if self.dtype == "c64" else np.complex128
+        a = np.ascontiguousarray(np.asarray(psi, dtype=npdt).reshape(-1))
+        if a.size != (self.batch << self.n):
+            raise ValueError("wrong number of amplitudes")
+        _check(self.lib.qs_density_init_pure(self.handle, ctypes.c_void_p(a.ctypes.data), 0))
+        return self
+
+    def set(self, values):
+        npdt = np.complex64 if self.dtype == "c64" else np.complex128
+        a = np.ascontiguousarray(np.asarray(values, dtype=npdt).reshape(-1))
+        if a.size != (self.batch << (2 * self.n)):
+            raise ValueError("wrong number of entries")
+        _check(self.lib.qs_state_set(self.handle, ctypes.c_void_p(a.ctypes.data), 0))
+        return self
+
+    def get(self) -> np.ndarray:
+        """The matrices: shape (2^n, 2^n), or (batch, 2^n, 2^n)."""
+        npdt = np.complex64 if self.dtype == "c64" else np.complex128
+        out = np.empty(self.batch << (2 * self.n), dtype=npdt)
+        _check(self.lib.qs_state_get(self.handle, ctypes.c_void_p(out.ctypes.data), 0))
+        d = 1 << self.n
+        return out.reshape(self.batch, d, d) if self.batch > 1 else out.reshape(d, d)
+
+    def apply_channels(self, channels, mode: str = "auto"):
+        """channels: list of (targets, kraus) with kraus a list of 2^k x 2^k matrices."""
+        arr = (CChannel * max(1, len(channels)))()
+        keep = []
+        for i, (targets, kraus) in enumerate(channels):
+            k = np.ascontiguousarray(np.asarray(kraus, dtype=np.complex128))
+            keep.append(k)
+            arr[i].n_targets = len(targets)
+            for j, q in enumerate(targets):
+                arr[i].targets[j] = int(q)
+            arr[i].n_kraus = int(k.shape[0])
+            arr[i].kraus = k.ctypes.data
+        o = opts(mode)
+        _check(self.lib.qs_apply_channels(self.handle, arr, len(channels), ctypes.byref(o)))
+        del keep
+        return self
+
+    def trace(self) -> np.ndarray:
+        out = np.empty(self.batch, dtype=np.float64)
+        _check(self.lib.qs_density_trace(self.handle, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def purity(self) -> np.ndarray:
+        return self.norm2()
+
+    def probabilities(self, on_device: bool = False):
+        if on_device:
+            import torch
+            out = torch.empty(self.batch << self.n, dtype=torch.float64, device=self.tensor.device)
+            _check(self.lib.qs_probabilities(self.handle, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        out = np.empty(self.batch << self.n, dtype=np.float64)
+        _check(self.lib.qs_probabilities(self.handle, ctypes.c_void_p(out.ctypes.data), 0))
+        return out.reshape(self.batch, 1 << self.n) if self.batch > 1 else out
+
+
+# ------------------------------------------------------------------ pass specialisation
+JIT_POLICY = {"off": 0, "tiered": 1, "eager": 2, "sync": 3}
+
+
+JIT_FOLD = 8
+
+
+def jit_set_policy(policy: str, fold: bool = False):
+    """When tiled passes get kernels specialised for them (qs_jit_set_policy):
+    "off", "tiered" (default), "eager" or "sync"; fold: passes repeated with
+    the same values also get kernels with the values compiled in."""
+    _check(load().qs_jit_set_policy(JIT_POLICY[policy] | (JIT_FOLD if fold else 0)))
+
+
+def jit_wait():
+    """Wait for the queued background compiles."""
+    _check(load().qs_jit_wait())
+
+
+def jit_stats() -> dict:
+    sp, ge, co, fa = (ctypes.c_longlong() for _ in range(4))
+    sec = ctypes.c_double()
+    _check(load().qs_jit_stats(ctypes.byref(sp), ctypes.byref(ge), ctypes.byref(co), ctypes.byref(fa),
+                               ctypes.byref(sec)))
+    return {"specialised_launches": sp.value, "generic_launches": ge.value, "compiled": co.value,
+            "failed": fa.value, "compile_seconds": sec.value}
 
 
 # ------------------------------------------------------------------ launch accounting

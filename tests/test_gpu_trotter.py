@@ -104,3 +104,46 @@ def test_config5_smallest_instance_sampled_steps(qs):
     for dtype in ("c128", "c64"):
         st = qs.State(n, dtype=dtype).init_plus().adiabatic_evolve(h0, h1, T, dt, steps=steps)
         close(st.get(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_uneven_widths_in_one_call(qs, dtype):
+    """Instances of several widths (one handle per width, two members where the
+    width repeats) evolved in one qs_adiabatic_run_batch call, 24 steps (three
+    chunks of the round-robin enqueue), each member against the oracle."""
+    widths = [12, 13, 14, 16] if dtype == "c128" else [13, 14, 16]
+    T, dt = 1.2, 0.05
+    r = qi.rng(91)
+    states, h0s, h1s, members = [], [], [], []
+    for i, n in enumerate(widths):
+        B = 2 if i % 2 == 0 else 1
+        st = qs.State(n, batch=B, dtype=dtype).init_plus()
+        h0 = qi.transverse_field_terms(n)
+        states.append(st)
+        h0s.append(h0)
+        for _ in range(B):
+            h1 = qi.random_ising_terms(n, r)
+            h1s.append(h1)
+            members.append((st, n, h0, h1))
+    qs.adiabatic_run_batch(states, h0s, h1s, T, dt)
+    got = {id(st): st.get().reshape(st.batch, -1) for st in states}
+    seen = {}
+    for st, n, h0, h1 in members:
+        b = seen.get(id(st), 0)
+        seen[id(st)] = b + 1
+        want = oracle.adiabatic_evolve(oracle.plus_state(n), n, h0, h1, T, dt)
+        close(got[id(st)][b], want, dtype)
+
+
+def test_uneven_widths_argument_errors(qs):
+    a = qs.State(13, dtype="c64").init_plus()
+    b = qs.State(14, dtype="c128").init_plus()
+    with pytest.raises(qs.QsimError) as e:
+        qs.adiabatic_run_batch([a, b], [qi.transverse_field_terms(13), qi.transverse_field_terms(14)],
+                               [qi.random_ising_terms(13, qi.rng(1)), qi.random_ising_terms(14, qi.rng(2))],
+                               1.0, 0.1)
+    assert e.value.status == 1
+    with pytest.raises(qs.QsimError) as e:
+        qs.adiabatic_run_batch([a, a], [qi.transverse_field_terms(13)] * 2,
+                               [qi.random_ising_terms(13, qi.rng(1))] * 2, 1.0, 0.1)
+    assert e.value.status == 1
