@@ -144,7 +144,7 @@ def alu_peak_tflops(dtype: str, sm_mhz: float) -> float:
     return FP64_TFLOPS
 
 
-TILED_SOURCES = ("kernels_tiled.cu", "tiled.h", "plan_tiled.cpp")
+TILED_SOURCES = ("kernels_tiled.cu", "tiled.h", "plan_tiled.cpp", "tile_device.cuh", "tile_jit.cpp")
 LAUNCH_PROFILE = os.path.join(ROOT, "profiles", "launches_random_layer_n32_c64.md")
 
 
@@ -860,6 +860,43 @@ def measurement(n: int = 32, reps: int = 3) -> dict:
     return out
 
 
+def host_memory(n: int = 34, layers: int = 2, device_gib: int = 16) -> dict:
+    """A state in host memory (Sec. 2.5: one device reused for a state's
+    pieces): the random-layer circuit's first layers at n = 34 complex64
+    (128 GiB of pinned host memory, the largest power of two the host holds)
+    through a device budget of 16 GiB; per-gate rate and the achieved
+    host<->device (C2C) bandwidth: every segment copies the state to the
+    device and back once."""
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    gates = qi.random_layer_circuit(n, layers, seed=2)
+    t0 = time.perf_counter()
+    hs = qsim.HostState(n, dtype="c64", device_bytes=device_gib << 30)
+    t_alloc = time.perf_counter() - t0
+    hs.init_basis(0)
+    qsim.profile_collect()
+    qsim.profile_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs.apply(gates)
+    nrm = hs.norm2()[0]  # synchronises
+    t = time.perf_counter() - t0
+    qsim.profile_enable(False)
+    raw = qsim.profile_collect()
+    state = (1 << n) * 8
+    hs.close()
+    hc = raw.get("host_copy", (0.0, 0, 0.0, 0.0))
+    return {"workload": f"random-layer circuit, first {layers} layers, n={n}, complex64, state in host memory, "
+                        f"device budget {device_gib} GiB", "gates": len(gates), "wall_s": t,
+            "gate_apps_per_s": len(gates) / t, "host_alloc_s": t_alloc, "norm2": nrm,
+            "state_GiB": state / 2 ** 30,
+            "host_copy_GB": hc[2] / 1e9, "host_copy_GBps": hc[2] / (hc[0] / 1000.0) / 1e9 if hc[0] else None,
+            "state_passes_over_c2c": hc[2] / (2 * state) if state else None,
+            "kernels": {k: {"ms": v[0], "launches": v[1], "GB": v[2] / 1e9} for k, v in raw.items() if v[1]},
+            "note": "wall time includes the final norm pass (one more stream of the state)"}
+
+
 SECONDARY = {
     "variational_adjoint": lambda: variational_adjoint(),
     "adiabatic_batch": lambda: adiabatic_batch(),
@@ -869,6 +906,7 @@ SECONDARY = {
     "qft_n18_c128": lambda: qft_n18(),
     "random_layer_c128_n33": lambda: random_layer_c128(),
     "measurement": lambda: measurement(),
+    "host_memory": lambda: host_memory(),
 }
 
 

@@ -310,7 +310,9 @@ qs_status qs_adiabatic_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0,
 /* Tracing aid (no counterpart in the paper). While enabled, every kernel launch
    of the library is bracketed by CUDA events on the launching stream, grouped
    by kernel class (dense, phase, diag, swap, param, tiled, fused_tc, reduce,
-   trotter_diag, adjoint, hpsi = the adjoint's lambda = H psi, init).
+   trotter_diag, adjoint, hpsi = the adjoint's lambda = H psi, evolve = the exact
+   time-evolution solvers, host_copy = chunk copies of host-memory states,
+   init).
    Process-wide. */
 qs_status qs_profile_enable(int on);
 /* Wait for the recorded launches, write per-class total milliseconds, launch
@@ -338,6 +340,64 @@ int qs_profile_class_count(void);
 qs_status qs_adiabatic_run_batch(qs_state *const *states, int n_states, const qs_pauli_term *h0,
                                  const size_t *h0_counts, const qs_pauli_term *h1, const size_t *h1_counts,
                                  double T, double dt, int steps);
+
+/* ---------------------------------------------------------------- exact evolution (Sec. 2.6) */
+/* Time evolution i d/dt psi = H(t) psi, H(t) = (1 - s) H0 + s H1 with s = t/T
+   (any Pauli terms; H0 = H1 gives a constant H), by the solvers the paper
+   names besides Trotter: QS_SOLVER_EXP applies exp(-i dt H(s_mid)) per step,
+   s_mid at the step's midpoint, as the Taylor series of the exponential on the
+   state (the step cut into pieces tau with sum|c| tau <= 1, each summed to
+   the order whose remainder bound falls below the precision's unit
+   roundoff); QS_SOLVER_RK4 the classical fourth-order Runge-Kutta step;
+   QS_SOLVER_RK45 the fifth-order solution of the Dormand-Prince 5(4) pair with
+   the fixed step dt. Each step applies H to whole states (no matrix is
+   built), so any n fits; the call allocates 2 (exp), 3 (rk4) or 7 (rk45)
+   scratch states with the stream-ordered allocator. K = round(T/dt) steps,
+   or `steps` >= 0 of them; every batch member. Asynchronous. */
+#define QS_SOLVER_EXP 0
+#define QS_SOLVER_RK4 1
+#define QS_SOLVER_RK45 2
+qs_status qs_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1, size_t n_h1,
+                    double T, double dt, int steps, int solver);
+
+/* Schedule gradient of the Trotterised adiabatic evolution (Sec. 4: the
+   schedule s(t) and the total time are optimised for the final energy). From
+   the handle's state psi_0 (per member) the call applies K second-order
+   Trotter steps of H(s_k) = (1 - s_k) H0 + s_k H1, step k with svals[k] and
+   the step dt (the splitting of qs_trotter_step: H0, H1 must have Z-string and
+   single-qubit X terms only, else QS_ERR_UNSUPPORTED), leaves psi_K in the
+   handle, and returns E = Re <psi_K|H1|psi_K> (energy: batch doubles, host,
+   may be NULL) with its derivatives by one adjoint sweep: dE_ds[b K + k] =
+   dE/ds_k and dE_ddt[b] = dE/d(dt) for dt shared by all steps (host arrays).
+   A schedule s(t; theta) and total time T = K dt follow by the chain rule
+   (dE/dtheta = sum_k dE/ds_k ds_k/dtheta). The sweep undoes each step's
+   factors on psi and lambda = H1 psi and reads <lambda|G|psi> for the
+   generators G (the diagonal and X parts of H0 and H1) the factors'
+   derivatives insert. Scratch: 3 states and K small buffers from the
+   stream-ordered allocator. Synchronises. */
+qs_status qs_schedule_gradient(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                               size_t n_h1, const double *svals, int K, double dt, double *energy, double *dE_ds,
+                               double *dE_ddt);
+
+/* ---------------------------------------------------------------- host-memory states (Sec. 2.5) */
+/* A state of n qubits (one member) whose 2^n amplitudes live in pinned host
+   memory, for states larger than the GPU's memory (Sec. 2.5: one device
+   reused for the pieces of a state; Sec. 3.1 reaches 34 qubits on a 32 GB GPU
+   this way). The handle uses at most device_bytes of device memory (0 = a
+   quarter of the free memory): two buffers of 2^m amplitudes. Gates run in
+   segments: a run of gates whose dense targets lie in the low chunk bits and
+   a few high bits S (at most 6) is applied to groups of 2^|S| chunks copied
+   into a buffer, every gate rewritten for the group (controls and diagonal
+   factors on the other high bits resolved), on the ordinary gate kernels;
+   groups alternate between the buffers on two streams, so copies of one
+   overlap kernels of the other. Supported on such a handle:
+   qs_state_init_basis / init_plus / set / get (the host copy; the call
+   synchronises), qs_apply_gates (any mode; a gate with more dense targets
+   above the chunk bits than a group holds: QS_ERR_UNSUPPORTED), qs_norm2,
+   qs_probabilities (host output) and qs_expectation (terms whose X bits act
+   on qubits n-m .. n-1; others QS_ERR_UNSUPPORTED); every other call returns
+   QS_ERR_UNSUPPORTED. cudaHostAlloc failing: QS_ERR_CUDA. */
+qs_status qs_state_create_host(int n, qs_dtype dtype, size_t device_bytes, void *cuda_stream, qs_state **out);
 
 /* ---------------------------------------------------------------- density matrices */
 /* Density matrices and noise channels (Sec. 2.4, "Density matrices and

@@ -160,7 +160,67 @@ static qs_status not_for_density(const qs_state *s, const char *what) {
         set_error("%s is not supported on a density matrix", what);
         return QS_ERR_UNSUPPORTED;
     }
+    if (s && s->host) {
+        set_error("%s is not supported on a host-memory state", what);
+        return QS_ERR_UNSUPPORTED;
+    }
     return QS_OK;
+}
+
+static qs_status not_for_host(const qs_state *s, const char *what) {
+    if (s && s->host) {
+        set_error("%s is not supported on a host-memory state", what);
+        return QS_ERR_UNSUPPORTED;
+    }
+    return QS_OK;
+}
+
+qs_status qs_state_create_host(int n, qs_dtype dtype, size_t device_bytes, void *stream, qs_state **out) {
+    QS_GUARD_BEGIN
+    clear_error();
+    if (!out) {
+        set_error("null output pointer");
+        return QS_ERR_ARG;
+    }
+    *out = nullptr;
+    QS_TRY(check_shape(n, 1, dtype));
+    int dev = 0;
+    QS_CUDA_TRY(cudaGetDevice(&dev));
+    const size_t b = dtype == QS_C64 ? 8 : 16;
+    if (device_bytes == 0) {
+        size_t free_b = 0, total_b = 0;
+        QS_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        device_bytes = free_b / 4;
+    }
+    int m = 0;
+    while (m < n && ((size_t)2 << (m + 1)) * b <= device_bytes) ++m;  // two buffers of 2^m amplitudes
+    if (m < 1) {
+        set_error("a device budget of %zu bytes holds no buffer", device_bytes);
+        return QS_ERR_ARG;
+    }
+    qs_state *s = new qs_state();
+    s->n = n;
+    s->ms = n;
+    s->batch = 1;
+    s->dtype = dtype;
+    s->stream = (cudaStream_t)stream;
+    s->device = dev;
+    s->owns = true;
+    s->pm = m;
+    // high bits a group brings into a buffer: up to 6, keeping chunks of at
+    // least 2^16 amplitudes where the buffer allows (copies stay large), and at
+    // least 2 (or m - 1 for a tiny buffer) so a two-qubit gate always fits
+    s->pm = std::min(m, n);
+    const int sg = std::min(std::min(6, std::max(2, m - 16)), std::max(0, m - 1));
+    s->pl = m - sg;
+    const cudaError_t e = cudaHostAlloc(&s->host, ((size_t)1 << n) * b, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_status(e, "cudaHostAlloc(state)");
+    }
+    *out = s;
+    return QS_OK;
+    QS_GUARD_END
 }
 
 qs_status qs_state_destroy(qs_state *s) {
@@ -169,6 +229,12 @@ qs_status qs_state_destroy(qs_state *s) {
     if (s->owns || s->scratch || s->host_pinned || s->gtab || s->ptab || s->itab || s->ithr)
         cudaStreamSynchronize(s->stream);
     if (s->owns && s->data) cudaFree(s->data);
+    if (s->host) {
+        cudaStreamSynchronize(s->stream);
+        cudaFreeHost(s->host);
+    }
+    for (void *pb : s->pbuf)
+        if (pb) cudaFree(pb);
     if (s->scratch) cudaFree(s->scratch);
     if (s->host_pinned) cudaFreeHost(s->host_pinned);
     if (s->gtab) cudaFree(s->gtab);
@@ -186,6 +252,10 @@ qs_status qs_state_data(const qs_state *s, void **dev_ptr) {
     if (!dev_ptr) {
         set_error("null output pointer");
         return QS_ERR_ARG;
+    }
+    if (s->host) {
+        set_error("a host-memory state has no device array");
+        return QS_ERR_UNSUPPORTED;
     }
     *dev_ptr = s->data;
     return QS_OK;
@@ -212,6 +282,7 @@ qs_status qs_state_init_basis(qs_state *s, uint64_t x) {
         set_error("basis index %llu >= 2^%d", (unsigned long long)x, s->n);
         return QS_ERR_ARG;
     }
+    if (s->host) return host_init(s, false, x);
     return k_init_basis(s, x);
     QS_GUARD_END
 }
@@ -220,6 +291,7 @@ qs_status qs_state_init_plus(qs_state *s) {
     QS_GUARD_BEGIN
     clear_error();
     QS_TRY(check_state(s));
+    if (s->host) return host_init(s, true, 0);
     return k_init_plus(s);
     QS_GUARD_END
 }
@@ -231,6 +303,11 @@ qs_status qs_state_set(qs_state *s, const void *src, int on_device) {
     if (!src) {
         set_error("null source");
         return QS_ERR_ARG;
+    }
+    if (s->host) {
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        QS_CUDA_TRY(cudaMemcpy(s->host, src, state_bytes(s), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+        return QS_OK;
     }
     QS_CUDA_TRY(cudaMemcpyAsync(s->data, src, state_bytes(s),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
@@ -247,25 +324,16 @@ qs_status qs_state_get(const qs_state *s, void *dst, int on_device) {
         set_error("null destination");
         return QS_ERR_ARG;
     }
+    if (s->host) {
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        QS_CUDA_TRY(cudaMemcpy(dst, s->host, state_bytes(s), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+        return QS_OK;
+    }
     QS_CUDA_TRY(cudaMemcpyAsync(dst, s->data, state_bytes(s),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
     if (!on_device) QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return QS_OK;
     QS_GUARD_END
-}
-
-// flags of a lowered matrix (as lower_gate sets them)
-static void matrix_flags(LGate *g) {
-    const int K = 1 << g->k;
-    bool diag = true, phase = true;
-    for (int r = 0; r < K; ++r)
-        for (int c = 0; c < K; ++c) {
-            const cd v = g->m[r * K + c];
-            if (r != c && v != cd(0.0)) diag = false;
-            if (r == c && r != K - 1 && v != cd(1.0)) phase = false;
-        }
-    g->diagonal = diag;
-    g->phase_only = diag && phase;
 }
 
 // On a density matrix of dm qubits (a 2 dm-qubit vector, row qubit q = vector
@@ -278,7 +346,7 @@ static void density_pair(int dm, const LGate &g, LGate *row, LGate *col) {
     *col = g;
     for (auto &v : col->m) v = std::conj(v);
     col->kind = QS_GATE_UNITARY;
-    matrix_flags(col);
+    set_matrix_flags(col);
 }
 
 static qs_status lower_all(const qs_state *s, const qs_gate *gates, size_t count, std::vector<LGate> *out) {
@@ -328,6 +396,7 @@ qs_status qs_apply_gates(qs_state *s, const qs_gate *gates, size_t count, const 
     QS_TRY(lower_all(s, gates, count, &lg));
     for (auto &g : lg)
         if (g.param_index >= 0) g.param_index = -1;  // unbatched call: angles come from params
+    if (s->host) return host_apply(s, lg, mode, opts);
     return run_gates(s, lg, mode, opts, nullptr, 0);
     QS_GUARD_END
 }
@@ -374,6 +443,13 @@ qs_status qs_probabilities(qs_state *s, double *out, int on_device) {
         return QS_ERR_ARG;
     }
     auto probs = [&](double *dst) { return s->dm ? k_dm_probabilities(s, dst) : k_probabilities(s, dst); };
+    if (s->host) {
+        if (on_device) {
+            set_error("probabilities of a host-memory state go to host memory");
+            return QS_ERR_UNSUPPORTED;
+        }
+        return host_probabilities(s, out);
+    }
     if (on_device) return probs(out);
     const size_t total = (size_t)s->batch << (s->dm ? s->dm : s->n);
     double *tmp = nullptr;
@@ -467,6 +543,7 @@ qs_status qs_norm2(qs_state *s, double *out) {
         set_error("null output");
         return QS_ERR_ARG;
     }
+    if (s->host) return host_norm2(s, out);
     QS_TRY(ensure_host_pinned(s, (size_t)s->batch));
     double *dev = nullptr;
     QS_TRY(k_norm2(s, &dev));
@@ -504,6 +581,7 @@ qs_status qs_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, 
         return QS_ERR_ARG;
     }
     QS_TRY(check_terms(s, terms, count));
+    if (s->host) return host_expectation(s, terms, count, out_re, out_im);
     QS_TRY(ensure_host_pinned(s, (size_t)2 * s->batch));
     double *dev = nullptr;
     if (s->dm)
@@ -693,6 +771,59 @@ qs_status qs_adiabatic_run_batch(qs_state *const *states, int n_states, const qs
     QS_GUARD_END
 }
 
+qs_status qs_evolve(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1, size_t n_h1,
+                    double T, double dt, int steps, int solver) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    QS_TRY(not_for_density(s, "time evolution"));
+    QS_TRY(check_terms(s, h0, n_h0));
+    QS_TRY(check_terms(s, h1, n_h1));
+    if (solver != QS_SOLVER_EXP && solver != QS_SOLVER_RK4 && solver != QS_SOLVER_RK45) {
+        set_error("unknown solver %d", solver);
+        return QS_ERR_ARG;
+    }
+    if (!(T > 0) || !(dt > 0) || !std::isfinite(T) || !std::isfinite(dt)) {
+        set_error("T and dt must be positive and finite");
+        return QS_ERR_ARG;
+    }
+    const long K = std::lround(T / dt);
+    if (K < 1 || K > (1l << 30)) {
+        set_error("T/dt gives %ld steps", K);
+        return QS_ERR_ARG;
+    }
+    const long run = steps < 0 ? K : std::min<long>(K, steps);
+    if (run == 0) return QS_OK;
+    return run_evolve(s, h0, n_h0, h1, n_h1, T, dt, (int)run, solver);
+    QS_GUARD_END
+}
+
+qs_status qs_schedule_gradient(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
+                               size_t n_h1, const double *svals, int K, double dt, double *energy, double *dE_ds,
+                               double *dE_ddt) {
+    QS_GUARD_BEGIN
+    clear_error();
+    QS_TRY(check_state(s));
+    QS_TRY(not_for_density(s, "the schedule gradient"));
+    QS_TRY(check_terms(s, h0, n_h0));
+    QS_TRY(check_terms(s, h1, n_h1));
+    if (K < 1 || !svals || !dE_ds || !dE_ddt) {
+        set_error("need K >= 1 schedule values and the gradient outputs");
+        return QS_ERR_ARG;
+    }
+    for (int k = 0; k < K; ++k)
+        if (!std::isfinite(svals[k])) {
+            set_error("schedule value %d is not finite", k);
+            return QS_ERR_ARG;
+        }
+    if (!(dt > 0) || !std::isfinite(dt)) {
+        set_error("dt must be positive and finite");
+        return QS_ERR_ARG;
+    }
+    return run_schedule_gradient(s, h0, n_h0, h1, n_h1, svals, K, dt, energy, dE_ds, dE_ddt);
+    QS_GUARD_END
+}
+
 qs_status qs_density_init_pure(qs_state *s, const void *psi, int on_device) {
     QS_GUARD_BEGIN
     clear_error();
@@ -793,7 +924,7 @@ static qs_status lower_channel(const qs_state *s, const qs_channel &ch, LGate *o
                     for (int c2 = 0; c2 < K; ++c2)
                         out->m[(size_t)(r1 * K + c1) * K2 + (r2 * K + c2)] += Ki[r1 * K + r2] * std::conj(Ki[c1 * K + c2]);
     }
-    matrix_flags(out);
+    set_matrix_flags(out);
     out->is_swap = false;
     return QS_OK;
 }

@@ -177,17 +177,22 @@ qs_status lower_gate(int n, const qs_gate &g, LGate *out) {
             }
         out->m = kind_matrix(g.kind, g.params);
     }
+    set_matrix_flags(out);
+    out->is_swap = (g.kind == QS_GATE_SWAP);
+    return QS_OK;
+}
+
+void set_matrix_flags(LGate *g) {
+    const int K = 1 << g->k;
     bool diag = true, phase = true;
     for (int r = 0; r < K; ++r)
         for (int c = 0; c < K; ++c) {
-            const cd v = out->m[r * K + c];
+            const cd v = g->m[r * K + c];
             if (r != c && v != cd(0.0)) diag = false;
             if (r == c && r != K - 1 && v != cd(1.0)) phase = false;
         }
-    out->diagonal = diag;
-    out->phase_only = diag && phase;
-    out->is_swap = (g.kind == QS_GATE_SWAP);
-    return QS_OK;
+    g->diagonal = diag;
+    g->phase_only = diag && phase;
 }
 
 }  // namespace qsim

@@ -42,6 +42,12 @@ struct qs_state {
     // density matrix of dm qubits (n = 2 dm: entry (r, c) at index r 2^dm + c);
     // 0 for a state vector
     int dm = 0;
+    // host-memory state (partition.cpp): the amplitudes in pinned host memory
+    // (data stays null), two device buffers of 2^pm amplitudes, chunks of 2^pl
+    void *host = nullptr;
+    int pm = 0;
+    int pl = 0;
+    void *pbuf[2] = {nullptr, nullptr};
 };
 
 namespace qsim {
@@ -102,6 +108,16 @@ int kind_params(int kind);
 std::vector<cd> kind_matrix(int kind, const double *p);
 // validate one gate against n qubits and lower it (qubit -> bit form)
 qs_status lower_gate(int n, const qs_gate &g, LGate *out);
+// diagonal / phase_only flags of a lowered matrix
+void set_matrix_flags(LGate *g);
+
+// host-memory states (partition.cpp)
+qs_status host_state_buffers(qs_state *s);
+qs_status host_init(qs_state *s, bool plus, uint64_t x);
+qs_status host_apply(qs_state *s, const std::vector<LGate> &G, int mode, const qs_opts *opts);
+qs_status host_norm2(qs_state *s, double *out);
+qs_status host_probabilities(qs_state *s, double *out);
+qs_status host_expectation(qs_state *s, const qs_pauli_term *terms, size_t count, double *re, double *im);
 
 // ------------------------------------------------------------------ kernels (host launchers)
 qs_status k_init_basis(qs_state *s, uint64_t x);

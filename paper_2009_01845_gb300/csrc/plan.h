@@ -51,6 +51,14 @@ qs_status run_adiabatic_multi(qs_state *const *states, int n_states, const qs_pa
                               const size_t *h0_off, const qs_pauli_term *h1, const size_t *h1_off, double dt,
                               double T, int steps, int chunk);
 
+// Exact time evolution (evolve.cpp): `steps` steps of dt of H(t) = (1 - s) H0
+// + s H1, s = t / T, with the solver QS_SOLVER_*; and the schedule gradient of
+// the Trotterised evolution with schedule values svals[0 .. K).
+qs_status run_evolve(qs_state *s, const qs_pauli_term *h0, size_t n0, const qs_pauli_term *h1, size_t n1, double T,
+                     double dt, int steps, int solver);
+qs_status run_schedule_gradient(qs_state *s, const qs_pauli_term *h0, size_t n0, const qs_pauli_term *h1, size_t n1,
+                                const double *svals, int K, double dt, double *energy, double *dE_ds, double *dE_ddt);
+
 // Free anything cached per state.
 void plan_cache_release(qs_state *s);
 

@@ -235,8 +235,8 @@ qs_status qs_plan_create(qs_state *s, const qs_gate *gates, size_t count, const 
             return QS_ERR_ARG;
         }
         *out = nullptr;
-        if (s->dm) {
-            set_error("plans are not supported on a density matrix");
+        if (s->dm || s->host) {
+            set_error("plans are not supported on a density matrix or a host-memory state");
             return QS_ERR_UNSUPPORTED;
         }
         if (count && !gates) {

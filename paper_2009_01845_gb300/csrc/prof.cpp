@@ -26,7 +26,7 @@ double g_bytes[KC_COUNT];
 double g_flops[KC_COUNT];
 
 const char *kNames[KC_COUNT] = {"init", "dense", "phase", "diag", "swap", "param",
-                                "tiled", "fused_tc", "reduce", "trotter_diag", "adjoint", "hpsi"};
+                                "tiled", "fused_tc", "reduce", "trotter_diag", "adjoint", "hpsi", "evolve", "host_copy"};
 
 cudaEvent_t take() {
     if (!g_pool.empty()) {

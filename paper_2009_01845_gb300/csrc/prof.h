@@ -19,6 +19,8 @@ enum KClass {
     KC_TROTTER_DIAG,
     KC_ADJOINT,
     KC_HPSI,     // lambda = H psi of the adjoint (Pauli-sum application)
+    KC_EVOLVE,   // exact time-evolution solvers: H psi and linear combinations
+    KC_HOSTCOPY, // host-memory states: chunk copies between host and device
     KC_COUNT
 };
 

@@ -25,6 +25,7 @@ _lib = None
 KIND = {"H": 0, "X": 1, "Y": 2, "Z": 3, "S": 4, "SDG": 5, "T": 6, "TDG": 7, "RX": 8, "RY": 9,
         "RZ": 10, "U1": 11, "U2": 12, "U3": 13, "CZ": 14, "CU1": 15, "SWAP": 16, "UNITARY": 17}
 MODE = {"auto": 0, "unfused": 1, "tiled": 2, "fused": 3}
+SOLVER = {"exp": 0, "rk4": 1, "rk45": 2}
 DTYPE = {"c64": 0, "c128": 1}
 STATUS = {0: "QS_OK", 1: "QS_ERR_ARG", 2: "QS_ERR_OOM", 3: "QS_ERR_CUDA", 4: "QS_ERR_UNSUPPORTED",
           5: "QS_ERR_TIMEOUT"}
@@ -65,6 +66,7 @@ _SIGS = {
     "qs_state_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, P], None),
     "qs_state_wrap": ([ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, P, P], None),
     "qs_state_destroy": ([P], None),
+    "qs_state_create_host": ([ctypes.c_int, ctypes.c_int32, ctypes.c_size_t, P, P], None),
     "qs_state_data": ([P, P], None),
     "qs_state_set_stream": ([P, P], None),
     "qs_state_init_basis": ([P, ctypes.c_uint64], None),
@@ -92,6 +94,10 @@ _SIGS = {
     "qs_plan_execute": ([P], None),
     "qs_plan_info": ([P, P, P, P, P], None),
     "qs_plan_destroy": ([P], None),
+    "qs_evolve": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                   ctypes.c_int], None),
+    "qs_schedule_gradient": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, P, ctypes.c_int, ctypes.c_double, P, P, P],
+                             None),
     "qs_adiabatic_run_batch": ([P, ctypes.c_int, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int],
                                None),
     "qs_density_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int32, P, P], None),
@@ -356,6 +362,28 @@ class State:
         _check(self.lib.qs_adiabatic_evolve(self.handle, a0, n0, a1, n1, float(T), float(dt), int(steps)))
         return self
 
+    def evolve(self, h0, h1, T: float, dt: float, solver: str = "exp", steps: int = -1):
+        """Exact solvers of Sec. 2.6: "exp", "rk4" or "rk45" (qs_evolve)."""
+        a0, n0 = marshal_terms(h0)
+        a1, n1 = marshal_terms(h1)
+        _check(self.lib.qs_evolve(self.handle, a0, n0, a1, n1, float(T), float(dt), int(steps), SOLVER[solver]))
+        return self
+
+    def schedule_gradient(self, h0, h1, svals, dt: float):
+        """(E, dE/ds_k, dE/d dt) per member of the Trotter evolution with
+        schedule values svals (qs_schedule_gradient); the state becomes psi_K."""
+        a0, n0 = marshal_terms(h0)
+        a1, n1 = marshal_terms(h1)
+        sv = np.ascontiguousarray(np.asarray(svals, dtype=np.float64))
+        K = int(sv.size)
+        e = np.empty(self.batch)
+        g = np.empty(self.batch * K)
+        gdt = np.empty(self.batch)
+        _check(self.lib.qs_schedule_gradient(self.handle, a0, n0, a1, n1, ctypes.c_void_p(sv.ctypes.data), K,
+                                             float(dt), ctypes.c_void_p(e.ctypes.data),
+                                             ctypes.c_void_p(g.ctypes.data), ctypes.c_void_p(gdt.ctypes.data)))
+        return e, g.reshape(self.batch, K), gdt
+
     def adiabatic_evolve_batch(self, h0, h1_per_member, T: float, dt: float, steps: int = -1):
         """Member b evolves under its own H1 = h1_per_member[b]."""
         if len(h1_per_member) != self.batch:
@@ -381,6 +409,22 @@ def adiabatic_run_batch(states, h0s, h1s, T: float, dt: float, steps: int = -1):
     c1 = (ctypes.c_size_t * len(h1s))(*[len(h) for h in h1s])
     _check(load().qs_adiabatic_run_batch(arr, n, a0, c0, a1, c1, float(T), float(dt), int(steps)))
     return states
+
+
+class HostState(State):
+    """A state in pinned host memory, larger than the device holds
+    (qs_state_create_host): gates and read-outs stream it through at most
+    device_bytes of device memory."""
+
+    def __init__(self, n: int, dtype: str = "c64", device_bytes: int = 0, stream=None):
+        self.lib = load()
+        self.n, self.batch, self.dtype = int(n), 1, dtype
+        self.tensor = None
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(self.lib.qs_state_create_host(self.n, DTYPE[dtype], int(device_bytes),
+                                             ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h)))
+        self.handle = h
 
 
 # ------------------------------------------------------------------ density matrices
