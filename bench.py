@@ -494,7 +494,8 @@ def _peak_hbm() -> float:
 def unfused_passes(n: int = 32, reps: int = 5) -> dict:
     """One-gate passes (the plain unfused simulator) at n = 32: a dense 1-qubit
     gate on the lowest and the highest index bit, a 2-qubit dense gate, CZ and
-    SWAP in complex64, and the dense 1-qubit gate in complex128; per pass the
+    SWAP in complex64, and the dense 1- and 2-qubit gates in complex128 (in
+    double-float and in FP64 arithmetic); per pass the
     CUDA-event time, the algorithmic bytes (2^n reads and writes of the
     amplitudes the gate touches) and the fraction of the measured HBM peak."""
     import torch
@@ -509,7 +510,8 @@ def unfused_passes(n: int = 32, reps: int = 5) -> dict:
              ("c64", "CZ(0, 1)", G("CZ", (0, 1))),
              ("c64", "SWAP(2, n-3)", G("SWAP", (2, n - 3))),
              ("c128", "H on qubit n-1 (index bit 0)", G("H", (n - 1,))),
-             ("c128", "U3 on qubit n/2", G("U3", (n // 2,), (), (0.3, 0.2, 0.1)))]
+             ("c128", "U3 on qubit n/2", G("U3", (n // 2,), (), (0.3, 0.2, 0.1))),
+             ("c128", "dense 2-qubit on qubits (3, n-5)", G("UNITARY", (3, n - 5), (), (), u4))]
     peak = _peak_hbm()
     out = {"workload": f"one-gate passes, n={n}", "peak_hbm_GBps": peak, "passes": []}
     st = None
@@ -522,17 +524,22 @@ def unfused_passes(n: int = 32, reps: int = 5) -> dict:
                 torch.cuda.empty_cache()
             st = qsim.State(n, dtype=dt).init_plus()
             cur = dt
-        t = _time_cuda(lambda: st.apply([g], mode="unfused"), reps, warmup=2)
-        qsim.profile_collect()
-        qsim.profile_enable(True)
-        st.apply([g], mode="unfused")
-        torch.cuda.synchronize()
-        qsim.profile_enable(False)
-        prof = qsim.profile_collect()
-        nbytes = sum(v[2] for v in prof.values())
-        gbs = nbytes / (t / 1000.0) / 1e9
-        out["passes"].append({"dtype": dt, "gate": name, "ms": t, "GB": nbytes / 1e9, "GBps": gbs,
-                              "frac_of_measured_hbm": gbs / peak})
+        # complex128: the default double-float arithmetic and the FP64 one
+        for fp64 in ((False, True) if dt == "c128" else (False,)):
+            t = _time_cuda(lambda: st.apply([g], mode="unfused", fp64=fp64), reps, warmup=2)
+            qsim.profile_collect()
+            qsim.profile_enable(True)
+            st.apply([g], mode="unfused", fp64=fp64)
+            torch.cuda.synchronize()
+            qsim.profile_enable(False)
+            prof = qsim.profile_collect()
+            nbytes = sum(v[2] for v in prof.values())
+            gbs = nbytes / (t / 1000.0) / 1e9
+            rec = {"dtype": dt, "gate": name, "ms": t, "GB": nbytes / 1e9, "GBps": gbs,
+                   "frac_of_measured_hbm": gbs / peak}
+            if dt == "c128":
+                rec["arithmetic"] = "fp64" if fp64 else "double-float"
+            out["passes"].append(rec)
     if st is not None:
         st.close()
         del st
@@ -637,8 +644,8 @@ def summary(line: dict) -> dict:
                            "fused_pass_ms": rnd(get(ft, "fused", "avg_pass_ms"))}
     up = sec.get("unfused_passes")
     if up:
-        out["unfused_hbm_frac"] = {f'{p["dtype"]} {p["gate"]}': rnd(p["frac_of_measured_hbm"], 3)
-                                   for p in up["passes"]}
+        out["unfused_hbm_frac"] = {" ".join([p["dtype"], p["gate"]] + ([p["arithmetic"]] if "arithmetic" in p else [])):
+                                   rnd(p["frac_of_measured_hbm"], 3) for p in up["passes"]}
     q = sec.get("qft_n18_c128")
     if q:
         out["qft_n18_gate_per_s"] = {k: rnd(v["gate_apps_per_s"]) for k, v in q.items() if isinstance(v, dict)}

@@ -122,8 +122,15 @@ typedef struct qs_opts {
     int32_t mode;             /* QS_MODE_* */
     int32_t tile_qubits;      /* tiled mode: tile width k (0 = default) */
     int32_t fuse_qubits;      /* fused mode: block width (0 = 5) */
-    int32_t flags;            /* reserved, must be 0 */
+    int32_t flags;            /* QS_OPT_* bits, or 0 */
 } qs_opts;
+
+/* complex128 one-gate passes: dense 1- and 2-qubit gates run in double-float
+   arithmetic on the FP32 pipes by default (each double split into two floats,
+   47 significant bits, relative error per gate ~1e-14; GB300's FP64 rate would
+   bind them at a third of the HBM bandwidth). This flag runs them in FP64
+   instead (the plain complex128 simulator). */
+#define QS_OPT_C128_FP64 1
 
 typedef struct qs_state qs_state;
 

@@ -379,8 +379,8 @@ static qs_status check_opts(const qs_opts *o, int *mode) {
         set_error("unknown mode %d", *mode);
         return QS_ERR_ARG;
     }
-    if (o && o->flags != 0) {
-        set_error("opts.flags must be 0");
+    if (o && (o->flags & ~QS_OPT_C128_FP64) != 0) {
+        set_error("unknown opts.flags bits 0x%x", o->flags & ~QS_OPT_C128_FP64);
         return QS_ERR_ARG;
     }
     return QS_OK;

@@ -123,6 +123,11 @@ qs_status host_expectation(qs_state *s, const qs_pauli_term *terms, size_t count
 qs_status k_init_basis(qs_state *s, uint64_t x);
 qs_status k_init_plus(qs_state *s);
 qs_status k_apply_unfused(qs_state *s, const LGate &g);
+// this thread's complex128 passes in FP64 (true) or in double-float on the
+// FP32 pipes (false, the default: one-gate passes of dense 1- and 2-qubit
+// gates, and tiled passes without per-member matrices or gradients)
+void set_c128_fp64(bool on);
+bool c128_fp64();
 qs_status k_probabilities(qs_state *s, double *out_dev);
 // reductions: results land in the state's scratch; *out_dev points at them
 qs_status k_norm2(qs_state *s, double **out_dev);        // batch doubles

@@ -264,6 +264,12 @@ static qs_status launch_swap(qs_state *s, const LGate &g) {
     return QS_OK;
 }
 
+bool k_dense_df(qs_state *s, const LGate &g, qs_status *st);
+
+thread_local bool t_c128_fp64 = false;
+void set_c128_fp64(bool on) { t_c128_fp64 = on; }
+bool c128_fp64() { return t_c128_fp64; }
+
 template <typename R>
 static qs_status apply_unfused_t(qs_state *s, const LGate &g) {
     const int K = 1 << g.k;
@@ -283,6 +289,10 @@ static qs_status apply_unfused_t(qs_state *s, const LGate &g) {
         case 4: return launch_diag<R, 4>(s, g);
         case 5: return launch_diag<R, 5>(s, g);
         }
+    }
+    if (sizeof(R) == 8 && !t_c128_fp64) {  // complex128 dense gates: double-float on the FP32 pipes
+        qs_status st = QS_OK;
+        if (k_dense_df(s, g, &st)) return st;
     }
     switch (g.k) {
     case 1: return launch_dense<R, 1>(s, g);

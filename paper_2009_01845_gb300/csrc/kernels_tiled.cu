@@ -185,14 +185,18 @@ static qs_status launch_tiled_t(qs_state *s, const TileParams<R> &p, int mode) {
 // one-time per-device kernel attributes (done before any graph capture)
 qs_status tiled_configure(qs_state *s) {
     TileParams<float> pf;
-    TileParams<double> pd;
     std::memset(&pf, 0, sizeof(pf));
-    std::memset(&pd, 0, sizeof(pd));
     pf.k = tile_bits(QS_C64);
-    pd.k = tile_bits(QS_C128);
     // total_tiles = 0: the launches configure the attributes and do no work
     QS_TRY(launch_tiled_t<float>(s, pf, 2));
-    return launch_tiled_t<double>(s, pd, 2);
+    static thread_local TileParams<double> pd;
+    std::memset(&pd, 0, sizeof(pd));
+    pd.k = tile_bits(QS_C128);
+    QS_TRY(launch_tiled_t<double>(s, pd, 2));
+    static thread_local TileParams<dd> pq;
+    std::memset(&pq, 0, sizeof(pq));
+    pq.k = tile_bits(QS_C128);
+    return launch_tiled_t<dd>(s, pq, 2);
 }
 
 // the smallest kernel MODE that holds every op of the pass
@@ -210,8 +214,31 @@ template <typename R> static int kernel_mode(const TileParams<R> &p) {
 qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) {
     return launch_tiled_t<float>(s, p, kernel_mode(p));
 }
+// A complex128 pass runs in double-float arithmetic unless FP64 is asked for
+// or it reads per-member matrices or takes gradients (those stay in FP64).
+// The descriptor converts in place: its values (matrix entries, diagonal
+// factors) become float pairs, everything else is copied.
+static bool double_float_pass(const TileParams<double> &p) {
+    if (c128_fp64() || p.n_grad > 0) return false;
+    for (int st = 0; st < p.n_stages; ++st)
+        for (int o = p.st[st].op_begin; o < p.st[st].op_end; ++o)
+            if (p.op[o].pm) return false;
+    return true;
+}
+
 qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) {
-    return launch_tiled_t<double>(s, p, kernel_mode(p));
+    if (!double_float_pass(p)) return launch_tiled_t<double>(s, p, kernel_mode(p));
+    static thread_local TileParams<dd> q;
+    std::memcpy(&q, &p, sizeof(p));
+    q.pmat = nullptr;
+    for (int i = 0; i < kTileMaxMat; ++i) q.mat[i] = ddc{dd(p.mat[i].x), dd(p.mat[i].y)};
+    for (int f = 0; f < kTileMaxDFac; ++f) {
+        const TileDFac<double> &d = p.dfac[f];
+        q.dfac[f].v0 = ddc{dd(d.v0.x), dd(d.v0.y)};
+        q.dfac[f].v1 = ddc{dd(d.v1.x), dd(d.v1.y)};
+        q.dfac[f].v2 = ddc{dd(d.v2.x), dd(d.v2.y)};
+    }
+    return launch_tiled_t<dd>(s, q, kernel_mode(q));
 }
 
 }  // namespace qsim

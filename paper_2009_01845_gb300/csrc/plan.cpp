@@ -24,6 +24,11 @@ static qs_status run_unfused(qs_state *s, const std::vector<LGate> &gates, const
 
 qs_status run_gates(qs_state *s, std::vector<LGate> &gates, int mode, const qs_opts *opts,
                     const double *params_dev, int n_params) {
+    // complex128 arithmetic of the one-gate passes for this call
+    struct Fp64Scope {
+        explicit Fp64Scope(bool on) { set_c128_fp64(on); }
+        ~Fp64Scope() { set_c128_fp64(false); }
+    } fp64(opts && (opts->flags & QS_OPT_C128_FP64));
     switch (mode) {
     case QS_MODE_UNFUSED:
         return run_unfused(s, gates, params_dev, n_params);

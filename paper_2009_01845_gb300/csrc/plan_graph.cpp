@@ -64,10 +64,12 @@ size_t ptab_need(const qs_state *s, const std::vector<LGate> &G) {
     return (s->dtype == QS_C64 ? 8 : 16) * 4 * np * (size_t)s->batch;
 }
 
-qs_status run_mode(qs_state *s, std::vector<LGate> &G, int mode, int width, const double *params, int n_params) {
+qs_status run_mode(qs_state *s, std::vector<LGate> &G, int mode, int width, const double *params, int n_params,
+                   int flags = 0) {
     qs_opts o{};
     o.mode = mode;
     o.fuse_qubits = width;
+    o.flags = flags;
     return run_gates(s, G, mode, &o, params, n_params);
 }
 
@@ -201,7 +203,7 @@ static qs_status capture(qs_plan *p) {
     if (e != cudaSuccess) {
         st = cuda_status(e, "cudaStreamBeginCapture");
     } else {
-        st = run_mode(s, p->gates, p->mode, p->opts.fuse_qubits, p->params, p->n_params);
+        st = run_mode(s, p->gates, p->mode, p->opts.fuse_qubits, p->params, p->n_params, p->opts.flags);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cap, &g);
         if (st == QS_OK && e != cudaSuccess) st = cuda_status(e, "cudaStreamEndCapture");
@@ -241,6 +243,10 @@ qs_status qs_plan_create(qs_state *s, const qs_gate *gates, size_t count, const 
         }
         if (count && !gates) {
             set_error("null gate array");
+            return QS_ERR_ARG;
+        }
+        if (opts && (opts->flags & ~QS_OPT_C128_FP64) != 0) {
+            set_error("unknown opts.flags bits 0x%x", opts->flags & ~QS_OPT_C128_FP64);
             return QS_ERR_ARG;
         }
         qs_plan *p = new qs_plan();

@@ -18,8 +18,15 @@ namespace qsim {
 
 template <typename R> __device__ __forceinline__ V<R> shfl_xor_c(V<R> v, int m) {
     V<R> o;
-    o.x = __shfl_xor_sync(0xffffffffu, v.x, m);
-    o.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+    if constexpr (is_dd<R>) {
+        o.x.h = __shfl_xor_sync(0xffffffffu, v.x.h, m);
+        o.x.l = __shfl_xor_sync(0xffffffffu, v.x.l, m);
+        o.y.h = __shfl_xor_sync(0xffffffffu, v.y.h, m);
+        o.y.l = __shfl_xor_sync(0xffffffffu, v.y.l, m);
+    } else {
+        o.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+        o.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+    }
     return o;
 }
 
@@ -267,6 +274,9 @@ __device__ __forceinline__ float2 fma_c2(float c, float2 v, float2 acc) {
 __device__ __forceinline__ double2 fma_c2(double c, double2 v, double2 acc) {
     return make_double2(fma(c, v.x, acc.x), fma(c, v.y, acc.y));
 }
+__device__ __forceinline__ ddc fma_c2(dd c, ddc v, ddc acc) {
+    return mkc<dd>(dd_fma(c, v.x, acc.x), dd_fma(c, v.y, acc.y));
+}
 
 // real rotation on register bit J as in-place shears (TOP_ROTS_R): x += s1 y,
 // then y += s2 x over the register pairs (x, y) that differ in bit J. Each
@@ -316,12 +326,7 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
         V<R> v = mkc<R>(1, 0);
         for (int f = f0 + lane; f < f0 + no; f += 32) v = cmul<R>(v, outside_factor<R>(p.dfac[f], dfv[f], tbase));
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            V<R> w;
-            w.x = __shfl_xor_sync(0xffffffffu, v.x, off);
-            w.y = __shfl_xor_sync(0xffffffffu, v.y, off);
-            v = cmul<R>(v, w);
-        }
+        for (int off = 16; off > 0; off >>= 1) v = cmul<R>(v, shfl_xor_c<R>(v, off));
         base = cmul<R>(base, v);
     }
     if (ns > 0) {
@@ -536,7 +541,14 @@ __device__ __forceinline__ void tile_load(V<R> *a, const V<R> *__restrict__ psi,
 #pragma unroll
     for (int j = 0; j < RB; ++j) gr[j] = 1ull << p.gbit[s0.rloc[j]];
 #pragma unroll
-    for (int r = 0; r < (1 << RB); ++r) a[r] = psi[gt | reg_offset<RB>(r, gr)];
+    for (int r = 0; r < (1 << RB); ++r) {
+        if constexpr (is_dd<R>) {  // complex128 in memory, split into double-float pairs
+            const double2 v = reinterpret_cast<const double2 *>(psi)[gt | reg_offset<RB>(r, gr)];
+            a[r] = mkc<dd>(dd(v.x), dd(v.y));
+        } else {
+            a[r] = psi[gt | reg_offset<RB>(r, gr)];
+        }
+    }
 }
 
 // Transpose into stage s (s > 0): write under the previous mapping, read under
@@ -706,7 +718,8 @@ __device__ __forceinline__ void tile_op(V<R> *a, const TileParams<R> &p, const V
         }
         break;
     case TOP_GRAD: {
-        if constexpr (!FULL) break;
+        // gradients are taken in FP32 / FP64 passes only (no double-float sweep)
+        if constexpr (FULL && !is_dd<R>) {
         const bool ok = req_ok();
         const uint32_t mr = op.mr;
         constexpr int H = NR / 2;
@@ -744,6 +757,7 @@ __device__ __forceinline__ void tile_op(V<R> *a, const TileParams<R> &p, const V
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
         if (lane == 0) sc.gsm[op.gl][warp] = acc;
+        }
         break;
     }
     default:
@@ -772,7 +786,13 @@ __device__ __forceinline__ void tile_store(V<R> *__restrict__ psi, const V<R> *a
         if ((sl.rflip >> j) & 1u) gt |= gr[j];  // register frame: r holds r ^ rflip
     }
 #pragma unroll
-    for (int r = 0; r < (1 << RB); ++r) psi[gt ^ reg_offset<RB>(r, gr)] = a[r];
+    for (int r = 0; r < (1 << RB); ++r) {
+        if constexpr (is_dd<R>)
+            reinterpret_cast<double2 *>(psi)[gt ^ reg_offset<RB>(r, gr)] =
+                make_double2(to_double(a[r].x), to_double(a[r].y));
+        else
+            psi[gt ^ reg_offset<RB>(r, gr)] = a[r];
+    }
 }
 
 // Gradient partials of this tile (adjoint sweep), summed over the warps in a
@@ -781,14 +801,16 @@ template <typename R>
 __device__ __forceinline__ void tile_grad_flush(const TileParams<R> &p, const TilePtrs<R> &q, uint64_t t,
                                                 const TileScratch<R> &sc) {
     constexpr int NW = 1 << TileCfg<R>::WB;
-    __syncthreads();
-    if ((int)threadIdx.x < p.n_grad) {
-        double sum = 0.0;
+    if constexpr (!is_dd<R>) {
+        __syncthreads();
+        if ((int)threadIdx.x < p.n_grad) {
+            double sum = 0.0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) sum += (double)sc.gsm[threadIdx.x][w];
-        q.gpart[(uint64_t)p.gslot[threadIdx.x] * p.total_tiles + t] = sum;
+            for (int w = 0; w < NW; ++w) sum += (double)sc.gsm[threadIdx.x][w];
+            q.gpart[(uint64_t)p.gslot[threadIdx.x] * p.total_tiles + t] = sum;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 }  // namespace qsim

@@ -66,11 +66,18 @@ const char *kStdintStub =
 
 enum JitState { JS_NEW = 0, JS_QUEUED, JS_COMPILING, JS_READY, JS_FAILED };
 
+// key flags: the arithmetic in bits 0 and 2 (complex64, complex128 in FP64 or
+// in double-float), the values compiled in (bit 1)
+template <typename R> constexpr unsigned char kTypeCode = 0;
+template <> constexpr unsigned char kTypeCode<double> = 1;
+template <> constexpr unsigned char kTypeCode<dd> = 4;
+constexpr unsigned char kKeyFolded = 2;
+
 constexpr int kMaxEntries = 1024;  // distinct passes tracked per process
 
 struct JitEntry {
-    std::vector<unsigned char> key;  // dtype byte + normalised descriptor bytes
-    bool dbl = false;
+    std::vector<unsigned char> key;  // flags byte + normalised descriptor bytes
+    int type = 0;                    // arithmetic: kTypeCode<R>
     int state = JS_NEW;
     long long hits = 0;
     std::vector<char> cubin;
@@ -168,15 +175,14 @@ struct Src {
     }
 };
 
-template <typename R> void real_lit(Src &o, R v) {
-    if (sizeof(R) == 4) o.f("%af", (double)v);
-    else o.f("%a", (double)v);
-}
+void real_lit(Src &o, float v) { o.f("%af", (double)v); }
+void real_lit(Src &o, double v) { o.f("%a", v); }
+void real_lit(Src &o, dd v) { o.f("{%af,%af}", (double)v.h, (double)v.l); }
 template <typename R> void cplx_lit(Src &o, const V<R> &v) {
     o.s += "{";
-    real_lit<R>(o, v.x);
+    real_lit(o, v.x);
     o.s += ",";
-    real_lit<R>(o, v.y);
+    real_lit(o, v.y);
     o.s += "}";
 }
 template <typename T> void int_list(Src &o, const T *a, int n) {
@@ -197,7 +203,7 @@ template <typename T> int used(const T *a, int n) {
 template <typename R> std::string generate(const TileParams<R> &P, bool folded) {
     constexpr int RB = TileCfg<R>::RB;
     constexpr int WB = TileCfg<R>::WB;
-    const char *RT = sizeof(R) == 4 ? "float" : "double";
+    const char *RT = is_dd<R> ? "dd" : sizeof(R) == 4 ? "float" : "double";
     Src o;
     o.s.reserve(1 << 17);
     o.s += "#include \"tile_device.cuh\"\nusing namespace qsim;\n";
@@ -334,12 +340,14 @@ bool nvrtc_compile(const std::string &src, const std::string &arch, std::vector<
 template <typename R> std::string generate_from_key(const std::vector<unsigned char> &key) {
     TileParams<R> P;
     std::memcpy(&P, key.data() + 1, sizeof(P));
-    return generate<R>(P, (key[0] & 2) != 0);
+    return generate<R>(P, (key[0] & kKeyFolded) != 0);
 }
 
 void compile_entry(const std::shared_ptr<JitEntry> &e, const std::string &arch) {
     const auto t0 = std::chrono::steady_clock::now();
-    const std::string src = e->dbl ? generate_from_key<double>(e->key) : generate_from_key<float>(e->key);
+    const std::string src = e->type == kTypeCode<dd>       ? generate_from_key<dd>(e->key)
+                            : e->type == kTypeCode<double> ? generate_from_key<double>(e->key)
+                                                           : generate_from_key<float>(e->key);
     std::vector<char> cubin;
     std::string log;
     const bool ok = nvrtc_compile(src, arch, &cubin, &log);
@@ -454,12 +462,12 @@ qs_status tile_jit_launch_t(qs_state *s, const TileParams<R> &p, bool *launched)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     QS_CUDA_TRY(cudaStreamIsCapturing(s->stream, &cs));
     const bool capturing = cs != cudaStreamCaptureStatusNone;
-    // keys: flags (bit 0: complex128, bit 1: values compiled in), then the
+    // keys: flags (kTypeCode, kKeyFolded: values compiled in), then the
     // descriptor with its run-time pointers and the Ising op's tau (which only
     // the table kernel reads) cleared; the structure key also clears the
     // values (matrix entries, diagonal factors)
     std::vector<unsigned char> full(1 + sizeof(TileParams<R>));
-    full[0] = (sizeof(R) == 8 ? 1 : 0) | 2;
+    full[0] = kTypeCode<R> | kKeyFolded;
     {
         TileParams<R> &k = *reinterpret_cast<TileParams<R> *>(full.data() + 1);
         std::memcpy(&k, &p, sizeof(p));
@@ -471,7 +479,7 @@ qs_status tile_jit_launch_t(qs_state *s, const TileParams<R> &p, bool *launched)
             if (k.op[o].type == TOP_ISING) k.op[o].tmask = 0;
     }
     std::vector<unsigned char> key(full);
-    key[0] &= 1;
+    key[0] = kTypeCode<R>;
     {
         TileParams<R> &k = *reinterpret_cast<TileParams<R> *>(key.data() + 1);
         std::memset(k.mat, 0, sizeof(k.mat));
@@ -511,7 +519,7 @@ qs_status tile_jit_launch_t(qs_state *s, const TileParams<R> &p, bool *launched)
                 ++g.entries;
                 ef = std::make_shared<JitEntry>();
                 ef->key = full;
-                ef->dbl = sizeof(R) == 8;
+                ef->type = kTypeCode<R>;
                 ef->state = JS_QUEUED;
                 g.table[hf].push_back(ef);
                 start_workers(g);
@@ -545,7 +553,7 @@ qs_status tile_jit_launch_t(qs_state *s, const TileParams<R> &p, bool *launched)
             ++g.entries;
             e = std::make_shared<JitEntry>();
             e->key = std::move(key);
-            e->dbl = sizeof(R) == 8;
+            e->type = kTypeCode<R>;
             bucket.push_back(e);
         }
         ++e->hits;
@@ -605,6 +613,7 @@ qs_status tile_jit_launch_t(qs_state *s, const TileParams<R> &p, bool *launched)
 
 template qs_status tile_jit_launch_t<float>(qs_state *, const TileParams<float> &, bool *);
 template qs_status tile_jit_launch_t<double>(qs_state *, const TileParams<double> &, bool *);
+template qs_status tile_jit_launch_t<dd>(qs_state *, const TileParams<dd> &, bool *);
 
 int jit_policy() { return policy_now(); }
 

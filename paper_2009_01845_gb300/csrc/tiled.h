@@ -47,6 +47,8 @@ constexpr int kTileMaxDFac = 96;   // diagonal-block factors per pass
 template <typename R> struct TileCfg;
 template <> struct TileCfg<float> { static constexpr int RB = 5, WB = 3, kMinBlocks = 2; };
 template <> struct TileCfg<double> { static constexpr int RB = 4, WB = 3, kMinBlocks = 1; };
+// complex128 computed in double-float: the same tile (16 bytes per amplitude)
+template <> struct TileCfg<dd> { static constexpr int RB = 4, WB = 3, kMinBlocks = 1; };
 inline int tile_reg_bits(qs_dtype dt) { return dt == QS_C64 ? 5 : 4; }
 inline int tile_warp_bits(qs_dtype dt) { return 3; }
 inline int tile_threads(qs_dtype dt) { return 32 << tile_warp_bits(dt); }
@@ -187,6 +189,10 @@ template <typename R> struct TileParams {
 };
 
 static_assert(sizeof(TileParams<double>) <= 32700, "kernel parameter block too large");
+// a complex128 pass descriptor converts to its double-float form in place
+static_assert(sizeof(TileParams<dd>) == sizeof(TileParams<double>) && sizeof(ddc) == sizeof(double2) &&
+                  alignof(ddc) == alignof(double2) && sizeof(TileDFac<dd>) == sizeof(TileDFac<double>),
+              "double-float pass descriptor layout");
 
 // Pointers a pass kernel needs at run time (not part of a pass's structure):
 // per-member matrices of batched-parameter gates, the gradient partials of the

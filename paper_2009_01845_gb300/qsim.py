@@ -198,8 +198,12 @@ def marshal_terms(terms: Iterable):
     return arr, len(terms)
 
 
-def opts(mode: str = "auto", tile_qubits: int = 0, fuse_qubits: int = 0) -> COpts:
-    return COpts(MODE[mode], int(tile_qubits), int(fuse_qubits), 0)
+OPT_C128_FP64 = 1
+
+
+def opts(mode: str = "auto", tile_qubits: int = 0, fuse_qubits: int = 0, fp64: bool = False) -> COpts:
+    """fp64: complex128 one-gate passes in FP64 (default: double-float)."""
+    return COpts(MODE[mode], int(tile_qubits), int(fuse_qubits), OPT_C128_FP64 if fp64 else 0)
 
 
 # ------------------------------------------------------------------ state
@@ -274,9 +278,9 @@ class State:
 
     # -- gates
     def apply(self, gates: Sequence[Gate], mode: str = "auto", tile_qubits: int = 0,
-              fuse_qubits: int = 0):
+              fuse_qubits: int = 0, fp64: bool = False):
         arr, keep = marshal_gates(gates)
-        o = opts(mode, tile_qubits, fuse_qubits)
+        o = opts(mode, tile_qubits, fuse_qubits, fp64)
         _check(self.lib.qs_apply_gates(self.handle, arr, len(gates), ctypes.byref(o)))
         del keep
         return self

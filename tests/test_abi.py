@@ -64,7 +64,8 @@ def test_kind_codes_match_header():
         m = re.search(rf"#define QS_GATE_{name}\s+(\d+)", text)
         assert m and int(m.group(1)) == code, name
     for name, code in (("QS_MODE_AUTO", 0), ("QS_MODE_UNFUSED", 1), ("QS_MODE_TILED", 2),
-                       ("QS_MODE_FUSED_TC", 3), ("QS_C64", 0), ("QS_C128", 1), ("QS_MAX_BATCH", 65535)):
+                       ("QS_MODE_FUSED_TC", 3), ("QS_C64", 0), ("QS_C128", 1), ("QS_MAX_BATCH", 65535),
+                       ("QS_OPT_C128_FP64", qsim.OPT_C128_FP64)):
         assert int(re.search(rf"#define {name}\s+(\d+)", text).group(1)) == code
     for name, code in qsim.SOLVER.items():
         assert int(re.search(rf"#define QS_SOLVER_{name.upper()}\s+(\d+)", text).group(1)) == code
