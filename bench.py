@@ -583,23 +583,32 @@ def qft_n18(reps: int = 20) -> dict:
 
 
 def random_layer_c128(n: int = 33, layers: int = 2) -> dict:
-    """The random-layer circuit's first `layers` layers at n = 33 in complex128
-    (128 GiB state): tiled passes against the plain unfused simulator on the
-    same GPU, per-gate rates and the full 20-layer circuit time they project."""
+    """The whole 20-layer random-layer circuit (seed 2) at n = 33 in complex128
+    (128 GiB state) in tiled passes, double-float arithmetic on specialised
+    kernels, timed end to end (one run after a run that specialises its
+    passes); then its first `layers` layers in tiled FP64 passes and in the
+    plain unfused simulator (double-float and FP64), with the full-circuit
+    times their per-gate rates project."""
     import torch
     from paper_2009_01845_gb300 import inputs as qi
     from paper_2009_01845_gb300 import qsim
-    gates = qi.random_layer_circuit(n, layers, seed=2)
-    full = len(qi.random_layer_circuit(n, 20, seed=2))
+    full = qi.random_layer_circuit(n, 20, seed=2)
+    part = qi.random_layer_circuit(n, layers, seed=2)
     st = qsim.State(n, dtype="c128")
-    out = {"workload": f"random-layer circuit, first {layers} of 20 layers, n={n}, complex128",
-           "gates_timed": len(gates)}
-    for mode in ("tiled", "unfused"):
+    out = {"workload": f"random-layer circuit, 20 layers ({len(full)} gates), n={n}, complex128"}
+    t = _time_cuda(lambda: st.init_basis(0).apply(full, mode="tiled"), 1, warmup=1)
+    out["tiled"] = {"ms": t, "gate_apps_per_s": len(full) / (t / 1000.0), "gates": len(full),
+                    "arithmetic": "double-float", "kernels": "specialised"}
+    out["norm2_after"] = float(st.norm2()[0])
+    for mode, fp64, key in (("tiled", True, "tiled_fp64"), ("unfused", False, "unfused"),
+                            ("unfused", True, "unfused_fp64")):
         st.init_basis(0)
         torch.cuda.synchronize()
-        t = _time_cuda(lambda: st.apply(gates, mode=mode), 1, warmup=0)
-        rate = len(gates) / (t / 1000.0)
-        out[mode] = {"ms": t, "gate_apps_per_s": rate, "projected_full_circuit_s": full / rate}
+        t = _time_cuda(lambda: st.apply(part, mode=mode, fp64=fp64), 1, warmup=0)
+        rate = len(part) / (t / 1000.0)
+        out[key] = {"ms": t, "gate_apps_per_s": rate, "gates": len(part),
+                    "arithmetic": "fp64" if fp64 else "double-float",
+                    "projected_full_circuit_s": len(full) / rate}
     st.close()
     del st
     torch.cuda.empty_cache()
@@ -652,6 +661,7 @@ def summary(line: dict) -> dict:
     rc = sec.get("random_layer_c128_n33")
     if rc:
         out["c128_n33_gate_per_s"] = {k: rnd(v["gate_apps_per_s"]) for k, v in rc.items() if isinstance(v, dict)}
+        out["c128_n33_full_circuit_s"] = rnd(get(rc, "tiled", "ms") / 1000.0) if get(rc, "tiled", "ms") else None
     ms = sec.get("measurement")
     if ms:
         out["marginal_hbm_frac"] = [rnd(m["frac_of_measured_hbm"], 3) for m in ms["marginals"]]

@@ -90,8 +90,11 @@ struct dd {
     }
 };
 
+// A complex double-float number, laid out for the paired FP32 instructions
+// (add/sub/mul/fma .f32x2, two lanes per instruction): h = (re.h, im.h),
+// l = (re.l, im.l).
 struct __align__(16) ddc {
-    dd x, y;
+    float2 h, l;
 };
 
 template <typename R> struct cvec;
@@ -105,55 +108,90 @@ template <> constexpr bool is_dd<dd> = true;
 #ifdef __CUDACC__
 __device__ __forceinline__ dd operator-(dd a) { return dd(-a.h, -a.l); }
 __device__ __forceinline__ bool operator==(dd a, dd b) { return a.h == b.h && a.l == b.l; }
-__device__ __forceinline__ dd operator+(dd a, dd b) {
-    float s, e;
-    two_sum(a.h, b.h, s, e);
-    e += a.l + b.l;
-    dd r;
-    fast_two_sum(s, e, r.h, r.l);
-    return r;
-}
-__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
-__device__ __forceinline__ dd operator*(dd a, dd b) {
-    const float p = a.h * b.h;
-    float q = fmaf(a.h, b.h, -p);  // p + q = a.h b.h exactly
-    q = fmaf(a.h, b.l, q);
-    q = fmaf(a.l, b.h, q);
-    dd r;
-    fast_two_sum(p, q, r.h, r.l);
-    return r;
-}
-__device__ __forceinline__ dd &operator+=(dd &a, dd b) { return a = a + b; }
-__device__ __forceinline__ dd &operator-=(dd &a, dd b) { return a = a - b; }
-// c + a b
-__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) {
-    const float p = a.h * b.h;
-    float q = fmaf(a.h, b.h, -p);
-    q = fmaf(a.h, b.l, q);
-    q = fmaf(a.l, b.h, q);
-    float s, e;
-    two_sum(c.h, p, s, e);
-    e += q + c.l;
-    dd r;
-    fast_two_sum(s, e, r.h, r.l);
-    return r;
-}
-// a b + c d (one renormalisation)
-__device__ __forceinline__ dd dd_dot2(dd a, dd b, dd c, dd d) {
-    const float p1 = a.h * b.h, p2 = c.h * d.h;
-    float q = fmaf(a.h, b.h, -p1) + fmaf(c.h, d.h, -p2);  // the two products' low parts
-    q = fmaf(a.h, b.l, q);
-    q = fmaf(a.l, b.h, q);
-    q = fmaf(c.h, d.l, q);
-    q = fmaf(c.l, d.h, q);
-    float s, e;
-    two_sum(p1, p2, s, e);
-    e += q;
-    dd r;
-    fast_two_sum(s, e, r.h, r.l);
-    return r;
-}
 __device__ __forceinline__ double to_double(dd a) { return df_join(a.h, a.l); }
+
+// ---- paired FP32 operations (round to nearest, never contracted)
+__device__ __forceinline__ unsigned long long pbits(float2 v) { return *reinterpret_cast<unsigned long long *>(&v); }
+__device__ __forceinline__ float2 pfloat(unsigned long long b) { return *reinterpret_cast<float2 *>(&b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pbits(a)), "l"(pbits(b)));
+    return pfloat(r);
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pbits(a)), "l"(pbits(b)));
+    return pfloat(r);
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pbits(a)), "l"(pbits(b)));
+    return pfloat(r);
+}
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pbits(a)), "l"(pbits(b)), "l"(pbits(c)));
+    return pfloat(r);
+}
+// sign flips by bit operations (exact, no FP instruction)
+__device__ __forceinline__ float2 pneg(float2 a) { return pfloat(pbits(a) ^ 0x8000000080000000ull); }
+__device__ __forceinline__ float2 pneg_hi(float2 a) { return pfloat(pbits(a) ^ 0x8000000000000000ull); }
+__device__ __forceinline__ float2 pneg_lo(float2 a) { return pfloat(pbits(a) ^ 0x0000000080000000ull); }
+
+// ---- complex double-float arithmetic on the lane pairs
+// a + b: exact two-sum of the high parts, then the low parts, renormalised
+__device__ __forceinline__ ddc dd_cadd(ddc a, ddc b) {
+    const float2 s = padd(a.h, b.h);
+    const float2 bb = psub(s, a.h);
+    float2 e = padd(psub(a.h, psub(s, bb)), psub(b.h, bb));
+    e = padd(e, padd(a.l, b.l));
+    ddc r;
+    r.h = padd(s, e);
+    r.l = psub(e, psub(r.h, s));
+    return r;
+}
+
+// c + x v for a real double-float x (both components)
+__device__ __forceinline__ ddc dd_fma_c2(dd x, ddc v, ddc c) {
+    const float2 xh = make_float2(x.h, x.h), xl = make_float2(x.l, x.l);
+    const float2 np = pmul(pneg(xh), v.h);  // -p, p = xh v.h rounded
+    float2 q = pfma(xh, v.h, np);           // xh v.h - p, exactly
+    q = pfma(xh, v.l, q);
+    q = pfma(xl, v.h, q);
+    // c.h + p = s + e exactly (two-sum with b = -np)
+    const float2 s = psub(c.h, np);
+    const float2 bb = psub(s, c.h);
+    float2 e = psub(psub(c.h, psub(s, bb)), padd(np, bb));
+    e = padd(e, padd(q, c.l));
+    ddc r;
+    r.h = padd(s, e);
+    r.l = psub(e, psub(r.h, s));
+    return r;
+}
+
+// a b = a.re (b.re, b.im) + (-a.im, a.im) (b.im, b.re): two paired exact
+// products, an exact two-sum of their high parts, the low parts in FP32
+__device__ __forceinline__ ddc dd_cmul(ddc a, ddc b) {
+    const float2 xh = make_float2(a.h.x, a.h.x), xl = make_float2(a.l.x, a.l.x);
+    const float2 yh = make_float2(-a.h.y, a.h.y), yl = make_float2(-a.l.y, a.l.y);
+    const float2 sh = make_float2(b.h.y, b.h.x), sl = make_float2(b.l.y, b.l.x);
+    const float2 np1 = pmul(pneg(xh), b.h);
+    const float2 np2 = pmul(pneg(yh), sh);
+    float2 q = padd(pfma(xh, b.h, np1), pfma(yh, sh, np2));
+    q = pfma(xh, b.l, q);
+    q = pfma(xl, b.h, q);
+    q = pfma(yh, sl, q);
+    q = pfma(yl, sh, q);
+    // np1 + np2 = ns + ne exactly; the product is -(ns + ne) + q
+    const float2 ns = padd(np1, np2);
+    const float2 bb = psub(ns, np1);
+    const float2 ne = padd(psub(np1, psub(ns, bb)), psub(np2, bb));
+    const float2 e = psub(q, ne);
+    ddc r;
+    r.h = psub(e, ns);
+    r.l = psub(e, padd(r.h, ns));
+    return r;
+}
 #endif  // __CUDACC__
 
 template <typename R> __host__ __device__ __forceinline__ V<R> mkc(R re, R im) {
@@ -162,6 +200,18 @@ template <typename R> __host__ __device__ __forceinline__ V<R> mkc(R re, R im) {
     v.y = im;
     return v;
 }
+template <> __host__ __device__ __forceinline__ ddc mkc<dd>(dd re, dd im) {
+    ddc v;
+    v.h = make_float2(re.h, im.h);
+    v.l = make_float2(re.l, im.l);
+    return v;
+}
+
+// real and imaginary parts as scalars of the arithmetic
+template <typename R> __host__ __device__ __forceinline__ R re_of(V<R> v) { return v.x; }
+template <typename R> __host__ __device__ __forceinline__ R im_of(V<R> v) { return v.y; }
+template <> __host__ __device__ __forceinline__ dd re_of<dd>(ddc v) { return dd(v.h.x, v.l.x); }
+template <> __host__ __device__ __forceinline__ dd im_of<dd>(ddc v) { return dd(v.h.y, v.l.y); }
 
 #ifdef __CUDACC__
 // a * b
@@ -178,12 +228,23 @@ template <typename R> __device__ __forceinline__ V<R> cmadd(V<R> a, V<R> b, V<R>
     return mkc<R>(re, im);
 }
 
-// double-float complex products: each component one two-product sum
-template <> __device__ __forceinline__ ddc cmul<dd>(ddc a, ddc b) {
-    return mkc<dd>(dd_dot2(a.x, b.x, -a.y, b.y), dd_dot2(a.x, b.y, a.y, b.x));
+template <> __device__ __forceinline__ ddc cmul<dd>(ddc a, ddc b) { return dd_cmul(a, b); }
+template <> __device__ __forceinline__ ddc cmadd<dd>(ddc a, ddc b, ddc c) { return dd_cadd(dd_cmul(a, b), c); }
+
+// -v and conj(v)
+template <typename R> __device__ __forceinline__ V<R> cneg(V<R> v) { return mkc<R>(-v.x, -v.y); }
+template <> __device__ __forceinline__ ddc cneg<dd>(ddc v) {
+    ddc r;
+    r.h = pneg(v.h);
+    r.l = pneg(v.l);
+    return r;
 }
-template <> __device__ __forceinline__ ddc cmadd<dd>(ddc a, ddc b, ddc c) {
-    return mkc<dd>(dd_dot2(a.x, b.x, -a.y, b.y) + c.x, dd_dot2(a.x, b.y, a.y, b.x) + c.y);
+template <typename R> __device__ __forceinline__ V<R> conjc(V<R> v) { return mkc<R>(v.x, -v.y); }
+template <> __device__ __forceinline__ ddc conjc<dd>(ddc v) {
+    ddc r;
+    r.h = pneg_hi(v.h);
+    r.l = pneg_hi(v.l);
+    return r;
 }
 
 #endif  // __CUDACC__

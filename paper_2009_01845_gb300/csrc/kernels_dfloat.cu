@@ -4,9 +4,10 @@
 // FP64-bound at ~0.31 of the HBM peak (8 FP64 FMAs per amplitude for a 2x2
 // gate). Here every double is split into a pair of floats h + l (df_split in
 // device.cuh: 47 of its 53 significant bits), the gate is applied in
-// double-float arithmetic (products by FMA-based exact multiplication, sums
-// of the products' high parts by exact two-sums, the low parts summed in
-// FP32), and the result is joined back into a double (df_join). The split and
+// double-float arithmetic (device.cuh: exact paired FMA products, exact
+// two-sums of their high parts, the low parts summed in FP32; the real and
+// imaginary parts share each paired .f32x2 instruction), and the result is
+// joined back into a double (df_join). The split and
 // the join are integer operations on the IEEE bit patterns, so no FP64
 // instruction remains. The error per gate is a few 2^-47 (~1e-14) of the
 // amplitudes' magnitude, which keeps the complex128 tolerance (1e-12 on
@@ -23,34 +24,8 @@ namespace qsim {
 
 namespace {
 
-// the running sum of double-float products: exact sum of the high parts,
-// FP32 sum of the low parts and the two-sum errors
-struct DFAcc {
-    float s = 0.f, e = 0.f;
-    __device__ __forceinline__ void add_prod(dd x, dd y, bool neg) {
-        float p = x.h * y.h;
-        float q = fmaf(x.h, y.h, -p);  // p + q = x.h y.h exactly
-        q = fmaf(x.h, y.l, q);
-        q = fmaf(x.l, y.h, q);
-        if (neg) {
-            p = -p;
-            q = -q;
-        }
-        float t, err;
-        two_sum(s, p, t, err);
-        s = t;
-        e += err + q;
-    }
-    __device__ __forceinline__ double result() const {
-        float h, l;  // renormalised (e may exceed s after cancellation)
-        two_sum(s, e, h, l);
-        return df_join(h, l);
-    }
-};
-
 template <int K> struct DenseDFP {
-    float mrh[(1 << K) * (1 << K)], mrl[(1 << K) * (1 << K)];
-    float mih[(1 << K) * (1 << K)], mil[(1 << K) * (1 << K)];
+    ddc m[(1 << K) * (1 << K)];  // row-major, split on the host
     uint64_t off[1 << K];
     uint64_t setmask;
     InsertBits ib;
@@ -67,25 +42,18 @@ __global__ void __launch_bounds__(256) dense_df_kernel(double2 *__restrict__ psi
     for (uint64_t g = global_tid(); g < p.total; g += global_stride()) {
         const uint64_t b = g >> p.n_free;
         const uint64_t base = (b << p.n) | expand_bits(g & fmask, p.ib) | p.setmask;
-        dd ar[D], ai[D];
+        ddc a[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const double2 v = psi[base | p.off[c]];
-            df_split(v.x, ar[c].h, ar[c].l);
-            df_split(v.y, ai[c].h, ai[c].l);
+            a[c] = mkc<dd>(dd(v.x), dd(v.y));
         }
 #pragma unroll
         for (int r = 0; r < D; ++r) {
-            DFAcc re, im;
+            ddc acc = dd_cmul(p.m[r * D], a[0]);
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const dd mr(p.mrh[r * D + c], p.mrl[r * D + c]), mi(p.mih[r * D + c], p.mil[r * D + c]);
-                re.add_prod(mr, ar[c], false);
-                re.add_prod(mi, ai[c], true);
-                im.add_prod(mr, ai[c], false);
-                im.add_prod(mi, ar[c], false);
-            }
-            psi[base | p.off[r]] = make_double2(re.result(), im.result());
+            for (int c = 1; c < D; ++c) acc = dd_cadd(acc, dd_cmul(p.m[r * D + c], a[c]));
+            psi[base | p.off[r]] = make_double2(to_double(re_of<dd>(acc)), to_double(im_of<dd>(acc)));
         }
     }
 }
@@ -96,19 +64,11 @@ unsigned grid_for_df(const qs_state *s, uint64_t work) {
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 8));
 }
 
-void split_host(double d, float *h, float *l) {
-    *h = (float)d;
-    *l = (float)(d - (double)*h);
-}
-
 template <int K> qs_status launch_dense_df(qs_state *s, const LGate &g) {
     constexpr int D = 1 << K;
     DenseDFP<K> p;
     std::memset(&p, 0, sizeof(p));
-    for (int i = 0; i < D * D; ++i) {
-        split_host(g.m[i].real(), &p.mrh[i], &p.mrl[i]);
-        split_host(g.m[i].imag(), &p.mih[i], &p.mil[i]);
-    }
+    for (int i = 0; i < D * D; ++i) p.m[i] = mkc<dd>(dd(g.m[i].real()), dd(g.m[i].imag()));
     uint64_t tmask = 0;
     for (int j = 0; j < K; ++j) tmask |= 1ull << g.tbit[j];
     for (int l = 0; l < D; ++l) {

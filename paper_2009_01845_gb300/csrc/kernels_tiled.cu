@@ -222,7 +222,7 @@ static bool double_float_pass(const TileParams<double> &p) {
     if (c128_fp64() || p.n_grad > 0) return false;
     for (int st = 0; st < p.n_stages; ++st)
         for (int o = p.st[st].op_begin; o < p.st[st].op_end; ++o)
-            if (p.op[o].pm) return false;
+            if (p.op[o].pm || p.op[o].type == TOP_PROT || p.op[o].type == TOP_GRAD) return false;
     return true;
 }
 
@@ -231,12 +231,13 @@ qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) {
     static thread_local TileParams<dd> q;
     std::memcpy(&q, &p, sizeof(p));
     q.pmat = nullptr;
-    for (int i = 0; i < kTileMaxMat; ++i) q.mat[i] = ddc{dd(p.mat[i].x), dd(p.mat[i].y)};
+    auto cv = [](double2 v) { return mkc<dd>(dd(v.x), dd(v.y)); };
+    for (int i = 0; i < kTileMaxMat; ++i) q.mat[i] = cv(p.mat[i]);
     for (int f = 0; f < kTileMaxDFac; ++f) {
         const TileDFac<double> &d = p.dfac[f];
-        q.dfac[f].v0 = ddc{dd(d.v0.x), dd(d.v0.y)};
-        q.dfac[f].v1 = ddc{dd(d.v1.x), dd(d.v1.y)};
-        q.dfac[f].v2 = ddc{dd(d.v2.x), dd(d.v2.y)};
+        q.dfac[f].v0 = cv(d.v0);
+        q.dfac[f].v1 = cv(d.v1);
+        q.dfac[f].v2 = cv(d.v2);
     }
     return launch_tiled_t<dd>(s, q, kernel_mode(q));
 }

@@ -19,10 +19,10 @@ namespace qsim {
 template <typename R> __device__ __forceinline__ V<R> shfl_xor_c(V<R> v, int m) {
     V<R> o;
     if constexpr (is_dd<R>) {
-        o.x.h = __shfl_xor_sync(0xffffffffu, v.x.h, m);
-        o.x.l = __shfl_xor_sync(0xffffffffu, v.x.l, m);
-        o.y.h = __shfl_xor_sync(0xffffffffu, v.y.h, m);
-        o.y.l = __shfl_xor_sync(0xffffffffu, v.y.l, m);
+        o.h.x = __shfl_xor_sync(0xffffffffu, v.h.x, m);
+        o.h.y = __shfl_xor_sync(0xffffffffu, v.h.y, m);
+        o.l.x = __shfl_xor_sync(0xffffffffu, v.l.x, m);
+        o.l.y = __shfl_xor_sync(0xffffffffu, v.l.y, m);
     } else {
         o.x = __shfl_xor_sync(0xffffffffu, v.x, m);
         o.y = __shfl_xor_sync(0xffffffffu, v.y, m);
@@ -187,7 +187,6 @@ template <typename R> __device__ __forceinline__ V<R> expi(double angle) {
     }
 }
 
-template <typename R> __device__ __forceinline__ V<R> conjc(V<R> v) { return mkc<R>(v.x, -v.y); }
 
 // psi_x *= exp(-i tau E(x)) for an Ising energy E(x) = c + sum_i h_i z_i +
 // sum_{i<j} J_ij z_i z_j, z_i = 1 - 2 x_i. Split over the tile: the outside bits
@@ -274,9 +273,7 @@ __device__ __forceinline__ float2 fma_c2(float c, float2 v, float2 acc) {
 __device__ __forceinline__ double2 fma_c2(double c, double2 v, double2 acc) {
     return make_double2(fma(c, v.x, acc.x), fma(c, v.y, acc.y));
 }
-__device__ __forceinline__ ddc fma_c2(dd c, ddc v, ddc acc) {
-    return mkc<dd>(dd_fma(c, v.x, acc.x), dd_fma(c, v.y, acc.y));
-}
+__device__ __forceinline__ ddc fma_c2(dd c, ddc v, ddc acc) { return dd_fma_c2(c, v, acc); }
 
 // real rotation on register bit J as in-place shears (TOP_ROTS_R): x += s1 y,
 // then y += s2 x over the register pairs (x, y) that differ in bit J. Each
@@ -336,10 +333,10 @@ __device__ __forceinline__ void diag_block(V<R> *a, const TileParams<R> &p, cons
             const TileDFac<R> &d = p.dfac[f];
             if ((tbase & d.mo) == d.mo && (lt & d.mt) == d.mt) neg ^= d.a;
         }
-        if (neg & 0x80u) base = mkc<R>(-base.x, -base.y);
+        if (neg & 0x80u) base = cneg<R>(base);
 #pragma unroll
         for (int j = 0; j < RB; ++j)
-            if ((neg >> j) & 1u) u[j] = mkc<R>(-u[j].x, -u[j].y);
+            if ((neg >> j) & 1u) u[j] = cneg<R>(u[j]);
     }
     // thread and mixed factors (two independent product chains)
     V<R> b2 = mkc<R>(1, 0);
@@ -425,7 +422,7 @@ template <typename R, int RB, int A, int B, int PA, int PB>
 __device__ __forceinline__ void flip_pat(V<R> *a) {
 #pragma unroll
     for (int r = 0; r < (1 << RB); ++r)
-        if (((r >> A) & 1) != PA && ((r >> B) & 1) != PB) a[r] = mkc<R>(-a[r].x, -a[r].y);
+        if (((r >> A) & 1) != PA && ((r >> B) & 1) != PB) a[r] = cneg<R>(a[r]);
 }
 
 template <typename R, int RB, int A, int B>
@@ -450,7 +447,7 @@ __device__ __forceinline__ void dispatch_flip(V<R> *a, int A, int B, uint32_t mr
     const uint32_t x = fx | ((pat & 1u) << A) | (((pat >> 1) & 1u) << B);
 #pragma unroll
     for (int r = 0; r < (1 << RB); ++r)
-        if ((((uint32_t)r ^ x) & m) == m) a[r] = mkc<R>(-a[r].x, -a[r].y);
+        if ((((uint32_t)r ^ x) & m) == m) a[r] = cneg<R>(a[r]);
 }
 
 // Shared-memory position of tile-local index x under a transpose's swizzle
@@ -673,12 +670,15 @@ __device__ __forceinline__ void tile_op(V<R> *a, const TileParams<R> &p, const V
         for (int j = 0; j < RB; ++j) {
             if (!((am >> j) & 1u)) continue;
             switch (j) {
-            case 0: rot_reg<R, RB, 0>(a, M[0].x, M[0].y); break;
-            case 1: rot_reg<R, RB, 1>(a, M[1].x, M[1].y); break;
-            case 2: rot_reg<R, RB, 2>(a, M[2].x, M[2].y); break;
-            case 3: rot_reg<R, RB, 3>(a, M[3].x, M[3].y); break;
-            case 4: if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, M[4].x, M[4].y); break;
-            default: if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, M[5].x, M[5].y);
+            case 0: rot_reg<R, RB, 0>(a, re_of<R>(M[0]), im_of<R>(M[0])); break;
+            case 1: rot_reg<R, RB, 1>(a, re_of<R>(M[1]), im_of<R>(M[1])); break;
+            case 2: rot_reg<R, RB, 2>(a, re_of<R>(M[2]), im_of<R>(M[2])); break;
+            case 3: rot_reg<R, RB, 3>(a, re_of<R>(M[3]), im_of<R>(M[3])); break;
+            case 4:
+                if constexpr (RB > 4) rot_reg<R, RB, (RB > 4 ? 4 : 0)>(a, re_of<R>(M[4]), im_of<R>(M[4]));
+                break;
+            default:
+                if constexpr (RB > 5) rot_reg<R, RB, (RB > 5 ? 5 : 0)>(a, re_of<R>(M[5]), im_of<R>(M[5]));
             }
         }
         break;
@@ -689,11 +689,11 @@ __device__ __forceinline__ void tile_op(V<R> *a, const TileParams<R> &p, const V
         const V<R> *M = &mat[op.m];
 #pragma unroll
         for (int j = 0; j < kTileLaneBits; ++j) {
-            const V<R> cf = M[j];
-            if (cf.y == (R)0) continue;
+            const R cfx = re_of<R>(M[j]), cfy = im_of<R>(M[j]);
+            if (cfy == (R)0) continue;
             const int bit = (lane >> j) & 1;
-            const R cc = bit ? cf.x : -cf.x;
-            const bool tan_form = cf.y == (R)(ROT_TAN + 1);
+            const R cc = bit ? cfx : -cfx;
+            const bool tan_form = cfy == (R)(ROT_TAN + 1);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const V<R> v = shfl_xor_c<R>(a[r], 1 << j);
@@ -709,8 +709,9 @@ __device__ __forceinline__ void tile_op(V<R> *a, const TileParams<R> &p, const V
         if (req_ok()) dispatch_flip<R, RB>(a, op.a, op.b, op.mr, op.tkind, op.fx);
         break;
     case TOP_PROT:
-        if constexpr (MODE < 1) break;
-        if (req_ok()) {
+        // per-member tables: FP32 / FP64 passes only
+        if constexpr (MODE < 1 || is_dd<R>) break;
+        else if (req_ok()) {
             const V<R> *M = mat_of();
             // table: RY m[2] = (s, 0); RX m[2] = (0, -s)
             const R c = M[0].x, sn = op.b ? -M[2].y : M[2].x;
@@ -789,7 +790,7 @@ __device__ __forceinline__ void tile_store(V<R> *__restrict__ psi, const V<R> *a
     for (int r = 0; r < (1 << RB); ++r) {
         if constexpr (is_dd<R>)
             reinterpret_cast<double2 *>(psi)[gt ^ reg_offset<RB>(r, gr)] =
-                make_double2(to_double(a[r].x), to_double(a[r].y));
+                make_double2(to_double(re_of<dd>(a[r])), to_double(im_of<dd>(a[r])));
         else
             psi[gt ^ reg_offset<RB>(r, gr)] = a[r];
     }

@@ -177,13 +177,17 @@ struct Src {
 
 void real_lit(Src &o, float v) { o.f("%af", (double)v); }
 void real_lit(Src &o, double v) { o.f("%a", v); }
-void real_lit(Src &o, dd v) { o.f("{%af,%af}", (double)v.h, (double)v.l); }
 template <typename R> void cplx_lit(Src &o, const V<R> &v) {
-    o.s += "{";
-    real_lit(o, v.x);
-    o.s += ",";
-    real_lit(o, v.y);
-    o.s += "}";
+    if constexpr (is_dd<R>) {
+        // the paired layout: {{re.h, im.h}, {re.l, im.l}}
+        o.f("{{%af,%af},{%af,%af}}", (double)v.h.x, (double)v.h.y, (double)v.l.x, (double)v.l.y);
+    } else {
+        o.s += "{";
+        real_lit(o, v.x);
+        o.s += ",";
+        real_lit(o, v.y);
+        o.s += "}";
+    }
 }
 template <typename T> void int_list(Src &o, const T *a, int n) {
     o.s += "{";
