@@ -132,19 +132,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# GB300: 152 SMs x 128 FP32 lanes x 2 flops per FMA per clock; FP64 ~1.2 TFLOP/s
-# (FP64 FMA microbenchmark on this pool: 1.19 TFLOP/s).
+# GB300: 152 SMs x 128 FP32 lanes x 2 flops per FMA per clock. complex128
+# passes compute in double-float on the same FP32 units.
 SMS, FP32_LANES = 152, 128
-FP64_TFLOPS = 1.19
 
 
-def alu_peak_tflops(dtype: str, sm_mhz: float) -> float:
-    if dtype == "c64":
-        return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-    return FP64_TFLOPS
+def alu_peak_tflops(sm_mhz: float) -> float:
+    return SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 
 
-TILED_SOURCES = ("kernels_tiled.cu", "tiled.h", "plan_tiled.cpp", "tile_device.cuh", "tile_jit.cpp")
+TILED_SOURCES = ("kernels_tiled.cu", "tiled.h", "plan_tiled.cpp", "tile_device.cuh", "tile_jit.cpp", "device.cuh")
 LAUNCH_PROFILE = os.path.join(ROOT, "profiles", "launches_random_layer_n32_c64.md")
 
 
@@ -177,15 +174,16 @@ def roofline(name, rec, a, clk):
     bandwidth. A secondary ALU figure reports the same launches' arithmetic:
     flops are the implementation's own count of its rotation / diagonal-block
     decomposition (4 per amplitude per rotation, 12 per diagonal block, ...),
-    and the peak is the unit count times the sampled SM clock (FP32: 152 SMs x
-    128 lanes x 2 flops per FMA; complex128: FP64 at 1.19 TFLOP/s, an FP64 FMA
-    loop timed on this GPU)."""
+    and the peak is the FP32 unit count times the sampled SM clock (152 SMs x
+    128 lanes x 2 flops per FMA). complex128 passes run in double-float on the
+    same units: there the flops are the decomposition's count in complex128
+    operations, each of which costs ~15-20 FP32 operations."""
     tot_ms, launches, nbytes, nflops = rec
     if not launches or tot_ms <= 0:
         return None
     bw, bw_src = measured_peaks()
     sm = clk.get("sm_mhz") or 2070.0
-    alu = alu_peak_tflops(a.dtype, sm)
+    alu = alu_peak_tflops(sm)
     t = tot_ms / 1000.0
     gbs = nbytes / t / 1e9
     tfl = nflops / t / 1e12
@@ -198,9 +196,10 @@ def roofline(name, rec, a, clk):
             "bytes_per_launch": nbytes / launches,
             "alu": {"achieved": tfl, "peak": alu, "unit": "TFLOP/s", "frac": tfl / alu,
                     "flops_per_launch": nflops / launches,
-                    "flops_source": "the implementation's own count of its decomposition",
-                    "peak_source": ("FP32 units: 152 SMs x 128 lanes x 2 x median SM clock" if a.dtype == "c64"
-                                    else "FP64 FMA loop timed on GB300")}}
+                    "flops_source": "the implementation's own count of its decomposition" +
+                                    ("" if a.dtype == "c64" else
+                                     " (complex128 operations, each ~15-20 FP32 operations in double-float)"),
+                    "peak_source": "FP32 units: 152 SMs x 128 lanes x 2 x median SM clock"}}
 
 
 # ------------------------------------------------------------------ CPU oracle
