@@ -341,6 +341,9 @@ def variational_adjoint(steps: int = 5) -> dict:
             "forward_ms": t_fwd, "forward_plus_adjoint_ms": t_full, "hpsi_ms": t_hpsi,
             # the reverse sweep plus lambda = H psi, over the forward without it
             "adjoint_incl_hpsi_over_forward": (t_full - t_fwd + t_hpsi) / (t_fwd - t_hpsi),
+            # the reverse sweep including H psi over the forward including the
+            # energy (which needs H psi too)
+            "sweep_incl_hpsi_over_forward_incl_energy": (t_full - t_fwd + t_hpsi) / t_fwd,
             "adjoint_over_forward": (t_full - t_fwd) / t_fwd, "total_over_forward": t_full / t_fwd,
             "gradients_per_s": B * P / (t_full / 1000.0),
             "kernels_full_call": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
@@ -596,8 +599,16 @@ def random_layer_c128(n: int = 33, layers: int = 2) -> dict:
     st = qsim.State(n, dtype="c128")
     out = {"workload": f"random-layer circuit, 20 layers ({len(full)} gates), n={n}, complex128"}
     t = _time_cuda(lambda: st.init_basis(0).apply(full, mode="tiled"), 1, warmup=1)
+    qsim.profile_collect()
+    qsim.profile_enable(True)
+    st.init_basis(0).apply(full, mode="tiled")
+    torch.cuda.synchronize()
+    qsim.profile_enable(False)
+    ms, launches, nbytes, _ = qsim.profile_collect()["tiled"]
     out["tiled"] = {"ms": t, "gate_apps_per_s": len(full) / (t / 1000.0), "gates": len(full),
-                    "arithmetic": "double-float", "kernels": "specialised"}
+                    "arithmetic": "double-float", "kernels": "specialised", "passes": launches,
+                    "avg_pass_ms": ms / max(1, launches),
+                    "pass_hbm_frac": nbytes / (ms / 1000.0) / 1e9 / _peak_hbm() if ms else None}
     out["norm2_after"] = float(st.norm2()[0])
     for mode, fp64, key in (("tiled", True, "tiled_fp64"), ("unfused", False, "unfused"),
                             ("unfused", True, "unfused_fp64")):
@@ -639,6 +650,8 @@ def summary(line: dict) -> dict:
     if va:
         out["adjoint"] = {"fwd_ms": rnd(va["forward_ms"]), "full_ms": rnd(va["forward_plus_adjoint_ms"]),
                           "adj_incl_hpsi_over_fwd": rnd(va["adjoint_incl_hpsi_over_forward"], 3),
+                          "sweep_incl_hpsi_over_fwd_incl_energy":
+                              rnd(va.get("sweep_incl_hpsi_over_forward_incl_energy"), 3),
                           "total_over_fwd": rnd(va["total_over_forward"], 3)}
     for key, name in (("adiabatic_batch", "adiabatic"), ("adiabatic_batch_c128", "adiabatic_c128")):
         ab = sec.get(key)

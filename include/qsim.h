@@ -125,11 +125,18 @@ typedef struct qs_opts {
     int32_t flags;            /* QS_OPT_* bits, or 0 */
 } qs_opts;
 
-/* complex128 one-gate passes: dense 1- and 2-qubit gates run in double-float
-   arithmetic on the FP32 pipes by default (each double split into two floats,
-   47 significant bits, relative error per gate ~1e-14; GB300's FP64 rate would
-   bind them at a third of the HBM bandwidth). This flag runs them in FP64
-   instead (the plain complex128 simulator). */
+/* complex128 arithmetic. By default complex128 gates run in double-float
+   arithmetic on the FP32 pipes: each double is split into two floats (47
+   significant bits), products are exact FMA products and sums exact two-sums,
+   and the result is joined back into a double; the error per gate is a few
+   2^-47 of the amplitudes' magnitude (~1e-14). This covers one-gate passes of
+   dense 1- and 2-qubit gates and tiled passes without per-member angles or
+   gradients (GB300's FP64 rate would bind them at a third of the HBM
+   bandwidth or less). QS_OPT_C128_FP64 in qs_opts.flags runs every complex128
+   gate of the call in FP64 instead. Either way, one-gate passes of diagonal
+   gates and of dense gates on 3 to 5 qubits are FP64 (swaps move amplitudes
+   exactly), passes with per-member angles and the adjoint sweep are FP64, and
+   read-outs accumulate in FP64. */
 #define QS_OPT_C128_FP64 1
 
 typedef struct qs_state qs_state;
@@ -187,7 +194,9 @@ qs_status qs_apply_gates_batched(qs_state *s, const qs_gate *gates, size_t count
    tensor-core blocks (width 5 and 4; complex64, n >= 11) and the one-gate-
    per-pass kernels, timed once on a scratch copy of the state (skipped, with
    the tiled passes chosen, when no copy fits) and remembered per circuit
-   shape for the process. The kernel sequence is captured in a CUDA graph.
+   shape for the process. The tuner first times the tiled planner's pass
+   schedules (qs_plan_schedule) and uses the fastest for the tiled passes.
+   The kernel sequence is captured in a CUDA graph.
    params_dev/n_params as in qs_apply_gates_batched (the pointer is captured:
    execute reads the table's current contents). */
 typedef struct qs_plan qs_plan;
@@ -198,6 +207,12 @@ qs_status qs_plan_execute(qs_plan *p);
 /* Chosen mode and fusion width, the autotuner's best time in ms (-1 if not
    tuned) and the number of graph nodes; NULL outputs are skipped. */
 qs_status qs_plan_info(const qs_plan *p, int *mode, int *fuse_qubits, double *tuned_ms, size_t *graph_nodes);
+/* The tiled planner's pass schedule in the plan: select 0 = per pass, the
+   most gates among the greedy choice of tile bits and every window of
+   consecutive bits (the default); 1 = the greedy choice only; 2 = the windows
+   only; max_gates > 0 caps the gates of a pass (0: no cap). The autotuner
+   chooses among {0, 0}, {1, 0}, {2, 0} and {0, 32}; untuned plans use {0, 0}. */
+qs_status qs_plan_schedule(const qs_plan *p, int *select, int *max_gates);
 /* Release the plan (the state is not touched). NULL is a no-op. */
 qs_status qs_plan_destroy(qs_plan *p);
 

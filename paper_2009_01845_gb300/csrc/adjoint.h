@@ -28,6 +28,10 @@ template <typename R> struct PauliApplyP {
     R gcre[kPAMaxGroups];
     R gcim[kPAMaxGroups];
     uint8_t gconst[kPAMaxGroups];
+    // groups 0 .. run0 - 1 are constant groups with one coefficient (run0 = 0:
+    // none); with no earlier partial sum (accumulate = 0) the tile kernel adds
+    // their partner amplitudes and multiplies by the coefficient once
+    int run0;
     // the group of Z-only terms (X mask 0), or -1; for the shared-memory tile
     // kernel its terms sorted by the bits 8 .. 8 + log2(tile / 256) - 1 their Z
     // masks include (the bits that tell a thread's outputs apart): dord[dmb[m]

@@ -129,6 +129,16 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
             if (g == p.gdiag) {
 #pragma unroll
                 for (int j = 0; j < PER; ++j) acc[j] = cmadd<R>(mkc<R>(Dr[j], Di[j]), v[j], acc[j]);
+            } else if (g < p.run0) {
+                // the leading run of groups with one coefficient: partners
+                // summed, then multiplied once
+#pragma unroll
+                for (int j = 0; j < PER; ++j) acc[j] = mkc<R>(acc[j].x + v[j].x, acc[j].y + v[j].y);
+                if (g + 1 == p.run0) {
+                    const V<R> c = mkc<R>(p.gcre[g], p.gcim[g]);
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) acc[j] = cmul<R>(c, acc[j]);
+                }
             } else if (p.gconst[g]) {
                 const V<R> c = mkc<R>(p.gcre[g], p.gcim[g]);
 #pragma unroll
@@ -171,6 +181,54 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
         }
         groups[gi].push_back(t);
     }
+    // constant groups (no Z bits) first, the largest set with one coefficient
+    // leading, then the others in their order
+    {
+        auto coef = [&](size_t gi, double *re, double *im, bool *cst) {
+            *re = *im = 0.0;
+            *cst = true;
+            for (size_t t : groups[gi]) {
+                const qs_pauli_term &tm = terms[t];
+                const int ny = __builtin_popcountll(tm.x_mask & tm.z_mask) & 3;
+                const double c = tm.coeff;
+                *re += ny == 0 ? c : ny == 2 ? -c : 0.0;
+                *im += ny == 1 ? c : ny == 3 ? -c : 0.0;
+                if (tm.z_mask) *cst = false;
+            }
+        };
+        std::vector<size_t> ord(masks.size());
+        std::vector<double> cre(masks.size()), cim(masks.size());
+        std::vector<int> cst(masks.size());
+        for (size_t gi = 0; gi < masks.size(); ++gi) {
+            bool c;
+            coef(gi, &cre[gi], &cim[gi], &c);
+            cst[gi] = c;
+            ord[gi] = gi;
+        }
+        // the coefficient shared by the most constant groups
+        size_t lead = masks.size(), lead_n = 0;
+        for (size_t a = 0; a < masks.size(); ++a) {
+            if (!cst[a]) continue;
+            size_t c = 0;
+            for (size_t b = 0; b < masks.size(); ++b) c += cst[b] && cre[b] == cre[a] && cim[b] == cim[a];
+            if (c > lead_n) {
+                lead_n = c;
+                lead = a;
+            }
+        }
+        auto in_lead = [&](size_t a) {
+            return lead < masks.size() && cst[a] && cre[a] == cre[lead] && cim[a] == cim[lead];
+        };
+        std::stable_partition(ord.begin(), ord.end(), in_lead);
+        std::vector<uint64_t> m2;
+        std::vector<std::vector<size_t>> g2;
+        for (size_t i : ord) {
+            m2.push_back(masks[i]);
+            g2.push_back(std::move(groups[i]));
+        }
+        masks.swap(m2);
+        groups.swap(g2);
+    }
     const uint64_t total = (uint64_t)src.batch << n;
     ProfScope _ps(st, KC_HPSI, 2.0 * total * sizeof(V<R>), 8.0 * total * (double)count);
     bool first = true;
@@ -211,6 +269,11 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
             return QS_ERR_UNSUPPORTED;
         }
         p.gbeg[p.ng] = nt;
+        p.run0 = 0;
+        if (first)
+            while (p.run0 < p.ng && p.gconst[p.run0] && p.gcre[p.run0] == p.gcre[0] && p.gcim[p.run0] == p.gcim[0] &&
+                   p.gx[p.run0] != 0)
+                ++p.run0;
         p.gdiag = -1;
         for (int g = 0; g < p.ng; ++g)
             if (p.gx[g] == 0 && !p.gconst[g]) p.gdiag = g;

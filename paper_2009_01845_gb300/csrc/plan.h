@@ -16,6 +16,18 @@ qs_status run_gates(qs_state *s, std::vector<LGate> &gates, int mode, const qs_o
 qs_status run_trotter(qs_state *s, const qs_pauli_term *h0, size_t n_h0, const qs_pauli_term *h1,
                       size_t n_h1, double s_fixed, double dt, double T, int steps);
 
+// How the tiled planner chooses its passes (the autotuner times the
+// variants). select 0: the pass that takes the most gates among the greedy
+// choice of high bits and every window of consecutive high bits; 1: the greedy
+// choice only; 2: the windows only (the greedy choice where no window takes a
+// gate). max_gates > 0 caps the gates of a pass.
+struct TileSchedule {
+    int select = 0;
+    int max_gates = 0;
+};
+TileSchedule tile_schedule();  // the calling thread's (default: {0, 0})
+void set_tile_schedule(TileSchedule s);
+
 // Tiled multi-gate passes (falls back to one pass per gate for gates a tile
 // cannot express and for states smaller than a tile).
 // force_bit >= 0 (adjoint sweep): that index bit is kept in every tile and

@@ -23,6 +23,7 @@ struct qs_plan {
     int n_params = 0;
     qs_opts opts{};
     int mode = QS_MODE_TILED;
+    qsim::TileSchedule sched;  // tiled passes: the planner's schedule
     double tuned_ms = -1.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -38,8 +39,12 @@ qs_status with_jit_policy(int policy, const std::function<qs_status()> &f);
 
 namespace {
 
+struct Tuned {
+    int mode, width;
+    TileSchedule sched;
+};
 std::mutex g_tune_mu;
-std::map<std::string, std::pair<int, int>> g_tune_cache;  // shape key -> (mode, fuse width)
+std::map<std::string, Tuned> g_tune_cache;  // shape key -> the tuner's choice
 
 // a key for the circuit's shape: sizes, dtype, and every gate's kind and bits
 std::string shape_key(const qs_state *s, const std::vector<LGate> &G) {
@@ -65,24 +70,29 @@ size_t ptab_need(const qs_state *s, const std::vector<LGate> &G) {
 }
 
 qs_status run_mode(qs_state *s, std::vector<LGate> &G, int mode, int width, const double *params, int n_params,
-                   int flags = 0) {
+                   int flags = 0, TileSchedule sched = {}) {
     qs_opts o{};
     o.mode = mode;
     o.fuse_qubits = width;
     o.flags = flags;
+    struct Scope {
+        TileSchedule saved = tile_schedule();
+        explicit Scope(TileSchedule s) { set_tile_schedule(s); }
+        ~Scope() { set_tile_schedule(saved); }
+    } scope(sched);
     return run_gates(s, G, mode, &o, params, n_params);
 }
 
 // time one strategy on a scratch state holding a copy of s's amplitudes
 qs_status time_mode(qs_state *scratch, std::vector<LGate> &G, int mode, int width, const double *params,
-                    int n_params, double *ms) {
+                    int n_params, double *ms, TileSchedule sched = {}) {
     cudaEvent_t a, b;
     QS_CUDA_TRY(cudaEventCreate(&a));
     QS_CUDA_TRY(cudaEventCreate(&b));
-    qs_status st = run_mode(scratch, G, mode, width, params, n_params);  // warm-up (and buffers)
+    qs_status st = run_mode(scratch, G, mode, width, params, n_params, 0, sched);  // warm-up (and buffers)
     if (st == QS_OK) {
         cudaEventRecord(a, scratch->stream);
-        st = run_mode(scratch, G, mode, width, params, n_params);
+        st = run_mode(scratch, G, mode, width, params, n_params, 0, sched);
         cudaEventRecord(b, scratch->stream);
         cudaError_t e = cudaEventSynchronize(b);
         float t = 0.f;
@@ -104,8 +114,9 @@ static qs_status autotune(qs_plan *p) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            p->mode = it->second.first;
-            p->opts.fuse_qubits = it->second.second;
+            p->mode = it->second.mode;
+            p->opts.fuse_qubits = it->second.width;
+            p->sched = it->second.sched;
             return QS_OK;
         }
     }
@@ -146,15 +157,34 @@ static qs_status autotune(qs_plan *p) {
     }
     double best = 1e300;
     int best_mode = QS_MODE_TILED, best_w = 0;
-    // the timing runs specialise the tiled passes first (their warm-up run
-    // waits for the compiles), so the tiled candidate is timed as it will run
-    // and the capture finds its kernels ready
+    // tile schedules first, timed on the generic pass kernel (no compiles):
+    // the most gates per pass of greedy and window choices, either alone, and
+    // a cap of 32 gates per pass (shorter kernel bodies)
+    TileSchedule best_sched;
+    if (s->n >= tile_bits(s->dtype)) {
+        const TileSchedule scheds[] = {{0, 0}, {1, 0}, {2, 0}, {0, 32}};
+        double bs = 1e300;
+        for (const TileSchedule &sc : scheds) {
+            if (st != QS_OK) break;
+            double ms = 0.0;
+            st = with_jit_policy(QS_JIT_OFF, [&] {
+                return time_mode(&scratch, p->gates, QS_MODE_TILED, 0, p->params, p->n_params, &ms, sc);
+            });
+            if (st == QS_OK && ms < bs) {
+                bs = ms;
+                best_sched = sc;
+            }
+        }
+    }
+    // the strategies; the timing runs specialise the tiled passes first (their
+    // warm-up run waits for the compiles), so the tiled candidate is timed as
+    // it will run and the capture finds its kernels ready
     const int jp = jit_policy() == QS_JIT_OFF ? QS_JIT_OFF : QS_JIT_SYNC;
     for (auto &c : cand) {
         if (st != QS_OK) break;
         double ms = 0.0;
         st = with_jit_policy(jp, [&] {
-            return time_mode(&scratch, p->gates, c.first, c.second, p->params, p->n_params, &ms);
+            return time_mode(&scratch, p->gates, c.first, c.second, p->params, p->n_params, &ms, best_sched);
         });
         if (st == QS_OK && ms < best) {
             best = ms;
@@ -173,9 +203,10 @@ static qs_status autotune(qs_plan *p) {
     if (st != QS_OK) return st;
     p->mode = best_mode;
     p->opts.fuse_qubits = best_w;
+    p->sched = best_sched;
     p->tuned_ms = best;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = {best_mode, best_w};
+    g_tune_cache[key] = {best_mode, best_w, best_sched};
     return QS_OK;
 }
 
@@ -203,7 +234,7 @@ static qs_status capture(qs_plan *p) {
     if (e != cudaSuccess) {
         st = cuda_status(e, "cudaStreamBeginCapture");
     } else {
-        st = run_mode(s, p->gates, p->mode, p->opts.fuse_qubits, p->params, p->n_params, p->opts.flags);
+        st = run_mode(s, p->gates, p->mode, p->opts.fuse_qubits, p->params, p->n_params, p->opts.flags, p->sched);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cap, &g);
         if (st == QS_OK && e != cudaSuccess) st = cuda_status(e, "cudaStreamEndCapture");
@@ -304,6 +335,16 @@ qs_status qs_plan_info(const qs_plan *p, int *mode, int *fuse_qubits, double *tu
     if (fuse_qubits) *fuse_qubits = p->opts.fuse_qubits;
     if (tuned_ms) *tuned_ms = p->tuned_ms;
     if (graph_nodes) *graph_nodes = p->nodes;
+    return QS_OK;
+}
+
+qs_status qs_plan_schedule(const qs_plan *p, int *select, int *max_gates) {
+    if (!p) {
+        set_error("null plan");
+        return QS_ERR_ARG;
+    }
+    if (select) *select = p->sched.select;
+    if (max_gates) *max_gates = p->sched.max_gates;
     return QS_OK;
 }
 

@@ -1305,8 +1305,14 @@ qs_status trotter_queue(int n, const std::vector<double> &a0, const std::vector<
     return QS_OK;
 }
 
+thread_local TileSchedule t_schedule;
+TileSchedule tile_schedule() { return t_schedule; }
+void set_tile_schedule(TileSchedule s) { t_schedule = s; }
+
 qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *params, int n_params, int force_bit,
                     double *gpart, double param_sign) {
+    const TileSchedule sched = t_schedule;
+    const int max_gates = sched.max_gates > 0 ? std::min(sched.max_gates, kTileMaxOps) : kTileMaxOps;
     const int n = s->n;
     const int k = tile_bits(s->dtype);
     if (n < k) {
@@ -1368,15 +1374,15 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
                 }
                 out->high |= nb;
                 out->gates.push_back((int)i);
-                if ((int)out->gates.size() >= kTileMaxOps) break;
+                if ((int)out->gates.size() >= max_gates) break;
             }
         };
         PassPlan pp;
-        select(false, 0, &pp);
+        if (sched.select != 2) select(false, 0, &pp);
         // high bits fixed to a window of consecutive index bits: circuits with
         // nearest-neighbour structure keep a whole light cone inside one window;
         // the window (or the greedy choice) that takes the most gates wins
-        {
+        if (sched.select != 1) {
             const int w = nh - __builtin_popcountll(force);
             const int top = force_bit >= 0 ? force_bit : n;
             for (int b = kTileLaneBits; w > 0 && b + w <= top; ++b) {
@@ -1384,6 +1390,7 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
                 select(true, ((1ull << w) - 1ull) << b, &q);
                 if (q.gates.size() > pp.gates.size()) pp = std::move(q);
             }
+            if (pp.gates.empty() && sched.select == 2) select(false, 0, &pp);
         }
         if (pp.gates.empty()) {
             // the front gate cannot run in a tile

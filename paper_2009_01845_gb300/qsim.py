@@ -94,6 +94,7 @@ _SIGS = {
     "qs_plan_execute": ([P], None),
     "qs_plan_info": ([P, P, P, P, P], None),
     "qs_plan_destroy": ([P], None),
+    "qs_plan_schedule": ([P, P, P], None),
     "qs_evolve": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                    ctypes.c_int], None),
     "qs_schedule_gradient": ([P, P, ctypes.c_size_t, P, ctypes.c_size_t, P, ctypes.c_int, ctypes.c_double, P, P, P],
@@ -685,7 +686,10 @@ class Plan:
         _check(self.lib.qs_plan_info(self.handle, ctypes.byref(m), ctypes.byref(w), ctypes.byref(t),
                                      ctypes.byref(nodes)))
         name = {v: k for k, v in MODE.items()}[m.value]
-        return {"mode": name, "fuse_qubits": w.value, "tuned_ms": t.value, "graph_nodes": nodes.value}
+        sel, cap = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.qs_plan_schedule(self.handle, ctypes.byref(sel), ctypes.byref(cap)))
+        return {"mode": name, "fuse_qubits": w.value, "tuned_ms": t.value, "graph_nodes": nodes.value,
+                "schedule": (sel.value, cap.value)}
 
     def close(self):
         if getattr(self, "handle", None):

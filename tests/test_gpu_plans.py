@@ -25,6 +25,7 @@ def test_autotuned_plan_replays_the_circuit(qs, dtype):
     info = plan.info()
     assert info["graph_nodes"] > 0
     assert info["mode"] in ("tiled", "fused", "unfused")
+    assert info["schedule"] in ((0, 0), (1, 0), (2, 0), (0, 32))
     st.init_basis(0)
     plan.execute()
     plan.execute()               # the circuit twice

@@ -48,6 +48,8 @@ def emu(tmp_path_factory):
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
     lib.emu_apply_flags.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_int]
+    lib.emu_apply_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     lib.emu_last_error.restype = ctypes.c_char_p
     return lib
 
@@ -85,6 +87,31 @@ def test_random_layer_window_passes(emu, dtype):
     got = run_emulated(emu, n, gates, dtype)
     want = oracle.run_circuit(n, gates)
     assert np.max(np.abs(got - want)) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_pass_schedules(emu, dtype):
+    """Every pass schedule the autotuner times (most gates of greedy and
+    window choices, greedy only, windows only, at most 32 gates per pass)
+    gives the oracle's state; the cap needs at least gates / 32 passes and the
+    default no more passes than greedy alone on this nearest-neighbour
+    circuit."""
+    n = 18
+    gates = qi.random_layer_circuit(n, 12, seed=4)
+    want = oracle.run_circuit(n, gates)
+    arr, keep = qsim.marshal_gates(gates)
+    passes = {}
+    for sched in ((0, 0), (1, 0), (2, 0), (0, 32)):
+        psi = np.zeros(1 << n, dtype=np.complex128)
+        psi[0] = 1.0
+        npass = ctypes.c_int()
+        st = emu.emu_apply_schedule(n, dtype, arr, len(gates), psi.ctypes.data, sched[0], sched[1],
+                                    ctypes.byref(npass))
+        assert st == 0, emu.emu_last_error().decode()
+        assert np.max(np.abs(psi - want)) < TOL[dtype]
+        passes[sched] = npass.value
+    assert passes[(0, 32)] >= -(-len(gates) // 32)
+    assert passes[(0, 0)] <= passes[(1, 0)]
 
 
 @pytest.mark.parametrize("dtype", [0, 1])

@@ -332,8 +332,15 @@ template <typename R> static qs_status emulate_pass(qs_state *s, const TileParam
 }
 
 namespace qsim {
-qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) { return emulate_pass<float>(s, p); }
-qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) { return emulate_pass<double>(s, p); }
+static int g_passes = 0;  // tiled passes emulated
+qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) {
+    ++g_passes;
+    return emulate_pass<float>(s, p);
+}
+qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) {
+    ++g_passes;
+    return emulate_pass<double>(s, p);
+}
 }  // namespace qsim
 
 static int g_calls = 0;
@@ -364,6 +371,19 @@ int emu_apply_flags(int n, int dtype, const qs_gate *gates, int count, double *p
     }
     ++g_calls;
     return (int)run_tiled(&s, G, nullptr, 0);
+}
+
+// the same under a pass schedule of the planner (the autotuner's variants);
+// *passes receives the number of tiled passes it ran
+int emu_apply_schedule(int n, int dtype, const qs_gate *gates, int count, double *psi, int select, int max_gates,
+                       int *passes) {
+    const TileSchedule saved = tile_schedule();
+    set_tile_schedule(TileSchedule{select, max_gates});
+    const int p0 = g_passes;
+    const int st = emu_apply_flags(n, dtype, gates, count, psi, 0);
+    *passes = g_passes - p0;
+    set_tile_schedule(saved);
+    return st;
 }
 
 // The adjoint reverse sweep as the library's driver builds it, over a
