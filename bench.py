@@ -931,7 +931,7 @@ SECONDARY = {
     "adiabatic_batch": lambda: adiabatic_batch(),
     "adiabatic_batch_c128": lambda: adiabatic_batch(steps=50, dtype="c128"),
     "fused_tc": lambda: fused_tc(),
-    "unfused_passes": lambda: unfused_passes(),
+    "unfused_passes": lambda n=32: unfused_passes(n=n),
     "qft_n18_c128": lambda: qft_n18(),
     "random_layer_c128_n33": lambda: random_layer_c128(),
     "measurement": lambda: measurement(),
@@ -942,7 +942,10 @@ SECONDARY = {
 def main():
     a = parse()
     if a.only:
-        print(json.dumps({a.only: SECONDARY[a.only]()}), flush=True)
+        # --n sizes the one-gate passes (e.g. a small case for a profiler)
+        fn = SECONDARY[a.only]
+        res = fn(n=a.n) if a.only == "unfused_passes" else fn()
+        print(json.dumps({a.only: res}), flush=True)
         return
     if a.impl == "reference":
         run_reference(a)
