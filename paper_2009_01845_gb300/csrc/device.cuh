@@ -15,50 +15,53 @@ namespace qsim {
 // after every operation): complex128 amplitudes are computed in this form on
 // the FP32 pipes (GB300's FP64 rate is 1/64 of its FP32 rate), loaded from and
 // stored to memory as doubles. A double becomes h + l with 47 of its 53
-// significant bits (values below 2^-103 keep h alone, below 2^-126 flush to
-// zero); an operation's error is a few 2^-47 of its operands' magnitude.
+// significant bits (the rest dropped: < 2^-46 relative; values below 2^-103
+// keep h alone, below 2^-126 flush to zero); an operation's error is a few
+// 2^-47 of its operands' magnitude.
 // Products use the exact FMA product (Dekker's method with a fused
 // multiply-add), sums Knuth's exact two-sum.
 
 #ifdef __CUDACC__
-// d = h + l from the bit pattern: h takes the implicit bit and the top 23
-// fraction bits, l the remaining 29 rounded to 23 (integer operations only)
+// d = h + l from the bit pattern (integer operations only): h takes the
+// implicit bit and the top 23 fraction bits, the exponent re-biased in place;
+// l the next 23 fraction bits (the last 6 dropped: |d - h - l| < 2^-46 |d|).
+// Exact range 2^-126 <= |d| < 2^128; below it h is 0 (and l below 2^-103).
 __device__ __forceinline__ void df_split(double d, float &h, float &l) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+    const unsigned lo = (unsigned)__double2loint(d), hi = (unsigned)__double2hiint(d);
+    const unsigned ex = hi & 0x7ff00000u;  // biased exponent field, in place
     const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
-    const unsigned f23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const unsigned rem = lo & 0x1fffffffu;
-    h = e >= -126 ? __uint_as_float(sign | ((unsigned)(e + 127) << 23) | f23) : 0.f;
-    // l = rem 2^(e-52) ~ round(rem / 64) 2^(e-46): a float of exponent e+104
-    // and fraction round(rem / 64), less the same float with fraction 0
-    // (exact; a fraction of 2^23 carries into the exponent, still exact)
-    const unsigned eb = (unsigned)(e + 104) << 23;
-    const float t = __uint_as_float(eb + ((rem + 32u) >> 6)) - __uint_as_float(eb);
-    l = e >= -103 ? __uint_as_float(__float_as_uint(t) | sign) : 0.f;
+    // (hi - (896 << 20)) << 3 | lo >> 29: the float exponent (double bias
+    // 1023, float bias 127) and the fraction's top 23 bits; bit 31 is 0 in range
+    const unsigned hb = __funnelshift_l(lo, hi - (896u << 20), 3);
+    h = ex >= (897u << 20) ? __uint_as_float(hb | sign) : 0.f;
+    // l = (fraction bits 28..6) 2^(e-46): a float of exponent e + 104 and
+    // those bits as its fraction, less the same float with fraction 0 (exact)
+    const unsigned eb = ex * 8u - (919u << 23);  // (biased e - 919) << 23 = (e + 104 + 127 - 127) << 23
+    const float t = __uint_as_float(eb | ((lo >> 6) & 0x7fffffu)) - __uint_as_float(eb);
+    l = ex >= (920u << 20) ? __uint_as_float(__float_as_uint(t) | sign) : 0.f;
 }
 
 // the double nearest h + l, for |l| <= ulp(h): h's bits widened to a double,
 // then l added as a whole number of the double's ulps
 __device__ __forceinline__ double df_join(float h, float l) {
     const unsigned hb = __float_as_uint(h);
+    const unsigned ef = hb & 0x7f800000u;  // float exponent field, in place
+    if (ef == 0u) return 0.0;
     const unsigned sign = hb & 0x80000000u;
-    const int eh = (int)((hb >> 23) & 0xffu);
-    if (eh == 0) return 0.0;
-    unsigned long long db =
-        ((unsigned long long)(sign | ((unsigned)(eh + 896) << 20) | ((hb & 0x7fffffu) >> 3)) << 32) |
-        ((unsigned long long)(hb & 7u) << 29);
-    if (eh >= 52) {
-        // l in units of the double's ulp 2^(eh - 127 - 52): l 2^(179 - eh)
-        const float q = l * __uint_as_float((unsigned)(306 - eh) << 23);
-        long long k = __float2int_rn(q);
+    // hi: sign, exponent + 896, the fraction's top 20 bits; lo: its last 3
+    const unsigned hi = (((hb & 0x7fffffffu) >> 3) + (896u << 20)) | sign;
+    const unsigned lo = hb << 29;
+    long long k = 0;
+    if (ef >= (52u << 23)) {
+        // l in units of the double's ulp 2^(eh - 127 - 52): l 2^(179 - eh),
+        // the scale's exponent field 306 - eh
+        const float q = l * __uint_as_float((306u << 23) - ef);
+        k = __float2int_rn(q);
         if (sign) k = -k;  // the ulps count in the magnitude's direction
         // below a power of two the binade's ulp is half as large
-        if (k < 0 && (hb & 0x7fffffu) == 0) k *= 2;
-        db += (unsigned long long)k;
+        if (k < 0 && (hb & 0x7fffffu) == 0u) k *= 2;
     }
-    return __longlong_as_double((long long)db);
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo) + k);
 }
 
 // a + b = s + e exactly (Knuth's two-sum)

@@ -24,6 +24,61 @@ namespace qsim {
 
 namespace {
 
+// A sum of complex double-float products kept unnormalised: S holds the
+// exact running sum of the products' high parts (two-sums), E the low parts
+// and the two-sums' errors in FP32; one renormalisation at the end.
+struct ProdSum {
+    float2 S, E;
+};
+
+// the product a b as a first sum (the paired products of dd_cmul)
+__device__ __forceinline__ ProdSum prod_first(ddc a, ddc b) {
+    const float2 xh = make_float2(a.h.x, a.h.x), xl = make_float2(a.l.x, a.l.x);
+    const float2 yh = make_float2(-a.h.y, a.h.y), yl = make_float2(-a.l.y, a.l.y);
+    const float2 sh = make_float2(b.h.y, b.h.x), sl = make_float2(b.l.y, b.l.x);
+    const float2 np1 = pmul(pneg(xh), b.h);
+    const float2 np2 = pmul(pneg(yh), sh);
+    float2 q = padd(pfma(xh, b.h, np1), pfma(yh, sh, np2));
+    q = pfma(xh, b.l, q);
+    q = pfma(xl, b.h, q);
+    q = pfma(yh, sl, q);
+    q = pfma(yl, sh, q);
+    const float2 ns = padd(np1, np2);
+    const float2 bb = psub(ns, np1);
+    const float2 ne = padd(psub(np1, psub(ns, bb)), psub(np2, bb));
+    return ProdSum{pneg(ns), psub(q, ne)};
+}
+
+// acc + a b
+__device__ __forceinline__ void prod_add(ProdSum &acc, ddc a, ddc b) {
+    const float2 xh = make_float2(a.h.x, a.h.x), xl = make_float2(a.l.x, a.l.x);
+    const float2 yh = make_float2(-a.h.y, a.h.y), yl = make_float2(-a.l.y, a.l.y);
+    const float2 sh = make_float2(b.h.y, b.h.x), sl = make_float2(b.l.y, b.l.x);
+    const float2 np1 = pmul(pneg(xh), b.h);
+    const float2 np2 = pmul(pneg(yh), sh);
+    float2 q = padd(pfma(xh, b.h, np1), pfma(yh, sh, np2));
+    q = pfma(xh, b.l, q);
+    q = pfma(xl, b.h, q);
+    q = pfma(yh, sl, q);
+    q = pfma(yl, sh, q);
+    // S - np1 - np2 by two exact two-sums
+    const float2 s1 = psub(acc.S, np1);
+    const float2 b1 = psub(s1, acc.S);
+    const float2 e1 = psub(psub(acc.S, psub(s1, b1)), padd(np1, b1));
+    const float2 s2 = psub(s1, np2);
+    const float2 b2 = psub(s2, s1);
+    const float2 e2 = psub(psub(s1, psub(s2, b2)), padd(np2, b2));
+    acc.E = padd(acc.E, padd(padd(e1, e2), q));
+    acc.S = s2;
+}
+
+__device__ __forceinline__ ddc prod_result(const ProdSum &acc) {
+    ddc r;
+    r.h = padd(acc.S, acc.E);
+    r.l = psub(acc.E, psub(r.h, acc.S));
+    return r;
+}
+
 template <int K> struct DenseDFP {
     ddc m[(1 << K) * (1 << K)];  // row-major, split on the host
     uint64_t off[1 << K];
@@ -50,10 +105,11 @@ __global__ void __launch_bounds__(256) dense_df_kernel(double2 *__restrict__ psi
         }
 #pragma unroll
         for (int r = 0; r < D; ++r) {
-            ddc acc = dd_cmul(p.m[r * D], a[0]);
+            ProdSum acc = prod_first(p.m[r * D], a[0]);
 #pragma unroll
-            for (int c = 1; c < D; ++c) acc = dd_cadd(acc, dd_cmul(p.m[r * D + c], a[c]));
-            psi[base | p.off[r]] = make_double2(to_double(re_of<dd>(acc)), to_double(im_of<dd>(acc)));
+            for (int c = 1; c < D; ++c) prod_add(acc, p.m[r * D + c], a[c]);
+            const ddc w = prod_result(acc);
+            psi[base | p.off[r]] = make_double2(to_double(re_of<dd>(w)), to_double(im_of<dd>(w)));
         }
     }
 }
