@@ -136,7 +136,10 @@ typedef struct qs_opts {
    gate of the call in FP64 instead. Either way, one-gate passes of diagonal
    gates and of dense gates on 3 to 5 qubits are FP64 (swaps move amplitudes
    exactly), passes with per-member angles and the adjoint sweep are FP64, and
-   read-outs accumulate in FP64. */
+   read-outs accumulate in FP64. The double-float range is that of a float
+   pair: amplitudes of magnitude 2^128 or more, and non-finite ones, are not
+   represented (below 2^-126 they become 0); use the FP64 flag for such
+   states. */
 #define QS_OPT_C128_FP64 1
 
 typedef struct qs_state qs_state;
