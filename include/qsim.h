@@ -120,7 +120,9 @@ typedef struct qs_pauli_term {
 
 typedef struct qs_opts {
     int32_t mode;             /* QS_MODE_* */
-    int32_t tile_qubits;      /* tiled mode: tile width k (0 = default) */
+    int32_t tile_qubits;      /* tiled mode: tile width k; 0 or the kernels' own
+                                 width (13 complex64, 12 complex128), else
+                                 QS_ERR_UNSUPPORTED */
     int32_t fuse_qubits;      /* fused mode: block width (0 = 5) */
     int32_t flags;            /* QS_OPT_* bits, or 0 */
 } qs_opts;

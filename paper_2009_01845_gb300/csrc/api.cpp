@@ -9,6 +9,7 @@
 
 #include "internal.h"
 #include "plan.h"
+#include "tiled.h"
 
 namespace qsim {
 qs_status energy_gradient(qs_state *w, const std::vector<LGate> &G, const double *params, int n_params,
@@ -373,11 +374,17 @@ static qs_status lower_all(const qs_state *s, const qs_gate *gates, size_t count
     return QS_OK;
 }
 
-static qs_status check_opts(const qs_opts *o, int *mode) {
+static qs_status check_opts(const qs_state *s, const qs_opts *o, int *mode) {
     *mode = o ? o->mode : QS_MODE_AUTO;
     if (*mode < QS_MODE_AUTO || *mode > QS_MODE_FUSED_TC) {
         set_error("unknown mode %d", *mode);
         return QS_ERR_ARG;
+    }
+    // the tile width is the kernel's own (its register, lane and warp bits)
+    if (o && o->tile_qubits != 0 && o->tile_qubits != tile_bits(s->dtype)) {
+        set_error("tile width %d: the tiled kernels take %d bits for this precision", o->tile_qubits,
+                  tile_bits(s->dtype));
+        return QS_ERR_UNSUPPORTED;
     }
     if (o && (o->flags & ~QS_OPT_C128_FP64) != 0) {
         set_error("unknown opts.flags bits 0x%x", o->flags & ~QS_OPT_C128_FP64);
@@ -391,7 +398,7 @@ qs_status qs_apply_gates(qs_state *s, const qs_gate *gates, size_t count, const 
     clear_error();
     QS_TRY(check_state(s));
     int mode;
-    QS_TRY(check_opts(opts, &mode));
+    QS_TRY(check_opts(s, opts, &mode));
     std::vector<LGate> lg;
     QS_TRY(lower_all(s, gates, count, &lg));
     for (auto &g : lg)
@@ -408,7 +415,7 @@ qs_status qs_apply_gates_batched(qs_state *s, const qs_gate *gates, size_t count
     QS_TRY(check_state(s));
     QS_TRY(not_for_density(s, "batched parameters"));
     int mode;
-    QS_TRY(check_opts(opts, &mode));
+    QS_TRY(check_opts(s, opts, &mode));
     std::vector<LGate> lg;
     QS_TRY(lower_all(s, gates, count, &lg));
     for (size_t i = 0; i < lg.size(); ++i) {
@@ -942,7 +949,7 @@ qs_status qs_apply_channels(qs_state *s, const qs_channel *channels, size_t coun
         return QS_ERR_ARG;
     }
     int mode;
-    QS_TRY(check_opts(opts, &mode));
+    QS_TRY(check_opts(s, opts, &mode));
     std::vector<LGate> lg(count);
     for (size_t i = 0; i < count; ++i) {
         const qs_status st = lower_channel(s, channels[i], &lg[i]);

@@ -280,6 +280,11 @@ qs_status qs_plan_create(qs_state *s, const qs_gate *gates, size_t count, const 
             set_error("unknown opts.flags bits 0x%x", opts->flags & ~QS_OPT_C128_FP64);
             return QS_ERR_ARG;
         }
+        if (opts && opts->tile_qubits != 0 && opts->tile_qubits != tile_bits(s->dtype)) {
+            set_error("tile width %d: the tiled kernels take %d bits for this precision", opts->tile_qubits,
+                      tile_bits(s->dtype));
+            return QS_ERR_UNSUPPORTED;
+        }
         qs_plan *p = new qs_plan();
         p->s = s;
         p->params = params_dev;

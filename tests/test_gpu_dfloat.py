@@ -103,3 +103,43 @@ def test_batch_and_controls(qs):
     got = qs.State(n, batch=B, dtype="c128").set(psis).apply(gates, mode="unfused").get()
     for b in range(B):
         close(got[b], oracle.apply_circuit(psis[b].copy(), n, gates))
+
+
+@pytest.mark.parametrize("n", [12, 13, 16])
+def test_tiled_double_float_and_fp64(qs, n):
+    """Tiled complex128 passes: the default double-float kernels and the FP64
+    ones both match the oracle on a mixed circuit (controls, 2-qubit dense
+    gates, swaps, diagonals inside and outside the tile), and round
+    differently (the flag reaches the tiled kernels)."""
+    gates = qi.random_mixed_circuit(n, 150, seed=700 + n, max_controls=2, max_unitary_k=2)
+    psi0 = qi.random_state(n, 710 + n)
+    want = oracle.apply_circuit(psi0.copy(), n, gates)
+    a = qs.State(n, dtype="c128").set(psi0).apply(gates, mode="tiled").get()
+    b = qs.State(n, dtype="c128").set(psi0).apply(gates, mode="tiled", fp64=True).get()
+    close(a, want)
+    close(b, want)
+    assert not np.array_equal(a, b)
+
+
+def test_tiled_special_values(qs):
+    """A tiled pass over a state holding exact zeros, powers of two, values at
+    the bottom of the double-float range and full-significand values: the
+    oracle's result within the tolerance, and a layer of H twice returns the
+    state to within 1e-13."""
+    n = 13
+    r = qi.rng(93)
+    psi = r.normal(size=1 << n) + 1j * r.normal(size=1 << n)
+    psi[:64] = 0.0
+    psi[64:80] = 0.5
+    psi[80:96] = -0.25j
+    psi[96:104] = 1e-35
+    psi[104:112] = 1e-40 - 1e-39j
+    psi[112:120] = np.nextafter(0.125, 1.0)
+    psi /= np.linalg.norm(psi)
+    gates = qi.random_layer_circuit(n, 3, seed=94)
+    want = oracle.apply_circuit(psi.copy(), n, gates)
+    close(qs.State(n, dtype="c128").set(psi).apply(gates, mode="tiled").get(), want)
+    H = [qi.Gate("H", (q,)) for q in range(n)]
+    hh = qs.State(n, dtype="c128").set(psi).apply(H + H, mode="tiled").get()
+    assert float(np.max(np.abs(hh - psi))) <= 1e-13
+

@@ -290,3 +290,19 @@ def test_largest_batch_read_outs(qs):
     with pytest.raises(qs.QsimError) as ex:
         qs.State(n, batch=batch + 1, dtype="c128")
     assert ex.value.status == 1
+
+
+def test_tile_width_option(qs):
+    """The tile width is the kernels' own: 0 or that width are accepted, any
+    other is QS_ERR_UNSUPPORTED and leaves the state unchanged."""
+    n = 13
+    gates = qi.random_layer_circuit(n, 2, seed=95)
+    want = oracle.run_circuit(n, gates)
+    for dtype, k in (("c128", 12), ("c64", 13)):
+        st = qs.State(n, dtype=dtype).init_basis(0).apply(gates, mode="tiled", tile_qubits=k)
+        assert np.max(np.abs(st.get() - want)) < (1e-12 if dtype == "c128" else 1e-5)
+        st.init_basis(0)
+        with pytest.raises(qs.QsimError) as e:
+            st.apply(gates, mode="tiled", tile_qubits=k - 1)
+        assert e.value.status == 4
+        assert st.get()[0] == 1.0
