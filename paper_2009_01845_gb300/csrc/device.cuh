@@ -64,19 +64,6 @@ __device__ __forceinline__ double df_join(float h, float l) {
     return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo) + k);
 }
 
-// a + b = s + e exactly (Knuth's two-sum)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-// a + b = s + e for |a| >= |b| (three operations); otherwise off by at most
-// 2^-24 |b|
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    e = b - (s - a);
-}
 #endif  // __CUDACC__
 
 struct dd {
@@ -139,9 +126,11 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
 // sign flips by bit operations (exact, no FP instruction)
 __device__ __forceinline__ float2 pneg(float2 a) { return pfloat(pbits(a) ^ 0x8000000080000000ull); }
 __device__ __forceinline__ float2 pneg_hi(float2 a) { return pfloat(pbits(a) ^ 0x8000000000000000ull); }
-__device__ __forceinline__ float2 pneg_lo(float2 a) { return pfloat(pbits(a) ^ 0x0000000080000000ull); }
 
 // ---- complex double-float arithmetic on the lane pairs
+// The exact sums below are Knuth's two-sum (s = a + b, bb = s - a,
+// e = (a - (s - bb)) + (b - bb): a + b = s + e exactly, six operations) and
+// the renormalisations its three-operation form for |a| >= |b|.
 // a + b: exact two-sum of the high parts, then the low parts, renormalised
 __device__ __forceinline__ ddc dd_cadd(ddc a, ddc b) {
     const float2 s = padd(a.h, b.h);
