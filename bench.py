@@ -17,9 +17,10 @@ the single-state path does not shard without an exchange step), weak scaling.
 simulator) on the host cores on a bounded sample of the same workload.
 
 ``--only NAME`` runs one secondary workload alone (variational_adjoint,
-adiabatic_batch, fused_tc, unfused_passes, qft_n18_c128,
-random_layer_c128_n33, measurement) and prints its result as one JSON line: for
-profiling those kernels; it is not the benchmark line.
+variational_adjoint_c128, adiabatic_batch, adiabatic_batch_c128, fused_tc,
+unfused_passes, qft_n18_c128, random_layer_c128_n33, measurement,
+host_memory) and prints its result as one JSON line: for profiling those
+kernels; it is not the benchmark line.
 """
 from __future__ import annotations
 
@@ -313,10 +314,11 @@ def _time_cuda(fn, steps: int, warmup: int = 2, jit: bool = True) -> float:
     return e0.elapsed_time(e1) / steps
 
 
-def variational_adjoint(steps: int = 5) -> dict:
+def variational_adjoint(steps: int = 5, dtype: str = "c64") -> dict:
     """Variational ansatz n = 20, 10 layers of RY + CZ ladder, 256 parameter sets
-    (seed 4), complex64, TFIM energy g = 1: forward (incl. lambda = H psi and the
-    energy) vs forward + adjoint reverse sweep, through qs_energy_gradient."""
+    (seed 4), complex64 (complex128: the same in double-float), TFIM energy
+    g = 1: forward (incl. lambda = H psi and the energy) vs forward + adjoint
+    reverse sweep, through qs_energy_gradient."""
     import torch
     from paper_2009_01845_gb300 import inputs as qi
     from paper_2009_01845_gb300 import qsim
@@ -324,7 +326,7 @@ def variational_adjoint(steps: int = 5) -> dict:
     th = qi.variational_params(B, L, n, seed=4)
     tmpl = qi.variational_circuit(n, th[0])
     pidx, P = qsim.param_indices(tmpl)
-    eng = qsim.EnergyGradient(n, B, tmpl, pidx, qi.tfim_terms(n, 1.0), dtype="c64")
+    eng = qsim.EnergyGradient(n, B, tmpl, pidx, qi.tfim_terms(n, 1.0), dtype=dtype)
     params = torch.tensor(th.reshape(B, -1), device="cuda")
     energy = torch.empty(B, dtype=torch.float64, device="cuda")
     grad = torch.empty(B, P, dtype=torch.float64, device="cuda")
@@ -337,7 +339,7 @@ def variational_adjoint(steps: int = 5) -> dict:
     qsim.profile_enable(False)
     prof = qsim.profile_collect()
     t_hpsi = prof.get("hpsi", (0.0,))[0]
-    return {"workload": "variational n=20, 10 layers, batch 256, complex64, TFIM g=1",
+    return {"workload": f"variational n=20, 10 layers, batch 256, {dtype}, TFIM g=1",
             "forward_ms": t_fwd, "forward_plus_adjoint_ms": t_full, "hpsi_ms": t_hpsi,
             # the reverse sweep plus lambda = H psi, over the forward without it
             "adjoint_incl_hpsi_over_forward": (t_full - t_fwd + t_hpsi) / (t_fwd - t_hpsi),
@@ -646,6 +648,10 @@ def summary(line: dict) -> dict:
            "e2e_gate_per_s": rnd(get(line, "e2e", "value")),
            "cpu_gate_per_s": rnd(get(line, "cpu_baseline", "value")),
            "cpu_cores": get(line, "cpu_baseline", "cores")}
+    va = sec.get("variational_adjoint_c128")
+    if va:
+        out["adjoint_c128"] = {"fwd_ms": rnd(va["forward_ms"]), "full_ms": rnd(va["forward_plus_adjoint_ms"]),
+                               "total_over_fwd": rnd(va["total_over_forward"], 3)}
     va = sec.get("variational_adjoint")
     if va:
         out["adjoint"] = {"fwd_ms": rnd(va["forward_ms"]), "full_ms": rnd(va["forward_plus_adjoint_ms"]),
@@ -928,6 +934,7 @@ def host_memory(n: int = 34, layers: int = 2, device_gib: int = 16) -> dict:
 
 SECONDARY = {
     "variational_adjoint": lambda: variational_adjoint(),
+    "variational_adjoint_c128": lambda: variational_adjoint(steps=2, dtype="c128"),
     "adiabatic_batch": lambda: adiabatic_batch(),
     "adiabatic_batch_c128": lambda: adiabatic_batch(steps=50, dtype="c128"),
     "fused_tc": lambda: fused_tc(),

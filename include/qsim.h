@@ -132,13 +132,12 @@ typedef struct qs_opts {
    significant bits), products are exact FMA products and sums exact two-sums,
    and the result is joined back into a double; the error per gate is a few
    2^-47 of the amplitudes' magnitude (~1e-14). This covers one-gate passes of
-   dense 1- and 2-qubit gates and tiled passes without per-member angles or
-   gradients (GB300's FP64 rate would bind them at a third of the HBM
-   bandwidth or less). QS_OPT_C128_FP64 in qs_opts.flags runs every complex128
+   dense 1- and 2-qubit gates and tiled passes, per-member angles and the
+   adjoint sweep's gradient ops included (GB300's FP64 rate would bind them
+   at a third of the HBM bandwidth or less). QS_OPT_C128_FP64 in qs_opts.flags runs every complex128
    gate of the call in FP64 instead. Either way, one-gate passes of diagonal
    gates and of dense gates on 3 to 5 qubits are FP64 (swaps move amplitudes
-   exactly), passes with per-member angles and the adjoint sweep are FP64, and
-   read-outs accumulate in FP64. The double-float range is that of a float
+   exactly), and read-outs and gradient partials accumulate in FP64. The double-float range is that of a float
    pair: amplitudes of magnitude 2^128 or more, and non-finite ones, are not
    represented (below 2^-126 they become 0); use the FP64 flag for such
    states. */
@@ -491,7 +490,9 @@ qs_status qs_apply_channels(qs_state *s, const qs_channel *channels, size_t coun
    compiled in (a few percent faster, e.g. for a circuit run many times with
    fixed angles; queued in the background; one kernel per set of values). The
    environment variable QSIM_JIT = off, tiered, eager or sync (with "+fold"
-   appended for QS_JIT_FOLD) sets the initial policy. Process-wide. */
+   appended for QS_JIT_FOLD) sets the initial policy. Process-wide.
+   Diagnostics on stderr: QSIM_JIT_VERBOSE (set) prints each compile's time and
+   log; QSIM_PLAN_STATS (set) prints each tiled pass's op and stage counts. */
 #define QS_JIT_OFF 0
 #define QS_JIT_TIERED 1
 #define QS_JIT_EAGER 2

@@ -43,6 +43,7 @@ static qs_status with_view(qs_state *base, int n, int ms, size_t offset_amps, F 
     base->gtab_bytes = v.gtab_bytes;
     base->ptab = v.ptab;
     base->ptab_bytes = v.ptab_bytes;
+    base->ptab_dd = v.ptab_dd;
     base->itab = v.itab;
     base->itab_bytes = v.itab_bytes;
     base->ithr = v.ithr;

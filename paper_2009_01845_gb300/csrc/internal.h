@@ -32,6 +32,7 @@ struct qs_state {
     // per-member matrices of all batched-parameter gates of one tiled run
     void *ptab = nullptr;
     size_t ptab_bytes = 0;
+    int ptab_dd = 0;  // the table holds double-float pairs (complex128 passes in double-float)
     // Ising coefficients of the Trotter diagonal (see tiled.h); stride 0 = shared
     double *itab = nullptr;
     size_t itab_bytes = 0;
@@ -146,8 +147,11 @@ qs_status k_sample(qs_state *s, int member, const double *u_dev, uint64_t shots,
 // block in entry 0. slot j uses column pidx[j] of the parameter
 // table, gate kind kind[j], angle sign * theta. Fills s->ptab as
 // [member][slot][4] in the state's precision; *stride = entries per member.
+// (dd_table: a complex128 table as double-float pairs, for double-float passes;
+// s->ptab_dd records the format)
 qs_status k_param_table(qs_state *s, const std::vector<int> &pidx, const std::vector<int> &kind,
-                        const double *params_dev, int n_params, double sign, uint32_t *stride);
+                        const double *params_dev, int n_params, double sign, uint32_t *stride,
+                        bool dd_table = false);
 // batched-parameter rotation (RX RY RZ U1 CU1) of one gate
 qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params_dev, int n_params,
                              double sign = 1.0);

@@ -1086,13 +1086,15 @@ static qs_status param_table_t(qs_state *s, const std::vector<int> &pidx, const 
 }
 
 qs_status k_param_table(qs_state *s, const std::vector<int> &pidx, const std::vector<int> &kind,
-                        const double *params, int n_params, double sign, uint32_t *stride) {
+                        const double *params, int n_params, double sign, uint32_t *stride, bool dd_table) {
     if (pidx.size() > 32767) {
         set_error("too many batched-parameter gates");
         return QS_ERR_ARG;
     }
-    return s->dtype == QS_C64 ? param_table_t<float>(s, pidx, kind, params, n_params, sign, stride)
-                              : param_table_t<double>(s, pidx, kind, params, n_params, sign, stride);
+    s->ptab_dd = s->dtype == QS_C128 && dd_table;
+    if (s->dtype == QS_C64) return param_table_t<float>(s, pidx, kind, params, n_params, sign, stride);
+    return dd_table ? param_table_t<dd>(s, pidx, kind, params, n_params, sign, stride)
+                    : param_table_t<double>(s, pidx, kind, params, n_params, sign, stride);
 }
 
 qs_status k_apply_param_gate(qs_state *s, const LGate &g, const double *params, int n_params, double sign) {

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(32 << TileCfg<R>::WB, TileCfg<R>::kMinBlocks)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw + (sizeof(V<R>) << p.k));
     uint16_t *ltab = reinterpret_cast<uint16_t *>(tab + p.n_stages * (NW * 32));
-    __shared__ R gsm[kTileMaxGrad][NW];
+    __shared__ GradT<R> gsm[kTileMaxGrad][NW];
     __shared__ V<R> s_e[16];
     __shared__ V<R> s_qp[NR];
     const TileScratch<R> sc{gsm, s_e, s_qp};
@@ -214,23 +214,23 @@ template <typename R> static int kernel_mode(const TileParams<R> &p) {
 qs_status k_tiled_pass_c64(qs_state *s, const TileParams<float> &p) {
     return launch_tiled_t<float>(s, p, kernel_mode(p));
 }
-// A complex128 pass runs in double-float arithmetic unless FP64 is asked for
-// or it reads per-member matrices or takes gradients (those stay in FP64).
-// The descriptor converts in place: its values (matrix entries, diagonal
-// factors) become float pairs, everything else is copied.
-static bool double_float_pass(const TileParams<double> &p) {
-    if (c128_fp64() || p.n_grad > 0) return false;
+// A complex128 pass runs in double-float arithmetic unless FP64 is asked for;
+// per-member matrices must then be in a double-float table (s->ptab_dd). The
+// descriptor converts in place: its values (matrix entries, diagonal factors)
+// become float pairs, everything else is copied.
+static bool double_float_pass(const qs_state *s, const TileParams<double> &p) {
+    if (c128_fp64()) return false;
     for (int st = 0; st < p.n_stages; ++st)
         for (int o = p.st[st].op_begin; o < p.st[st].op_end; ++o)
-            if (p.op[o].pm || p.op[o].type == TOP_PROT || p.op[o].type == TOP_GRAD) return false;
+            if (p.op[o].pm && !s->ptab_dd) return false;
     return true;
 }
 
 qs_status k_tiled_pass_c128(qs_state *s, const TileParams<double> &p) {
-    if (!double_float_pass(p)) return launch_tiled_t<double>(s, p, kernel_mode(p));
+    if (!double_float_pass(s, p)) return launch_tiled_t<double>(s, p, kernel_mode(p));
     static thread_local TileParams<dd> q;
     std::memcpy(&q, &p, sizeof(p));
-    q.pmat = nullptr;
+    q.pmat = s->ptab_dd ? reinterpret_cast<const ddc *>(p.pmat) : nullptr;
     auto cv = [](double2 v) { return mkc<dd>(dd(v.x), dd(v.y)); };
     for (int i = 0; i < kTileMaxMat; ++i) q.mat[i] = cv(p.mat[i]);
     for (int f = 0; f < kTileMaxDFac; ++f) {

@@ -144,6 +144,7 @@ static qs_status autotune(qs_plan *p) {
     scratch.gtab_bytes = 0;
     scratch.ptab = nullptr;
     scratch.ptab_bytes = 0;
+    scratch.ptab_dd = 0;
     scratch.itab = nullptr;
     scratch.itab_bytes = 0;
     scratch.ithr = nullptr;

@@ -1341,7 +1341,11 @@ qs_status run_tiled(qs_state *s, const std::vector<LGate> &G, const double *para
             skind.push_back(G[i].kind);
         }
     uint32_t pm_stride = 0;
-    if (!spidx.empty()) QS_TRY(k_param_table(s, spidx, skind, params, n_params, param_sign, &pm_stride));
+    // complex128 passes read a double-float table (their kernels are
+    // double-float unless FP64 is asked for)
+    if (!spidx.empty())
+        QS_TRY(k_param_table(s, spidx, skind, params, n_params, param_sign, &pm_stride,
+                             s->dtype == QS_C128 && !c128_fp64()));
     std::vector<char> done(G.size(), 0);
     size_t first = 0;
     while (true) {

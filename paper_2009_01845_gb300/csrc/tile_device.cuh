@@ -289,6 +289,15 @@ __device__ __forceinline__ void rot_reg(V<R> *a, R s1, R s2) {
     }
 }
 
+// -i v for a double-float complex v: (v.im, -v.re), lanes swapped, the new
+// imaginary lane negated
+__device__ __forceinline__ ddc mul_minus_i(ddc v) {
+    ddc r;
+    r.h = make_float2(v.h.y, -v.h.x);
+    r.l = make_float2(v.l.y, -v.l.x);
+    return r;
+}
+
 // Value of an outside-only factor for this tile.
 template <typename R>
 __device__ __forceinline__ V<R> outside_factor(const TileDFac<R> &d, const TileDFac<R> &dv, uint64_t tbase) {
@@ -396,6 +405,10 @@ __device__ __forceinline__ void prot_reg(V<R> *a, R c, R s, bool rx, uint32_t mr
         if (!rx) {
             a[r] = fma_c2(c, x, fma_c2(-s, y, mkc<R>(0, 0)));
             a[r | (1 << J)] = fma_c2(c, y, fma_c2(s, x, mkc<R>(0, 0)));
+        } else if constexpr (is_dd<R>) {
+            // c x - i s y and c y - i s x: -i v = (v.im, -v.re)
+            a[r] = fma_c2(s, mul_minus_i(y), fma_c2(c, x, mkc<R>(0, 0)));
+            a[r | (1 << J)] = fma_c2(s, mul_minus_i(x), fma_c2(c, y, mkc<R>(0, 0)));
         } else {
             a[r] = mkc<R>(c * x.x + s * y.y, c * x.y - s * y.x);
             a[r | (1 << J)] = mkc<R>(c * y.x + s * x.y, c * y.y - s * x.x);
@@ -571,10 +584,90 @@ __device__ __forceinline__ void tile_transpose(V<R> *a, unsigned char *smem, con
     __syncthreads();
 }
 
+// Per-warp gradient sums: in the state's precision, double for double-float.
+template <typename R> struct GradType { using type = R; };
+template <> struct GradType<dd> { using type = double; };
+template <typename R> using GradT = typename GradType<R>::type;
+
+// Gradient op (TOP_GRAD) in double-float: sum_r w_r conj(lambda_r) phi_r over
+// the thread's registers as a complex double-float sum (w_r = +-1: the Y
+// generator's sign by the target bit, Z's by the target bit; phi the partner
+// across the target for X and Y), summed over the warp, then the generator's
+// component (X, Z, projector: the imaginary part; Y: the real part) as a
+// double into the warp's slot.
+__device__ __forceinline__ ddc grad_term_dd(ddc la, ddc ph, bool neg) {
+    const ddc t = dd_cmul(conjc<dd>(la), ph);
+    return neg ? cneg<dd>(t) : t;
+}
+
+template <int RB, int J>
+__device__ __forceinline__ ddc grad_xy_reg_dd(const ddc *a, int gen, uint32_t mr) {
+    constexpr int H = 1 << (RB - 1);
+    ddc acc = mkc<dd>(dd(0.f, 0.f), dd(0.f, 0.f));
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+        if ((r & mr) != mr) continue;
+        acc = dd_cadd(acc, grad_term_dd(a[r + H], a[r ^ (1 << J)], gen == GEN_Y && !((r >> J) & 1)));
+    }
+    return acc;
+}
+
+template <int RB>
+__device__ __forceinline__ void grad_dd(const ddc *a, const TileOp &op, bool ok, uint32_t lt, uint64_t tbase,
+                                        int lane, int warp, double (*gsm)[1 << TileCfg<dd>::WB]) {
+    constexpr int H = 1 << (RB - 1);
+    const uint32_t mr = op.mr;
+    ddc acc = mkc<dd>(dd(0.f, 0.f), dd(0.f, 0.f));
+    if (op.b == GEN_X || op.b == GEN_Y) {
+        if (op.tkind == TB_REG) {
+            if (ok) {
+                switch (op.a) {
+                case 0: acc = grad_xy_reg_dd<RB, 0>(a, op.b, mr); break;
+                case 1: acc = grad_xy_reg_dd<RB, 1>(a, op.b, mr); break;
+                case 2: acc = grad_xy_reg_dd<RB, 2>(a, op.b, mr); break;
+                default:
+                    if constexpr (RB > 4) acc = grad_xy_reg_dd<RB, (RB > 4 ? 3 : 0)>(a, op.b, mr);
+                    break;
+                }
+            }
+        } else {
+            // target on lane bit op.a: partner phi by shuffle (every lane takes part)
+            const int bit = (lane >> op.a) & 1;
+#pragma unroll
+            for (int r = 0; r < H; ++r) {
+                const ddc ph = shfl_xor_c<dd>(a[r], 1 << op.a);
+                if (ok && (r & mr) == mr) acc = dd_cadd(acc, grad_term_dd(a[r + H], ph, op.b == GEN_Y && !bit));
+            }
+        }
+    } else if (ok) {
+        // diagonal generator: Z on one bit, or the all-ones projector
+        bool tz = false;
+        if (op.b == GEN_Z && op.tkind != TB_REG)
+            tz = op.tkind == TB_THREAD ? ((lt & (uint32_t)op.tmask) != 0) : ((tbase & op.tmask) != 0);
+#pragma unroll
+        for (int r = 0; r < H; ++r) {
+            if ((r & mr) != mr) continue;
+            bool neg = false;
+            if (op.b == GEN_Z) neg = op.tkind == TB_REG ? (((r >> op.a) & 1) != 0) : tz;
+            acc = dd_cadd(acc, grad_term_dd(a[r + H], a[r], neg));
+        }
+    }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        ddc other;
+        other.h.x = __shfl_down_sync(0xffffffffu, acc.h.x, o2);
+        other.h.y = __shfl_down_sync(0xffffffffu, acc.h.y, o2);
+        other.l.x = __shfl_down_sync(0xffffffffu, acc.l.x, o2);
+        other.l.y = __shfl_down_sync(0xffffffffu, acc.l.y, o2);
+        acc = dd_cadd(acc, other);
+    }
+    if (lane == 0) gsm[op.gl][warp] = to_double(op.b == GEN_Y ? re_of<dd>(acc) : im_of<dd>(acc));
+}
+
 // Scratch a CTA's ops share: per-warp gradient sums, the Ising op's per-tile
 // factors and register-pair factors.
 template <typename R> struct TileScratch {
-    R (*gsm)[1 << TileCfg<R>::WB];
+    GradT<R> (*gsm)[1 << TileCfg<R>::WB];
     V<R> *s_e;
     V<R> *s_qp;
 };
@@ -709,18 +802,18 @@ __device__ __forceinline__ void tile_op(V<R> *a, const TileParams<R> &p, const V
         if (req_ok()) dispatch_flip<R, RB>(a, op.a, op.b, op.mr, op.tkind, op.fx);
         break;
     case TOP_PROT:
-        // per-member tables: FP32 / FP64 passes only
-        if constexpr (MODE < 1 || is_dd<R>) break;
-        else if (req_ok()) {
+        if constexpr (MODE < 1) break;
+        if (req_ok()) {
             const V<R> *M = mat_of();
             // table: RY m[2] = (s, 0); RX m[2] = (0, -s)
-            const R c = M[0].x, sn = op.b ? -M[2].y : M[2].x;
+            const R c = re_of<R>(M[0]), sn = op.b ? -im_of<R>(M[2]) : re_of<R>(M[2]);
             dispatch_prot<R, RB>(a, op.a, c, sn, op.b != 0, op.mr);
         }
         break;
     case TOP_GRAD: {
-        // gradients are taken in FP32 / FP64 passes only (no double-float sweep)
-        if constexpr (FULL && !is_dd<R>) {
+        if constexpr (FULL && is_dd<R>) {
+            grad_dd<RB>(a, op, req_ok(), lt, tbase, lane, warp, sc.gsm);
+        } else if constexpr (FULL) {
         const bool ok = req_ok();
         const uint32_t mr = op.mr;
         constexpr int H = NR / 2;
@@ -802,16 +895,14 @@ template <typename R>
 __device__ __forceinline__ void tile_grad_flush(const TileParams<R> &p, const TilePtrs<R> &q, uint64_t t,
                                                 const TileScratch<R> &sc) {
     constexpr int NW = 1 << TileCfg<R>::WB;
-    if constexpr (!is_dd<R>) {
-        __syncthreads();
-        if ((int)threadIdx.x < p.n_grad) {
-            double sum = 0.0;
+    __syncthreads();
+    if ((int)threadIdx.x < p.n_grad) {
+        double sum = 0.0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) sum += (double)sc.gsm[threadIdx.x][w];
-            q.gpart[(uint64_t)p.gslot[threadIdx.x] * p.total_tiles + t] = sum;
-        }
-        __syncthreads();
+        for (int w = 0; w < NW; ++w) sum += (double)sc.gsm[threadIdx.x][w];
+        q.gpart[(uint64_t)p.gslot[threadIdx.x] * p.total_tiles + t] = sum;
     }
+    __syncthreads();
 }
 
 }  // namespace qsim

@@ -276,7 +276,7 @@ template <typename R> std::string generate(const TileParams<R> &P, bool folded) 
         "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
         "  uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw + (sizeof(V<R>) << kP.k));\n"
         "  uint16_t *ltab = reinterpret_cast<uint16_t *>(tab + kP.n_stages * (NW * 32));\n"
-        "  __shared__ R gsm[kTileMaxGrad][NW];\n"
+        "  __shared__ GradT<R> gsm[kTileMaxGrad][NW];\n"
         "  __shared__ V<R> s_e[16];\n"
         "  __shared__ V<R> s_qp[1 << RB];\n"
         "  const TileScratch<R> sc{gsm, s_e, s_qp};\n"

@@ -286,7 +286,8 @@ class State:
         del keep
         return self
 
-    def apply_batched(self, gates: Sequence[Gate], param_index: Sequence[int], params, mode: str = "auto"):
+    def apply_batched(self, gates: Sequence[Gate], param_index: Sequence[int], params, mode: str = "auto",
+                      fp64: bool = False):
         """``params``: CUDA float64 tensor (batch, n_params); gate i takes its angle
         from column param_index[i] when that is >= 0."""
         import torch
@@ -296,7 +297,7 @@ class State:
         if params.dim() != 2 or params.shape[0] != self.batch:
             raise ValueError("params must have shape (batch, n_params)")
         arr, keep = marshal_gates(gates, param_index)
-        o = opts(mode)
+        o = opts(mode, fp64=fp64)
         _check(self.lib.qs_apply_gates_batched(self.handle, arr, len(gates),
                                                ctypes.c_void_p(params.data_ptr()),
                                                int(params.shape[1]), ctypes.byref(o)))

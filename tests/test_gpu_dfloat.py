@@ -143,3 +143,38 @@ def test_tiled_special_values(qs):
     hh = qs.State(n, dtype="c128").set(psi).apply(H + H, mode="tiled").get()
     assert float(np.max(np.abs(hh - psi))) <= 1e-13
 
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_tiled_per_member_angles(qs, fp64):
+    """Tiled complex128 passes whose rotations take per-member angles (RX, RY
+    as per-member rotations, RZ, U1 and CU1 as per-member diagonals), read
+    from a double-float table by default and an FP64 one with the flag: every
+    member against the oracle with its own angles."""
+    import torch
+    n, B = 13, 3
+    r = qi.rng(97)
+    gates, pidx = [], []
+    P = 0
+    for layer in range(3):
+        for q in range(n):
+            kind = ("RX", "RY", "RZ", "U1")[(q + layer) % 4]
+            gates.append(qi.Gate(kind, (q,), (), (0.0,)))
+            pidx.append(P)
+            P += 1
+        for q in range(layer % 2, n - 1, 2):
+            gates.append(qi.Gate("CZ", (q, q + 1)))
+            pidx.append(-1)
+        gates.append(qi.Gate("CU1", (layer, n - 1 - layer), (), (0.0,)))
+        pidx.append(P)
+        P += 1
+        gates.append(qi.Gate("U3", ((5 * layer) % n,), (), tuple(r.uniform(0, 6.28, 3))))
+        pidx.append(-1)
+    th = r.uniform(0.0, 2.0 * np.pi, size=(B, P))
+    params = torch.tensor(th, dtype=torch.float64, device="cuda")
+    psis = np.stack([qi.random_state(n, 980 + b) for b in range(B)])
+    st = qs.State(n, batch=B, dtype="c128").set(psis)
+    got = st.apply_batched(gates, pidx, params, mode="tiled", fp64=fp64).get()
+    for b in range(B):
+        gb = [g._replace(params=(float(th[b, pi]),)) if pi >= 0 else g for g, pi in zip(gates, pidx)]
+        close(got[b], oracle.apply_circuit(psis[b].copy(), n, gb))

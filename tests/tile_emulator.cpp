@@ -87,10 +87,11 @@ qs_status k_apply_param_gate(qs_state *, const LGate &, const double *, int, dou
     return QS_ERR_UNSUPPORTED;
 }
 qs_status k_param_table(qs_state *, const std::vector<int> &, const std::vector<int> &, const double *, int, double,
-                        uint32_t *) {
+                        uint32_t *, bool) {
     set_error("batched parameters are not emulated");
     return QS_ERR_UNSUPPORTED;
 }
+bool c128_fp64() { return false; }
 qs_status k_ising_table(qs_state *, const IsingTabP &) { return QS_OK; }
 }  // namespace qsim
 
