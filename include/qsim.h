@@ -133,11 +133,14 @@ typedef struct qs_opts {
    and the result is joined back into a double; the error per gate is a few
    2^-47 of the amplitudes' magnitude (~1e-14). This covers one-gate passes of
    dense 1- and 2-qubit gates and tiled passes, per-member angles and the
-   adjoint sweep's gradient ops included (GB300's FP64 rate would bind them
-   at a third of the HBM bandwidth or less). QS_OPT_C128_FP64 in qs_opts.flags runs every complex128
-   gate of the call in FP64 instead. Either way, one-gate passes of diagonal
-   gates and of dense gates on 3 to 5 qubits are FP64 (swaps move amplitudes
-   exactly), and read-outs and gradient partials accumulate in FP64. The double-float range is that of a float
+   adjoint sweep's gradient ops included (GB300's FP64 rate would bind them at
+   a third of the HBM bandwidth or less). QS_OPT_C128_FP64 in qs_opts.flags
+   runs every complex128 gate of the call in FP64 instead (the calls that take
+   qs_opts: gate application, batched application, channels and plans; the
+   Trotter, adiabatic, evolution and gradient calls always use the default).
+   Either way, one-gate passes of diagonal gates and of dense gates on 3 to 5
+   qubits are FP64 (swaps move amplitudes exactly), and read-outs and gradient
+   partials accumulate in FP64. The double-float range is that of a float
    pair: amplitudes of magnitude 2^128 or more, and non-finite ones, are not
    represented (below 2^-126 they become 0); use the FP64 flag for such
    states. */
