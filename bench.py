@@ -19,7 +19,7 @@ simulator) on the host cores on a bounded sample of the same workload.
 ``--only NAME`` runs one secondary workload alone (variational_adjoint,
 variational_adjoint_c128, adiabatic_batch, adiabatic_batch_c128, fused_tc,
 unfused_passes, qft_n18_c128, random_layer_c128_n33, measurement,
-host_memory) and prints its result as one JSON line: for profiling those
+host_memory, evolution, density_channels) and prints its result as one JSON line: for profiling those
 kernels; it is not the benchmark line.
 """
 from __future__ import annotations
@@ -627,6 +627,90 @@ def random_layer_c128(n: int = 33, layers: int = 2) -> dict:
     return out
 
 
+def _profiled(fn):
+    """Run fn once with the library's per-class launch accounting on: class ->
+    (ms, launches, GB, GB/s as a fraction of the measured HBM peak)."""
+    import torch
+    from paper_2009_01845_gb300 import qsim
+    qsim.profile_collect()
+    qsim.profile_enable(True)
+    fn()
+    torch.cuda.synchronize()
+    qsim.profile_enable(False)
+    peak = _peak_hbm()
+    out = {}
+    for k, v in qsim.profile_collect().items():
+        ms, launches, nbytes = v[0], v[1], v[2]
+        if launches:
+            out[k] = {"ms": ms, "launches": launches, "GB": nbytes / 1e9,
+                      "hbm_frac": nbytes / (ms / 1000.0) / 1e9 / peak if ms > 0 and nbytes else None}
+    return out
+
+
+def evolution(n: int = 24, steps: int = 10) -> dict:
+    """Exact time evolution (Sec. 2.6) at n = 24: H(s) = (1 - s) H0 + s H1,
+    H0 = -sum X, H1 = a seeded Ising chain with fields plus 8 random Pauli
+    terms; T = steps * dt, dt = 0.05; the exp (Taylor), rk4 and rk45 solvers
+    in complex64 and complex128: steps/s and the kernels' HBM fractions
+    (H psi and the state combinations)."""
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    h0 = qi.transverse_field_terms(n)
+    h1 = qi.random_ising_terms(n, qi.rng(31)) + qi.random_pauli_terms(n, 8, seed=32)
+    dt = 0.05
+    out = {"workload": f"exact evolution, n={n}, {steps} steps of dt={dt}, H0 = -sum X, H1 = Ising + 8 Pauli terms"}
+    for dtype in ("c64", "c128"):
+        st = qsim.State(n, dtype=dtype)
+        for solver in ("exp", "rk4", "rk45"):
+            run = lambda: st.init_plus().evolve(h0, h1, steps * dt, dt, solver=solver)
+            t = _time_cuda(run, 1, warmup=1, jit=False)
+            out[f"{dtype}_{solver}"] = {"ms": t, "steps_per_s": steps / (t / 1000.0), "kernels": _profiled(run)}
+        st.close()
+        del st
+        torch.cuda.empty_cache()
+    return out
+
+
+def density_channels(n: int = 14, layers: int = 4) -> dict:
+    """Density matrices and noise (Sec. 2.4) at n = 14 (rho as a 28-qubit
+    vector): per layer U3 on every qubit and the CZ ladder (random-layer
+    circuit, seed 6) as rho -> U rho U^dag, then a depolarizing channel
+    (p = 0.01) on every qubit, in complex64 and complex128: gates and channels
+    per second and the kernels' HBM fractions."""
+    import numpy as np
+    import torch
+    from paper_2009_01845_gb300 import inputs as qi
+    from paper_2009_01845_gb300 import qsim
+    gates = qi.random_layer_circuit(n, layers, seed=6)
+    p = 0.01
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Y = np.array([[0, -1j], [1j, 0]], dtype=complex)
+    Z = np.diag([1.0, -1.0]).astype(complex)
+    dep = [np.sqrt(1 - 3 * p / 4) * np.eye(2), np.sqrt(p / 4) * X, np.sqrt(p / 4) * Y, np.sqrt(p / 4) * Z]
+    chans = [([q], dep) for q in range(n)]
+    per_layer = len(gates) // layers
+    out = {"workload": f"density matrix n={n} (4^n entries), {layers} random layers + depolarizing p={p} on every qubit"}
+    for dtype in ("c64", "c128"):
+        dm = qsim.DensityMatrix(n, dtype=dtype)
+        psi0 = np.zeros(1 << n, dtype=complex)
+        psi0[0] = 1.0
+
+        def run():
+            dm.init_pure(psi0)
+            for l in range(layers):
+                dm.apply(gates[l * per_layer:(l + 1) * per_layer])
+                dm.apply_channels(chans)
+
+        t = _time_cuda(run, 1, warmup=2)
+        ops = len(gates) + layers * n
+        out[dtype] = {"ms": t, "ops_per_s": ops / (t / 1000.0), "trace": float(dm.trace()[0]),
+                      "kernels": _profiled(run)}
+        del dm
+        torch.cuda.empty_cache()
+    return out
+
+
 def summary(line: dict) -> dict:
     """A compact digest of the line: headline, roofline, and one or two
     figures per secondary workload."""
@@ -680,6 +764,12 @@ def summary(line: dict) -> dict:
     if rc:
         out["c128_n33_gate_per_s"] = {k: rnd(v["gate_apps_per_s"]) for k, v in rc.items() if isinstance(v, dict)}
         out["c128_n33_full_circuit_s"] = rnd(get(rc, "tiled", "ms") / 1000.0) if get(rc, "tiled", "ms") else None
+    ev = sec.get("evolution")
+    if ev:
+        out["evolution_steps_per_s"] = {k: rnd(v["steps_per_s"]) for k, v in ev.items() if isinstance(v, dict)}
+    dc = sec.get("density_channels")
+    if dc:
+        out["density_ops_per_s"] = {k: rnd(v["ops_per_s"]) for k, v in dc.items() if isinstance(v, dict)}
     ms = sec.get("measurement")
     if ms:
         out["marginal_hbm_frac"] = [rnd(m["frac_of_measured_hbm"], 3) for m in ms["marginals"]]
@@ -942,6 +1032,8 @@ SECONDARY = {
     "qft_n18_c128": lambda: qft_n18(),
     "random_layer_c128_n33": lambda: random_layer_c128(),
     "measurement": lambda: measurement(),
+    "evolution": lambda: evolution(),
+    "density_channels": lambda: density_channels(),
     "host_memory": lambda: host_memory(),
 }
 

@@ -39,12 +39,25 @@ template <typename R> struct PauliApplyP {
     int gdiag;
     uint16_t dord[kPAMaxTerms];
     int dmb[17];
+    // The Z-only group's terms of weight 0, 1 and 2 (an Ising energy) are not
+    // in dord: the tile kernel evaluates E(y) = qc0 + sum_i qh[i] z_i +
+    // sum_{i<j} qJ[i][j] z_i z_j (z_i = 1 - 2 y_i, index bits, qJ symmetric
+    // with a zero diagonal) by its split over the outside bits (per tile), the
+    // thread bits (per thread) and the chunk bits (per output); qecc[c] is the
+    // chunk bits' pair energy for chunk value c. quad = 0: no such term.
+    int quad;
+    R qc0;
+    R qh[32];
+    R qJ[32][32];
+    R qecc[16];
     int ng;
     int n;
     int ms;
     int accumulate;
     uint64_t total;
 };
+
+static_assert(sizeof(PauliApplyP<double>) <= 32764, "Pauli-sum kernel parameters exceed the parameter space");
 
 constexpr int kGRMaxRows = 1024;   // parameters per reduction launch
 constexpr int kGRMaxSlots = 2048;  // gradient slots per reduction launch

@@ -69,7 +69,25 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
                                                                const __grid_constant__ PauliApplyP<R> p) {
     constexpr int K = PATile<R>::kBits;
     constexpr int PER = (1 << K) / 256;
+    constexpr int CB = K - 8;  // chunk bits: bits 8 .. K-1 tell a thread's outputs apart
     __shared__ V<R> tile[1 << K];
+    __shared__ R s_f[K];       // Ising fields of the outside bits on the tile bits
+    __shared__ R s_eout;       // the outside bits' own energy
+    // per thread, once: the thread bits' pair energy and their fields on the chunk bits
+    R e_bb = 0, g_b[CB];
+    if (p.quad) {
+        const uint32_t tb = threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < CB; ++j) g_b[j] = 0;
+        for (int i = 0; i < 8; ++i) {
+            const R zi = ((tb >> i) & 1u) ? R(-1) : R(1);
+            R half = 0;
+            for (int j = 0; j < 8; ++j) half += ((tb >> j) & 1u) ? -p.qJ[i][j] : p.qJ[i][j];
+            e_bb += R(0.5) * zi * half;
+#pragma unroll
+            for (int j = 0; j < CB; ++j) g_b[j] += zi * p.qJ[8 + j][i];
+        }
+    }
     const uint32_t lowm = (1u << K) - 1u;
     const uint64_t tiles = p.total >> K;
     const int tshift = p.n - K;  // tiles per member: 2^tshift
@@ -79,6 +97,27 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
         const V<R> *sm = src + moff;
         V<R> *dm = dst + moff;
         __syncthreads();  // the previous tile's readers are done
+        if (p.quad) {
+            // warp 0: the outside bits' fields on tile bit j (lanes j < K);
+            // warp 1: the outside energy, one outside bit per lane, summed
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (warp == 0 && lane < K) {
+                R f = p.qh[lane];
+                for (int i = K; i < p.n; ++i) f += ((yb >> i) & 1u) ? -p.qJ[lane][i] : p.qJ[lane][i];
+                s_f[lane] = f;
+            } else if (warp == 1) {
+                R u = 0;
+                const int i = K + lane;
+                if (i < p.n) {
+                    R half = 0;
+                    for (int j = K; j < p.n; ++j) half += ((yb >> j) & 1u) ? -p.qJ[i][j] : p.qJ[i][j];
+                    u = (((yb >> i) & 1u) ? R(-1) : R(1)) * (p.qh[i] + R(0.5) * half);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+                if (lane == 0) s_eout = p.qc0 + u;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < PER; ++j) tile[threadIdx.x + 256 * j] = sm[yb + threadIdx.x + 256 * j];
         __syncthreads();
@@ -110,6 +149,23 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
                         Di[i] = ui + vi;
                         Di[i | h] = ui - vi;
                     }
+            if (p.quad) {
+                // E = outside energy + thread bits (their fields from outside,
+                // their pairs) + chunk bits (fields from outside and from the
+                // thread bits, their pairs)
+                R base = s_eout + e_bb, g[CB];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) base += ((threadIdx.x >> i) & 1u) ? -s_f[i] : s_f[i];
+#pragma unroll
+                for (int j = 0; j < CB; ++j) g[j] = s_f[8 + j] + g_b[j];
+#pragma unroll
+                for (int c = 0; c < PER; ++c) {
+                    R e = base + p.qecc[c];
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) e += ((c >> j) & 1) ? -g[j] : g[j];
+                    Dr[c] += e;
+                }
+            }
         }
         // groups outer, this thread's PER outputs inner: the PER partner loads of
         // one X mask are independent and in flight together
@@ -279,11 +335,48 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
             if (p.gx[g] == 0 && !p.gconst[g]) p.gdiag = g;
         if (p.gdiag >= 0) {
             constexpr int cb = PATile<R>::kBits - 8;  // log2 of outputs per thread
+            // weight 0-2 terms of the Z-only group: the Ising form (tile kernel
+            // only, n <= 32); the others by their parities per chunk mask
+            const bool tiled = n >= PATile<R>::kBits && n <= 32;
+            std::vector<char> quad(kPAMaxTerms, 0);
+            if (tiled) {
+                std::vector<double> h(32, 0.0), J(32 * 32, 0.0);
+                double c0 = 0.0;
+                for (int t = p.gbeg[p.gdiag]; t < p.gbeg[p.gdiag + 1]; ++t) {
+                    const uint64_t zb = p.zb[t];
+                    const int w = __builtin_popcountll(zb);
+                    if (w > 2) continue;
+                    quad[t] = 1;
+                    p.quad = 1;
+                    const double c = (double)p.cre[t];  // Z-only terms: real coefficients
+                    if (w == 0) {
+                        c0 += c;
+                    } else if (w == 1) {
+                        h[__builtin_ctzll(zb)] += c;
+                    } else {
+                        const int i = __builtin_ctzll(zb), j = 63 - __builtin_clzll(zb);
+                        J[i * 32 + j] += c;
+                        J[j * 32 + i] += c;
+                    }
+                }
+                p.qc0 = (R)c0;
+                for (int i = 0; i < 32; ++i) {
+                    p.qh[i] = (R)h[i];
+                    for (int j = 0; j < 32; ++j) p.qJ[i][j] = (R)J[i * 32 + j];
+                }
+                for (int c = 0; c < (1 << cb); ++c) {
+                    double e = 0.0;
+                    for (int i = 0; i < cb; ++i)
+                        for (int j = i + 1; j < cb; ++j)
+                            e += ((((c >> i) ^ (c >> j)) & 1) ? -1.0 : 1.0) * J[(8 + i) * 32 + 8 + j];
+                    p.qecc[c] = (R)e;
+                }
+            }
             int k2 = 0;
             for (int m = 0; m < (1 << cb); ++m) {
                 p.dmb[m] = k2;
                 for (int t = p.gbeg[p.gdiag]; t < p.gbeg[p.gdiag + 1]; ++t)
-                    if ((int)((p.zb[t] >> 8) & ((1u << cb) - 1u)) == m) p.dord[k2++] = (uint16_t)t;
+                    if (!quad[t] && (int)((p.zb[t] >> 8) & ((1u << cb) - 1u)) == m) p.dord[k2++] = (uint16_t)t;
             }
             p.dmb[1 << cb] = k2;
         }
