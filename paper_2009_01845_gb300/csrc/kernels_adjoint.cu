@@ -6,6 +6,7 @@
 // The reverse sweep itself runs in the tiled pass kernel (TOP_GRAD ops).
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "adjoint.h"
 #include "device.cuh"
@@ -64,13 +65,43 @@ __global__ void __launch_bounds__(256) pauli_apply_kernel(const V<R> *__restrict
 // offsets tid + 256 j).
 template <typename R> struct PATile { static constexpr int kBits = sizeof(R) == 4 ? 12 : 11; };
 
-template <typename R>
-__global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__restrict__ src, V<R> *__restrict__ dst,
+// Amplitude arithmetic A of the tile kernel: the state's own (complex64), or
+// double-float for complex128 (loads split, stores joined; the coefficients,
+// R = double, are summed in FP64 and converted per use).
+template <typename A, typename R> __device__ __forceinline__ V<A> amp_in(const V<R> *p, uint64_t i) {
+    if constexpr (is_dd<A>) {
+        const double2 v = p[i];
+        return mkc<dd>(dd(v.x), dd(v.y));
+    } else {
+        return p[i];
+    }
+}
+template <typename A, typename R> __device__ __forceinline__ void amp_out(V<R> *p, uint64_t i, V<A> v) {
+    if constexpr (is_dd<A>)
+        p[i] = make_double2(to_double(re_of<dd>(v)), to_double(im_of<dd>(v)));
+    else
+        p[i] = v;
+}
+template <typename A> __device__ __forceinline__ V<A> coef(double re, double im) {
+    if constexpr (is_dd<A>)
+        return mkc<dd>(dd(re), dd(im));
+    else
+        return mkc<A>((A)re, (A)im);
+}
+template <typename A> __device__ __forceinline__ V<A> cadd(V<A> a, V<A> b) {
+    if constexpr (is_dd<A>)
+        return dd_cadd(a, b);
+    else
+        return mkc<A>(a.x + b.x, a.y + b.y);
+}
+
+template <typename R, typename A>
+__global__ void __launch_bounds__(256, is_dd<A> ? 1 : 2) pauli_apply_tile_kernel(const V<R> *__restrict__ src, V<R> *__restrict__ dst,
                                                                const __grid_constant__ PauliApplyP<R> p) {
     constexpr int K = PATile<R>::kBits;
     constexpr int PER = (1 << K) / 256;
     constexpr int CB = K - 8;  // chunk bits: bits 8 .. K-1 tell a thread's outputs apart
-    __shared__ V<R> tile[1 << K];
+    __shared__ V<A> tile[1 << K];
     __shared__ R s_f[K];       // Ising fields of the outside bits on the tile bits
     __shared__ R s_eout;       // the outside bits' own energy
     // per thread, once: the thread bits' pair energy and their fields on the chunk bits
@@ -119,7 +150,7 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
             }
         }
 #pragma unroll
-        for (int j = 0; j < PER; ++j) tile[threadIdx.x + 256 * j] = sm[yb + threadIdx.x + 256 * j];
+        for (int j = 0; j < PER; ++j) tile[threadIdx.x + 256 * j] = amp_in<A, R>(sm, yb + threadIdx.x + 256 * j);
         __syncthreads();
         // Z-only group: coefficient of output j = f(j), from the terms' signs on
         // the other bits summed per mask of bits 8.. and a Walsh-Hadamard
@@ -169,36 +200,37 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
         }
         // groups outer, this thread's PER outputs inner: the PER partner loads of
         // one X mask are independent and in flight together
-        V<R> acc[PER];
+        V<A> acc[PER];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) acc[j] = p.accumulate ? dm[yb | (threadIdx.x + 256 * j)] : mkc<R>(0, 0);
+        for (int j = 0; j < PER; ++j)
+            acc[j] = p.accumulate ? amp_in<A, R>(dm, yb | (threadIdx.x + 256 * j)) : coef<A>(0.0, 0.0);
         for (int g = 0; g < p.ng; ++g) {
             const uint32_t m = (uint32_t)p.gx[g];
-            V<R> v[PER];
+            V<A> v[PER];
             if ((m & ~lowm) == 0) {
 #pragma unroll
                 for (int j = 0; j < PER; ++j) v[j] = tile[(threadIdx.x + 256 * j) ^ m];
             } else {
 #pragma unroll
-                for (int j = 0; j < PER; ++j) v[j] = sm[(yb | (threadIdx.x + 256 * j)) ^ m];
+                for (int j = 0; j < PER; ++j) v[j] = amp_in<A, R>(sm, (yb | (threadIdx.x + 256 * j)) ^ m);
             }
             if (g == p.gdiag) {
 #pragma unroll
-                for (int j = 0; j < PER; ++j) acc[j] = cmadd<R>(mkc<R>(Dr[j], Di[j]), v[j], acc[j]);
+                for (int j = 0; j < PER; ++j) acc[j] = cmadd<A>(coef<A>(Dr[j], Di[j]), v[j], acc[j]);
             } else if (g < p.run0) {
                 // the leading run of groups with one coefficient: partners
                 // summed, then multiplied once
 #pragma unroll
-                for (int j = 0; j < PER; ++j) acc[j] = mkc<R>(acc[j].x + v[j].x, acc[j].y + v[j].y);
+                for (int j = 0; j < PER; ++j) acc[j] = cadd<A>(acc[j], v[j]);
                 if (g + 1 == p.run0) {
-                    const V<R> c = mkc<R>(p.gcre[g], p.gcim[g]);
+                    const V<A> c = coef<A>(p.gcre[g], p.gcim[g]);
 #pragma unroll
-                    for (int j = 0; j < PER; ++j) acc[j] = cmul<R>(c, acc[j]);
+                    for (int j = 0; j < PER; ++j) acc[j] = cmul<A>(c, acc[j]);
                 }
             } else if (p.gconst[g]) {
-                const V<R> c = mkc<R>(p.gcre[g], p.gcim[g]);
+                const V<A> c = coef<A>(p.gcre[g], p.gcim[g]);
 #pragma unroll
-                for (int j = 0; j < PER; ++j) acc[j] = cmadd<R>(c, v[j], acc[j]);
+                for (int j = 0; j < PER; ++j) acc[j] = cmadd<A>(c, v[j], acc[j]);
             } else {
 #pragma unroll
                 for (int j = 0; j < PER; ++j) {
@@ -209,12 +241,12 @@ __global__ void __launch_bounds__(256) pauli_apply_tile_kernel(const V<R> *__res
                         fr += odd ? -p.cre[tt] : p.cre[tt];
                         fi += odd ? -p.cim[tt] : p.cim[tt];
                     }
-                    acc[j] = cmadd<R>(mkc<R>(fr, fi), v[j], acc[j]);
+                    acc[j] = cmadd<A>(coef<A>(fr, fi), v[j], acc[j]);
                 }
             }
         }
 #pragma unroll
-        for (int j = 0; j < PER; ++j) dm[yb | (threadIdx.x + 256 * j)] = acc[j];
+        for (int j = 0; j < PER; ++j) amp_out<A, R>(dm, yb | (threadIdx.x + 256 * j), acc[j]);
     }
 }
 
@@ -385,8 +417,10 @@ static qs_status pauli_apply_t(const StateView &src, const StateView &dst, const
         p.total = total;
         p.accumulate = first ? 0 : 1;
         first = false;
+        // complex128 partner arithmetic in double-float
+        using A = typename std::conditional<sizeof(R) == 4, float, dd>::type;
         if (n >= PATile<R>::kBits && n <= 32)
-            pauli_apply_tile_kernel<R>
+            pauli_apply_tile_kernel<R, A>
                 <<<grid_cap(total >> PATile<R>::kBits, 1), 256, 0, st>>>((const V<R> *)src.data, (V<R> *)dst.data, p);
         else if (n <= 32)
             pauli_apply_kernel<R, uint32_t>
