@@ -203,7 +203,8 @@ OPT_C128_FP64 = 1
 
 
 def opts(mode: str = "auto", tile_qubits: int = 0, fuse_qubits: int = 0, fp64: bool = False) -> COpts:
-    """fp64: complex128 one-gate passes in FP64 (default: double-float)."""
+    """fp64: complex128 gates of the call in FP64 (QS_OPT_C128_FP64; default:
+    double-float arithmetic on the FP32 pipes)."""
     return COpts(MODE[mode], int(tile_qubits), int(fuse_qubits), OPT_C128_FP64 if fp64 else 0)
 
 
