@@ -96,7 +96,7 @@ template <typename A> __device__ __forceinline__ V<A> cadd(V<A> a, V<A> b) {
 }
 
 template <typename R, typename A>
-__global__ void __launch_bounds__(256, is_dd<A> ? 1 : 2) pauli_apply_tile_kernel(const V<R> *__restrict__ src, V<R> *__restrict__ dst,
+__global__ void __launch_bounds__(256, 2) pauli_apply_tile_kernel(const V<R> *__restrict__ src, V<R> *__restrict__ dst,
                                                                const __grid_constant__ PauliApplyP<R> p) {
     constexpr int K = PATile<R>::kBits;
     constexpr int PER = (1 << K) / 256;
