@@ -63,6 +63,20 @@ def test_mixed_gates_with_controls(qs, dtype):
     close(st.get(), want, dtype)
 
 
+@pytest.mark.parametrize("dtype,n,batch", [("c64", 13, 3), ("c64", 14, 1), ("c128", 12, 3), ("c128", 13, 1)])
+def test_tile_counts_odd_and_even(qs, dtype, n, batch):
+    """Specialised kernels over odd and even numbers of tiles (one tile per
+    member with three members, or two tiles of one member), with per-member
+    states: every member against the oracle."""
+    gates = qi.random_layer_circuit(n, 6, seed=40 + n)
+    psis = np.stack([qi.random_state(n, 420 + b) for b in range(batch)])
+    st = qs.State(n, batch=batch, dtype=dtype).set(psis if batch > 1 else psis[0])
+    assert specialised(qs, lambda: st.apply(gates, mode="tiled")) > 0
+    got = np.asarray(st.get()).reshape(batch, -1)
+    for b in range(batch):
+        close(got[b], oracle.apply_circuit(psis[b].copy(), n, gates), dtype)
+
+
 def test_qft_closed_form(qs):
     n = 15
     x = 12345
