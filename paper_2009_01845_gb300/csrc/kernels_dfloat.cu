@@ -26,7 +26,7 @@ namespace qsim {
 namespace {
 
 template <int K> struct DenseDFP {
-    ddc m[(1 << K) * (1 << K)];  // row-major, split on the host
+    PairFactor m[(1 << K) * (1 << K)];  // row-major, split and arranged on the host
     uint64_t off[1 << K];
     uint64_t setmask;
     InsertBits ib;
@@ -35,18 +35,32 @@ template <int K> struct DenseDFP {
     uint64_t total;
 };
 
-template <int K>
+// zero bits inserted at ib's positions into g, in I-bit arithmetic (every
+// shift below the width)
+template <typename I> __device__ __forceinline__ I expand_bits_i(I g, const InsertBits &ib) {
+    for (int i = 0; i < ib.count; ++i) {
+        const int q = ib.pos[i];
+        const I lo = g & ((I(1) << q) - I(1));
+        g = (((g >> q) << q) << 1) | lo;
+    }
+    return g;
+}
+
+// I: the index type, 32-bit where every amplitude index of the batch fits
+template <int K, typename I>
 __global__ void __launch_bounds__(256) dense_df_kernel(double2 *__restrict__ psi,
                                                        const __grid_constant__ DenseDFP<K> p) {
     constexpr int D = 1 << K;
-    const uint64_t fmask = (1ull << p.n_free) - 1ull;
-    for (uint64_t g = global_tid(); g < p.total; g += global_stride()) {
-        const uint64_t b = g >> p.n_free;
-        const uint64_t base = (b << p.n) | expand_bits(g & fmask, p.ib) | p.setmask;
+    const I fmask = (I(1) << p.n_free) - I(1);
+    const I total = (I)p.total;
+    for (I g = (I)global_tid(); g < total; g += (I)global_stride()) {
+        const I b = g >> p.n_free;
+        // b > 0 only in a batch, whose member stride is then below the width
+        const I base = (b << (p.n & (int)(8 * sizeof(I) - 1))) | expand_bits_i<I>(g & fmask, p.ib) | (I)p.setmask;
         ddc a[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const double2 v = psi[base | p.off[c]];
+            const double2 v = psi[base | (I)p.off[c]];
             a[c] = mkc<dd>(dd(v.x), dd(v.y));
         }
 #pragma unroll
@@ -55,7 +69,7 @@ __global__ void __launch_bounds__(256) dense_df_kernel(double2 *__restrict__ psi
 #pragma unroll
             for (int c = 1; c < D; ++c) prod_add(acc, p.m[r * D + c], a[c]);
             const ddc w = prod_result(acc);
-            psi[base | p.off[r]] = make_double2(to_double(re_of<dd>(w)), to_double(im_of<dd>(w)));
+            psi[base | (I)p.off[r]] = make_double2(to_double(re_of<dd>(w)), to_double(im_of<dd>(w)));
         }
     }
 }
@@ -70,7 +84,7 @@ template <int K> qs_status launch_dense_df(qs_state *s, const LGate &g) {
     constexpr int D = 1 << K;
     DenseDFP<K> p;
     std::memset(&p, 0, sizeof(p));
-    for (int i = 0; i < D * D; ++i) p.m[i] = mkc<dd>(dd(g.m[i].real()), dd(g.m[i].imag()));
+    for (int i = 0; i < D * D; ++i) p.m[i] = pair_factor(mkc<dd>(dd(g.m[i].real()), dd(g.m[i].imag())));
     uint64_t tmask = 0;
     for (int j = 0; j < K; ++j) tmask |= 1ull << g.tbit[j];
     for (int l = 0; l < D; ++l) {
@@ -90,7 +104,10 @@ template <int K> qs_status launch_dense_df(qs_state *s, const LGate &g) {
     p.total = (uint64_t)s->batch << p.n_free;
     const double amps = (double)p.total * D;
     ProfScope _ps(s->stream, KC_DENSE, amps * 2.0 * 16.0, amps * 8.0 * D);
-    dense_df_kernel<K><<<grid_for_df(s, p.total), 256, 0, s->stream>>>((double2 *)s->data, p);
+    if (((uint64_t)s->batch << s->ms) <= (1ull << 32))
+        dense_df_kernel<K, uint32_t><<<grid_for_df(s, p.total), 256, 0, s->stream>>>((double2 *)s->data, p);
+    else
+        dense_df_kernel<K, uint64_t><<<grid_for_df(s, p.total), 256, 0, s->stream>>>((double2 *)s->data, p);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;
 }
